@@ -1,0 +1,123 @@
+"""CPU FP64 oracle - TEST INFRASTRUCTURE ONLY.
+
+Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline / reference legs of `bench.py` may
+import this package.  The GPU product path (`paper_1912_13403_gb300`) never imports it and shares
+no code with it.
+
+Two parts:
+  * `jacobi.c` (built into `_build/liboracle.so` with gcc + OpenMP): the plain definition of the
+    result - Jacobi eigenpairs of S and of H~ = S^{-1/2} H S^{-1/2}, then P = C_occ C_occ^T
+    (Sec. 1 Eqs. evp, density_matrix; Sec. 2.2.2 Eq. ntpoly_lowdin).
+  * `steps.py` (numpy float64): the individual steps of the purification route written out in
+    the paper's order (Eq. ntpoly_scale_hamiltonian initial guess, Eq. ntpoly_purification with
+    the trace-resetting map the paper cites, Loewdin orthogonalisation), plus the closed forms
+    the synthetic inputs allow.
+
+Parity status: every function here is pinned by `tests/test_oracle_*.py` against closed forms,
+library eigensolvers on special cases, invariants or brute force; none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "jacobi.c")
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "OK", 1: "ERR_ARG", 3: "NOT_SPD", 5: "NO_GAP", 6: "NOT_CONVERGED", 7: "OOM"}
+
+
+def build(force: bool = False) -> str:
+    """Compile jacobi.c with gcc (-O2 -fopenmp); returns the path of the shared object."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99", _SRC, "-o", tmp, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            lib = ctypes.CDLL(path)
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.oracle_jacobi_eigh.argtypes = [ctypes.c_int64, dp, dp, dp, ctypes.c_double,
+                                               ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+            lib.oracle_jacobi_eigh.restype = ctypes.c_int
+            lib.oracle_inv_sqrt.argtypes = [ctypes.c_int64, dp, dp, dp, dp]
+            lib.oracle_inv_sqrt.restype = ctypes.c_int
+            lib.oracle_density_matrix.argtypes = [ctypes.c_int64, ctypes.c_int64, dp, dp, dp,
+                                                  dp, dp, dp, dp, dp]
+            lib.oracle_density_matrix.restype = ctypes.c_int
+            lib.oracle_num_threads.argtypes = []
+            lib.oracle_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def num_threads() -> int:
+    """OpenMP threads the C oracle runs with."""
+    return int(_load().oracle_num_threads())
+
+
+def jacobi_eigh(A, tol: float = 1e-15, max_sweeps: int = 60):
+    """Eigenpairs of a symmetric matrix by two-sided cyclic Jacobi.
+    Returns (evals ascending, V with eigenvectors in columns, sweeps, status string)."""
+    A = _f64(A).copy()
+    n = A.shape[0]
+    w = np.empty(n)
+    V = np.empty((n, n))
+    sw = ctypes.c_int(0)
+    st = _load().oracle_jacobi_eigh(n, _ptr(A), _ptr(w), _ptr(V), tol, max_sweeps,
+                                    ctypes.byref(sw))
+    return w, V, int(sw.value), STATUS.get(st, str(st))
+
+
+def inv_sqrt(S):
+    """Loewdin factor Z = S^{-1/2} (Eq. ntpoly_lowdin) via Jacobi.  Returns (Z, status)."""
+    S = _f64(S)
+    n = S.shape[0]
+    Z = np.empty((n, n))
+    smin = ctypes.c_double(0)
+    smax = ctypes.c_double(0)
+    st = _load().oracle_inv_sqrt(n, _ptr(S), _ptr(Z), ctypes.byref(smin), ctypes.byref(smax))
+    return Z, STATUS.get(st, str(st))
+
+
+def density_matrix(H, S, n_occ: int):
+    """Zero-temperature density matrix (Eq. density_matrix, f_l in {0,1}) of (H, S).
+
+    Returns dict(P, energy, trace_ps, idem, gap, evals, status)."""
+    H = _f64(H)
+    S = _f64(S)
+    n = H.shape[0]
+    P = np.empty((n, n))
+    w = np.empty(n)
+    e, t, d, g = (ctypes.c_double(0) for _ in range(4))
+    st = _load().oracle_density_matrix(n, int(n_occ), _ptr(H), _ptr(S), _ptr(P),
+                                       ctypes.byref(e), ctypes.byref(t), ctypes.byref(d),
+                                       ctypes.byref(g), _ptr(w))
+    return dict(P=P, energy=e.value, trace_ps=t.value, idem=d.value, gap=g.value, evals=w,
+                status=STATUS.get(st, str(st)))

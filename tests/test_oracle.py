@@ -1,0 +1,299 @@
+"""Pins for the CPU oracle (runs without a GPU).
+
+The oracle is checked against things other than itself: closed forms of the synthetic inputs,
+library eigensolvers on special cases, hand-derived golden values, invariants of the density
+matrix (Sec. 2.2.2, Eq. density_matrix_conditions, mapped to the S metric) and brute force over
+all occupation choices on tiny inputs.  A few tests plant a mistake in a copy of an oracle step
+and check that a pin catches it.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+from oracle import steps
+from workloads import (make_config0, make_random_small, make_small_diag, make_spectrum_problem,
+                       haar_orthogonal)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+# ------------------------------------------------------------------------------------------
+# Jacobi eigensolver
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 7, 40, 41])
+def test_jacobi_recovers_constructed_spectrum(n):
+    rng = np.random.default_rng(100 + n)
+    Q = haar_orthogonal(rng, n)
+    lam = np.sort(rng.uniform(-5, 5, n))
+    A = (Q * lam) @ Q.T
+    w, V, sweeps, st = oracle.jacobi_eigh(A)
+    assert st == "OK"
+    assert np.max(np.abs(w - lam)) <= 1e-12 * max(1.0, np.abs(lam).max())
+    assert np.linalg.norm(V.T @ V - np.eye(n)) <= 1e-12 * n
+    assert np.linalg.norm(A @ V - V * w) <= 1e-11 * np.linalg.norm(A) + 1e-300
+
+
+def test_jacobi_matches_library_eigvalsh():
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((64, 64))
+    A = A + A.T
+    w, V, _, st = oracle.jacobi_eigh(A)
+    assert st == "OK"
+    np.testing.assert_allclose(w, np.linalg.eigvalsh(A), rtol=0, atol=1e-12 * np.abs(w).max())
+
+
+def test_jacobi_repeated_eigenvalues_keep_orthonormal_basis():
+    rng = np.random.default_rng(6)
+    n = 12
+    Q = haar_orthogonal(rng, n)
+    lam = np.array([1.0] * 5 + [2.0] * 7)
+    w, V, _, st = oracle.jacobi_eigh((Q * lam) @ Q.T)
+    assert st == "OK"
+    np.testing.assert_allclose(w, lam, atol=1e-13)
+    assert np.linalg.norm(V.T @ V - np.eye(n)) < 1e-12
+
+
+# ------------------------------------------------------------------------------------------
+# density matrix: closed forms, special cases, golden values
+# ------------------------------------------------------------------------------------------
+
+def test_dm_config0_closed_form():
+    p = make_config0()
+    r = oracle.density_matrix(p.H, p.S, p.n_occ)
+    Pc, Ec = steps.closed_form_dm(p.factors, p.n_occ)
+    assert r["status"] == "OK"
+    assert rel(r["P"], Pc) <= 1e-11
+    assert abs(r["energy"] - Ec) <= 1e-10 * abs(Ec)
+    assert abs(r["trace_ps"] - p.n_occ) <= 1e-10
+    assert r["idem"] <= 1e-10
+    np.testing.assert_allclose(r["evals"], p.factors["lam"], atol=1e-11)
+
+
+@pytest.mark.parametrize("cond,gap", [(10.0, 0.5), (1e3, 0.2), (1e3, 0.05)])
+def test_dm_ill_conditioned_overlap_closed_form(cond, gap):
+    p = make_spectrum_problem(7, 96, 24, cond_S=cond, gap=gap)
+    r = oracle.density_matrix(p.H, p.S, p.n_occ)
+    Pc, Ec = steps.closed_form_dm(p.factors, p.n_occ)
+    assert r["status"] == "OK"
+    assert rel(r["P"], Pc) <= 1e-10
+    assert abs(r["energy"] - Ec) <= 1e-10 * max(1.0, abs(Ec))
+    assert abs(r["gap"] - gap) <= 1e-10
+
+
+def test_dm_identity_overlap_is_standard_eigenproblem():
+    p = make_random_small(11, 50, 17)
+    S = np.eye(50)
+    r = oracle.density_matrix(p.H, S, p.n_occ)
+    w, V = np.linalg.eigh(p.H)
+    Vo = V[:, :p.n_occ]
+    assert rel(r["P"], Vo @ Vo.T) <= 1e-11
+    assert abs(r["energy"] - w[:p.n_occ].sum()) <= 1e-11 * abs(w[:p.n_occ].sum())
+
+
+def test_dm_diagonal_case():
+    p = make_small_diag(3, 20, 6)
+    h, s = np.diag(p.H), np.diag(p.S)
+    order = np.argsort(h / s, kind="stable")[:6]
+    P_expect = np.zeros((20, 20))
+    P_expect[order, order] = 1.0 / s[order]
+    r = oracle.density_matrix(p.H, p.S, 6)
+    assert np.max(np.abs(r["P"] - P_expect)) <= 1e-13
+    assert abs(r["energy"] - np.sort(h / s)[:6].sum()) <= 1e-13
+
+
+def test_dm_golden_2x2():
+    with open(os.path.join(GOLDEN, "dm_2x2.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        r = oracle.density_matrix(np.array(c["H"]), np.array(c["S"]), c["n_occ"])
+        np.testing.assert_allclose(r["P"], np.array(c["P"]), atol=1e-14, err_msg=c["name"])
+        assert abs(r["energy"] - c["energy"]) <= 1e-14, c["name"]
+        np.testing.assert_allclose(r["evals"], c["evals"], atol=1e-14, err_msg=c["name"])
+
+
+def test_dm_full_occupation_is_inverse_overlap():
+    p = make_random_small(12, 30, 30)
+    r = oracle.density_matrix(p.H, p.S, 30)
+    assert rel(r["P"], np.linalg.inv(p.S)) <= 1e-12
+
+
+def test_dm_zero_occupation():
+    p = make_random_small(13, 10, 0)
+    r = oracle.density_matrix(p.H, p.S, 0)
+    assert np.all(r["P"] == 0.0) and r["energy"] == 0.0
+
+
+@pytest.mark.parametrize("n,n_occ", [(4, 2), (6, 2), (7, 3), (8, 4)])
+def test_dm_brute_force_minimum(n, n_occ):
+    """Among all projectors onto n_occ generalised eigenvectors, the oracle's P has the least
+    band energy Tr(P H), and it equals that projector."""
+    p = make_random_small(20 + n, n, n_occ)
+    w, C = scipy.linalg.eigh(p.H, p.S)  # library routine, C^T S C = I
+    best = None
+    for sub in itertools.combinations(range(n), n_occ):
+        Cs = C[:, list(sub)]
+        P = Cs @ Cs.T
+        e = float(np.sum(P * p.H))
+        if best is None or e < best[0]:
+            best = (e, P)
+    r = oracle.density_matrix(p.H, p.S, n_occ)
+    assert abs(r["energy"] - best[0]) <= 1e-12 * max(1.0, abs(best[0]))
+    assert np.max(np.abs(r["P"] - best[1])) <= 1e-11
+
+
+def test_dm_invariants_on_unstructured_input():
+    p = make_random_small(31, 60, 25)
+    r = oracle.density_matrix(p.H, p.S, p.n_occ)
+    inv = steps.invariants(r["P"], p.H, p.S, p.n_occ)
+    assert inv["idem"] < 1e-11 and inv["trace_err"] < 1e-11
+    assert inv["asym"] == 0.0 and inv["commut"] < 1e-10
+    assert abs(inv["energy"] - r["energy"]) < 1e-11 * max(1, abs(r["energy"]))
+
+
+def test_dm_status_no_gap_and_not_spd():
+    rng = np.random.default_rng(1)
+    Q = haar_orthogonal(rng, 8)
+    lam = np.array([-2.0, -1.0, 0.5, 0.5, 1.0, 2.0, 3.0, 4.0])
+    H = (Q * lam) @ Q.T
+    r = oracle.density_matrix(H, np.eye(8), 3)
+    assert r["status"] == "NO_GAP"
+    S = np.eye(8)
+    S[0, 0] = -1.0
+    assert oracle.density_matrix(H, S, 3)["status"] == "NOT_SPD"
+
+
+def test_inv_sqrt_matches_factors():
+    p = make_spectrum_problem(9, 64, 16, cond_S=1e3, gap=0.3)
+    Z, st = oracle.inv_sqrt(p.S)
+    assert st == "OK"
+    assert rel(Z, steps.closed_form_inv_sqrt(p.factors)) <= 1e-11
+
+
+# ------------------------------------------------------------------------------------------
+# step-level definitions of the purification route
+# ------------------------------------------------------------------------------------------
+
+def test_gershgorin_bounds_enclose_spectrum_and_are_tight_for_diagonal():
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((40, 40))
+    A = A + A.T
+    lo, hi = steps.gershgorin_bounds(A)
+    w = np.linalg.eigvalsh(A)
+    assert lo <= w[0] and hi >= w[-1]
+    d = rng.uniform(-3, 4, 9)
+    assert steps.gershgorin_bounds(np.diag(d)) == (d.min(), d.max())
+
+
+def test_initial_guess_maps_bounds_to_unit_interval():
+    d = np.array([-3.0, -1.0, 0.0, 2.0, 5.0])
+    X0 = steps.initial_guess(np.diag(d), d.min(), d.max())
+    np.testing.assert_allclose(np.diag(X0), (5.0 - d) / 8.0)
+    assert X0[0, 0] == 1.0 and X0[-1, -1] == 0.0
+
+
+def test_trs4_step_resets_trace_and_fixes_projectors():
+    rng = np.random.default_rng(8)
+    n, N = 30, 11
+    Q = haar_orthogonal(rng, n)
+    x = rng.uniform(0.05, 0.95, n)
+    X = (Q * x) @ Q.T
+    Xn, g, br = steps.trs4_step(X, N)
+    if br == "F+gG":
+        assert abs(np.trace(Xn) - N) <= 1e-12      # the trace-resetting property of gamma
+    # exact projectors are fixed points of every branch
+    Pq = Q[:, :N] @ Q[:, :N].T
+    Pn, _, _ = steps.trs4_step(Pq, N)
+    assert np.linalg.norm(Pn - Pq) <= 1e-12
+    # the map acts on eigenvalues only: eigenvectors are kept
+    assert np.linalg.norm(Xn @ X - X @ Xn) <= 1e-12
+
+
+def test_trs4_purify_reaches_eigh_projector():
+    p = make_random_small(41, 80, 30)
+    Ht = p.H
+    Pt, it, hist = steps.trs4_purify(Ht, 30)
+    w, V = np.linalg.eigh(Ht)
+    assert w[30] - w[29] > 1e-3
+    Vo = V[:, :30]
+    assert rel(Pt, Vo @ Vo.T) <= 1e-10
+    assert it < 100 and all(0.0 <= g <= 6.0 or br != "F+gG" for g, br in hist)
+
+
+def test_newton_schulz_and_refinement():
+    p = make_spectrum_problem(12, 64, 16, cond_S=1e3, gap=0.3)
+    Zc = steps.closed_form_inv_sqrt(p.factors)
+    Z, it = steps.newton_schulz_inv_sqrt(p.S)
+    assert rel(Z, Zc) <= 1e-9 and it < 60
+    Zp = Zc * (1.0 + 1e-4)                        # a commuting perturbation
+    e0 = rel(Zp, Zc)
+    e1 = rel(steps.inv_sqrt_refine(Zp, p.S), Zc)
+    assert e1 <= 10 * e0 ** 2                     # quadratic (in fact cubic) contraction
+
+
+def test_mcweeny_fixes_projectors_and_moves_eigenvalues_to_0_1():
+    rng = np.random.default_rng(9)
+    Q = haar_orthogonal(rng, 20)
+    x = np.concatenate([np.full(8, 0.9), np.full(12, 0.1)])
+    X = (Q * x) @ Q.T
+    Y = steps.mcweeny(X)
+    wy = np.linalg.eigvalsh(Y)
+    assert np.all(wy[:12] < 0.1) and np.all(wy[12:] > 0.9)
+
+
+def test_purification_route_matches_closed_form():
+    p = make_config0(n=128, n_occ=32, seed=5)
+    r = steps.purification_route(p.H, p.S, p.n_occ)
+    Pc, Ec = steps.closed_form_dm(p.factors, p.n_occ)
+    assert rel(r["P"], Pc) <= 1e-10
+    assert abs(r["trace_ps"] - p.n_occ) <= 1e-10
+    assert abs(r["energy"] - Ec) <= 1e-10 * abs(Ec)
+
+
+# ------------------------------------------------------------------------------------------
+# planted mistakes: each must be caught by one of the pins above
+# ------------------------------------------------------------------------------------------
+
+def _route_with(trs4_step=None, inv_sqrt=None):
+    p = make_config0(n=64, n_occ=16, seed=6)
+    Z = inv_sqrt(p.S) if inv_sqrt else steps.newton_schulz_inv_sqrt(p.S)[0]
+    Ht = steps.sym(Z @ p.H @ Z)
+    lo, hi = steps.gershgorin_bounds(Ht)
+    X = steps.initial_guess(Ht, lo, hi)
+    for _ in range(60):
+        X, _, _ = (trs4_step or steps.trs4_step)(X, p.n_occ)
+    P = Z @ X @ Z
+    Pc, _ = steps.closed_form_dm(p.factors, p.n_occ)
+    return rel(P, Pc)
+
+
+def test_planted_mistakes_are_caught():
+    assert _route_with() <= 1e-10
+
+    def wrong_sign_G(X, N):           # G = X^2 (I + X)^2 instead of (I - X)^2
+        X2 = X @ X
+        Y = np.eye(X.shape[0]) + X
+        trF = np.trace(X2 @ (4 * X - 3 * X2))
+        G = X2 @ Y @ Y
+        g = (N - trF) / np.trace(G)
+        g = min(max(g, 0.0), 6.0)
+        return steps.sym(X2 @ (4 * X - 3 * X2) + g * G), g, "F+gG"
+    assert not _route_with(trs4_step=wrong_sign_G) <= 1e-3   # NaN also counts as caught
+
+    def no_sqrt(S):                   # S^{-1} instead of S^{-1/2}
+        return np.linalg.inv(S)
+    assert not _route_with(inv_sqrt=no_sqrt) <= 1e-3
+
+    def transposed_scale(S):          # a non-symmetric "S^{-1/2}" (row/column mix-up)
+        Z = steps.newton_schulz_inv_sqrt(S)[0]
+        return Z @ np.diag(np.linspace(0.99, 1.01, S.shape[0]))
+    assert not _route_with(inv_sqrt=transposed_scale) <= 1e-4

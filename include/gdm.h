@@ -1,0 +1,168 @@
+/*
+ * gdm.h - C ABI of the GB300 density-matrix engine.
+ *
+ * The engine turns a Hamiltonian H and an overlap S (dense, real symmetric, n_basis x n_basis)
+ * into the zero-temperature density matrix P and the band energy Tr(P H).
+ *
+ * What is computed (paper: "ELSI - An Open Infrastructure for Electronic Structure Solvers",
+ * arXiv:1912.13403):
+ *   - the problem is the generalised eigenproblem H C = S C eps            (Sec. 1, Eq. evp)
+ *   - the result is p_ij = sum_l f_l c_il c_jl with f_l = 1 for the n_occ lowest eps and 0
+ *     otherwise (Sec. 1, Eq. density_matrix), so Tr(P S) = n_occ and E = Tr(P H)
+ *   - route: Loewdin-type orthogonalisation H~ = Z^T H Z with Z^T S Z = I (Sec. 2.2.2,
+ *     Eq. ntpoly_lowdin; Z from a coupled Newton-Schulz iteration for S^{-1/2} refined to
+ *     Z^T S Z = I), initial guess P_0 = (eps_max I - H~)/(eps_max - eps_min) with Gershgorin
+ *     bounds (Eq. ntpoly_scale_hamiltonian), 4th-order trace-resetting purification
+ *     P_{n+1} = f(P_n) (Eq. ntpoly_purification; Sec. 4, Table 1), back-transform
+ *     P = Z P~ Z^T (Sec. 4, the "repeated steps" of the NTPoly route).
+ *   - the handle life cycle follows the paper's API: init -> set_* -> solve -> reinit (new
+ *     geometry) -> finalize (Sec. 2.1; Sec. 2.7, Algorithms 1-2).
+ *
+ * Conventions for every call:
+ *   - Matrices are dense row-major float64 with leading dimension `ld` (elements, ld >= n).
+ *     H, S and P are symmetric, so row- and column-major are the same matrix.  Inputs are
+ *     symmetrised on ingest ((A + A^T)/2).
+ *   - `mem` says where a buffer lives: GDM_MEM_HOST (ordinary or pinned host memory) or
+ *     GDM_MEM_DEVICE (memory of the handle's device).  The caller owns every buffer passed in
+ *     or out; the library copies what it needs before returning and keeps no pointer.
+ *   - Errors are return codes only: no exceptions cross the ABI, nothing aborts, no kernel
+ *     traps.  gdm_last_error() gives a one-line message for the handle's last failure.
+ *   - Handles are not thread-safe: use one handle per host thread (or serialise calls).
+ */
+#ifndef GDM_H
+#define GDM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gdm_handle gdm_handle; /* opaque */
+
+typedef enum {
+  GDM_OK = 0,
+  GDM_ERR_ARG = 1,            /* invalid argument (sizes, pointers, n_occ outside 0 < n_occ < n) */
+  GDM_ERR_STATE = 2,          /* call out of order (e.g. solve before set_overlap) */
+  GDM_ERR_NOT_SPD = 3,        /* S is not positive definite (Newton-Schulz diverged) */
+  GDM_ERR_NONFINITE = 4,      /* NaN / Inf in an input or during the solve */
+  GDM_ERR_NO_GAP = 5,         /* purification cannot separate occupied / virtual states */
+  GDM_ERR_NOT_CONVERGED = 6,  /* iteration cap reached; outputs are still written */
+  GDM_ERR_OOM = 7,            /* device allocation failed */
+  GDM_ERR_BUDGET = 8,         /* request does not fit the configured memory budget */
+  GDM_ERR_TIMEOUT = 9,        /* a bounded wait ran out */
+  GDM_ERR_CUDA = 10           /* a CUDA call failed; see gdm_last_error */
+} gdm_status;
+
+typedef enum { GDM_MEM_HOST = 0, GDM_MEM_DEVICE = 1 } gdm_mem;
+
+/* GDM_PREC_MIXED: every product on the tensor cores as FP16 integer slices with exact
+ * (FP32-integer) accumulation per slice order, combined in FP64 (FP64-class results).
+ * GDM_PREC_FP64: every product in plain FP64 on the CUDA cores (the reference path). */
+typedef enum { GDM_PREC_FP64 = 0, GDM_PREC_MIXED = 1 } gdm_precision;
+
+/* Phases whose slice format can be tuned with gdm_set_slices. */
+typedef enum {
+  GDM_PHASE_NEWTON_SCHULZ = 0, /* coupled Newton-Schulz iterations for S^{-1/2} */
+  GDM_PHASE_REFINE = 1,        /* Z <- Z (I + delta)^{-1/2} refinement, delta = Z^T S Z - I */
+  GDM_PHASE_TRANSFORM = 2,     /* H~ = Z^T H Z and P = Z P~ Z^T */
+  GDM_PHASE_PURIFY = 3         /* TRS4 purification products */
+} gdm_phase;
+
+typedef struct {
+  int ns_iters;        /* Newton-Schulz iterations run in this call (0 when Z was reused) */
+  int refine_iters;    /* Z refinement steps run in this call */
+  int purif_iters;     /* TRS4 iterations */
+  int stop_reason;     /* 1 converged, 2 idempotency floor reached, 3 non-finite, 4 cap */
+  double idem_err;     /* Tr(P~ - P~^2) of the final orthogonal-basis density matrix */
+  double z_err;        /* ||Z^T S Z - I||_F after refinement */
+  double trace_err;    /* |Tr(P S) - n_occ| */
+  double energy;       /* Tr(P H) */
+  double eps_min, eps_max; /* Gershgorin bounds of H~ */
+  double ms_total;     /* device time of the solve (ms), CUDA events on the handle's stream */
+} gdm_info;
+
+/* Create a handle for n_basis x n_basis problems with n_occ occupied states (f_l in {0,1})
+ * on CUDA device `device`.  Allocates the device workspace (about 14 * 8 * n^2 bytes; 0.9 GB
+ * at n = 2048, 15 GB at n = 8192).  Requires 1 <= n_basis, 0 < n_occ < n_basis.  Errors:
+ * GDM_ERR_ARG, GDM_ERR_OOM, GDM_ERR_CUDA (no *h is created on error). */
+gdm_status gdm_init(gdm_handle** h, int64_t n_basis, int64_t n_occ, int device);
+
+/* Choose the product arithmetic (default GDM_PREC_MIXED).  Invalidates a cached Z. */
+gdm_status gdm_set_precision(gdm_handle* h, gdm_precision prec);
+
+/* Slice format of one phase in GDM_PREC_MIXED: nslice in 1..4 FP16 slices per operand, and
+ * slice pairs up to order max_order (0..3, <= 2*(nslice-1)).  Defaults: Newton-Schulz (2,1),
+ * refine (4,3), transform (4,3), purify (3,3). */
+gdm_status gdm_set_slices(gdm_handle* h, gdm_phase phase, int nslice, int max_order);
+
+/* Stopping tolerance of the purification: stop when |Tr(X - X^2)| <= idem_tol * n_occ
+ * (default 1e-13) or when that error stops falling; trace_tol is the |Tr(P S) - n_occ|
+ * above which the solve reports GDM_ERR_NOT_CONVERGED (default 1e-6; 0 disables). */
+gdm_status gdm_set_tolerance(gdm_handle* h, double idem_tol, double trace_tol);
+
+/* Iteration caps (defaults 100 and 200; 0 keeps the current value). */
+gdm_status gdm_set_max_iter(gdm_handle* h, int ns_max, int purif_max);
+
+/* Run all work of this handle on `stream` (a cudaStream_t of the handle's device; NULL = the
+ * handle's own stream).  The caller keeps ownership of the stream. */
+gdm_status gdm_set_stream(gdm_handle* h, void* stream);
+
+/* Copy S (n x n, leading dimension ld >= n) into the handle and symmetrise it.  Invalidates the
+ * cached Z (a new geometry).  Errors: GDM_ERR_ARG, GDM_ERR_NONFINITE, GDM_ERR_CUDA. */
+gdm_status gdm_set_overlap(gdm_handle* h, const double* S, int64_t ld, gdm_mem mem);
+
+/* Copy H into the handle and symmetrise it.  Errors as gdm_set_overlap. */
+gdm_status gdm_set_hamiltonian(gdm_handle* h, const double* H, int64_t ld, gdm_mem mem);
+
+/* Solve: write P (n x n, leading dimension ld) to `P` (host or device per `mem`), the band
+ * energy Tr(P H) to *energy (may be NULL) and details to *info (may be NULL).  Reuses the
+ * cached Z while S is unchanged.  Blocks until P has been written.  Errors: GDM_ERR_STATE
+ * (H or S not set), GDM_ERR_NOT_SPD, GDM_ERR_NONFINITE, GDM_ERR_NOT_CONVERGED (P still
+ * written), GDM_ERR_CUDA, GDM_ERR_TIMEOUT. */
+gdm_status gdm_solve_dm(gdm_handle* h, double* P, int64_t ld, gdm_mem mem, double* energy,
+                        gdm_info* info);
+
+/* New geometry (Sec. 2.7): drop S, H and the cached Z; keep sizes and settings. */
+gdm_status gdm_reinit(gdm_handle* h);
+
+/* Free everything the handle owns.  NULL is accepted. */
+gdm_status gdm_finalize(gdm_handle* h);
+
+/* Static strings; never NULL. */
+const char* gdm_status_string(gdm_status s);
+const char* gdm_last_error(const gdm_handle* h);
+
+/* ---------------------------------------------------------------------------------------
+ * Stateless operations on device buffers (for building blocks and step-level checks).
+ * All pointers are device pointers of the current CUDA device; `stream` is a cudaStream_t
+ * (NULL = default stream); scratch is allocated stream-ordered and freed before return.
+ * Every call synchronises `stream` before returning.
+ * --------------------------------------------------------------------------------------- */
+
+/* C = A * B for A (m x k, lda) and B given as Bt = B^T (n x k, ldb); C is m x n (ldc).
+ * nslice = 0: plain FP64 kernel; nslice 1..4: sliced FP16 tensor-core kernel with slice pairs
+ * up to order max_order.  symmetric != 0: the caller asserts C is symmetric (m == n); only
+ * tiles on/above the diagonal are computed and mirrored.  Errors: GDM_ERR_ARG, GDM_ERR_CUDA. */
+gdm_status gdm_op_product(const double* A, int64_t lda, const double* Bt, int64_t ldb, double* C,
+                          int64_t ldc, int64_t m, int64_t n, int64_t k, int nslice, int max_order,
+                          int symmetric, void* stream);
+
+/* Gershgorin bounds of the symmetric n x n matrix A: bounds_host[0] = min_i (a_ii - r_i),
+ * bounds_host[1] = max_i (a_ii + r_i), r_i = sum_{j != i} |a_ij| (host array of 2). */
+gdm_status gdm_op_gershgorin(const double* A, int64_t lda, int64_t n, double* bounds_host,
+                             void* stream);
+
+/* One TRS4 step in place on the symmetric n x n matrix X (ld), target trace n_occ:
+ * gamma = (n_occ - Tr F)/Tr G with F = X^2 (4X - 3X^2), G = X^2 (I - X)^2;
+ * X <- 2X - X^2 (gamma > 6), X^2 (gamma < 0), F + gamma G (otherwise).
+ * Products as in gdm_op_product (nslice = 0: FP64).  gamma_host / branch_host (0, 1, 2 for
+ * the three cases) may be NULL. */
+gdm_status gdm_op_trs4_step(double* X, int64_t ld, int64_t n, double n_occ, int nslice,
+                            int max_order, double* gamma_host, int* branch_host, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GDM_H */

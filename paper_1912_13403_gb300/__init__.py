@@ -1,0 +1,222 @@
+"""Python binding of the GB300 density-matrix engine (C ABI in include/gdm.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library
+`_build/libgdm.so` (built by `paper_1912_13403_gb300.build`).  Importing this package without
+the built library raises ImportError; there is no CPU fallback.
+
+Functions keep the C names (`gdm_init`, `gdm_solve_dm`, ...).  `Handle` and the `op_*`
+helpers accept numpy arrays (host memory) or CUDA torch tensors (device memory).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgdm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("CUDA library %s is not built; run `python -m paper_1912_13403_gb300.build` "
+                      "(or __graft_entry__.build())" % LIB_PATH)
+
+lib = ctypes.CDLL(LIB_PATH)
+
+GDM_OK, GDM_ERR_ARG, GDM_ERR_STATE, GDM_ERR_NOT_SPD, GDM_ERR_NONFINITE, GDM_ERR_NO_GAP, \
+    GDM_ERR_NOT_CONVERGED, GDM_ERR_OOM, GDM_ERR_BUDGET, GDM_ERR_TIMEOUT, GDM_ERR_CUDA = range(11)
+GDM_MEM_HOST, GDM_MEM_DEVICE = 0, 1
+GDM_PREC_FP64, GDM_PREC_MIXED = 0, 1
+GDM_PHASE_NEWTON_SCHULZ, GDM_PHASE_REFINE, GDM_PHASE_TRANSFORM, GDM_PHASE_PURIFY = range(4)
+
+
+class gdm_info(ctypes.Structure):
+    _fields_ = [("ns_iters", ctypes.c_int), ("refine_iters", ctypes.c_int),
+                ("purif_iters", ctypes.c_int), ("stop_reason", ctypes.c_int),
+                ("idem_err", ctypes.c_double), ("z_err", ctypes.c_double),
+                ("trace_err", ctypes.c_double), ("energy", ctypes.c_double),
+                ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double),
+                ("ms_total", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def _decl(name, res, args):
+    f = getattr(lib, name)
+    f.restype = res
+    f.argtypes = args
+    globals()[name] = f
+    return f
+
+
+_decl("gdm_init", _int, [ctypes.POINTER(_vp), _i64, _i64, _int])
+_decl("gdm_set_precision", _int, [_vp, _int])
+_decl("gdm_set_slices", _int, [_vp, _int, _int, _int])
+_decl("gdm_set_tolerance", _int, [_vp, _dbl, _dbl])
+_decl("gdm_set_max_iter", _int, [_vp, _int, _int])
+_decl("gdm_set_stream", _int, [_vp, _vp])
+_decl("gdm_set_overlap", _int, [_vp, _vp, _i64, _int])
+_decl("gdm_set_hamiltonian", _int, [_vp, _vp, _i64, _int])
+_decl("gdm_solve_dm", _int, [_vp, _vp, _i64, _int, _dp, ctypes.POINTER(gdm_info)])
+_decl("gdm_reinit", _int, [_vp])
+_decl("gdm_finalize", _int, [_vp])
+_decl("gdm_status_string", ctypes.c_char_p, [_int])
+_decl("gdm_last_error", ctypes.c_char_p, [_vp])
+_decl("gdm_op_product", _int, [_vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _int, _int,
+                               _int, _vp])
+_decl("gdm_op_gershgorin", _int, [_vp, _i64, _i64, _dp, _vp])
+_decl("gdm_op_trs4_step", _int, [_vp, _i64, _i64, _dbl, _int, _int, _dp,
+                                 ctypes.POINTER(_int), _vp])
+
+
+class GdmError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        name = gdm_status_string(status).decode()
+        super().__init__("%s%s" % (name, (": " + msg) if msg else ""))
+
+
+def status_name(st: int) -> str:
+    return gdm_status_string(st).decode()
+
+
+# ------------------------------------------------------------------------------------------
+# marshalling helpers
+# ------------------------------------------------------------------------------------------
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _buf(x):
+    """(pointer, leading dimension, mem kind) of a 2-D row-major float64 buffer."""
+    if _is_torch(x):
+        if x.dtype.itemsize != 8 or not x.is_floating_point():
+            raise TypeError("float64 tensor expected")
+        if x.dim() != 2 or x.stride(1) != 1:
+            raise ValueError("2-D row-major tensor expected")
+        return x.data_ptr(), x.stride(0), (GDM_MEM_DEVICE if x.is_cuda else GDM_MEM_HOST)
+    if not isinstance(x, np.ndarray) or x.dtype != np.float64 or x.ndim != 2 or \
+            x.strides[1] != 8:
+        raise TypeError("2-D row-major float64 numpy array expected")
+    return x.ctypes.data, x.strides[0] // 8, GDM_MEM_HOST
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Handle:
+    """One solver handle (gdm_init ... gdm_finalize)."""
+
+    def __init__(self, n_basis: int, n_occ: int, device: int = 0):
+        self._h = _vp()
+        st = gdm_init(ctypes.byref(self._h), int(n_basis), int(n_occ), int(device))
+        if st != GDM_OK:
+            raise GdmError(st, "gdm_init(n=%d, n_occ=%d)" % (n_basis, n_occ))
+        self.n, self.n_occ = int(n_basis), int(n_occ)
+
+    def _check(self, st, allow=()):
+        if st != GDM_OK and st not in allow:
+            raise GdmError(st, gdm_last_error(self._h).decode())
+        return st
+
+    def set_precision(self, prec):
+        return self._check(gdm_set_precision(self._h, prec))
+
+    def set_slices(self, phase, nslice, max_order):
+        return self._check(gdm_set_slices(self._h, phase, nslice, max_order))
+
+    def set_tolerance(self, idem_tol, trace_tol):
+        return self._check(gdm_set_tolerance(self._h, idem_tol, trace_tol))
+
+    def set_max_iter(self, ns_max, purif_max):
+        return self._check(gdm_set_max_iter(self._h, ns_max, purif_max))
+
+    def set_stream(self, stream):
+        return self._check(gdm_set_stream(self._h, _stream_ptr(stream)))
+
+    def set_overlap(self, S):
+        p, ld, mem = _buf(S)
+        return self._check(gdm_set_overlap(self._h, p, ld, mem))
+
+    def set_hamiltonian(self, H):
+        p, ld, mem = _buf(H)
+        return self._check(gdm_set_hamiltonian(self._h, p, ld, mem))
+
+    def solve(self, P=None, allow=(GDM_ERR_NOT_CONVERGED,)):
+        """Solve into P (numpy or torch float64 n x n; allocated on the host when None).
+        Returns (P, energy, info dict, status)."""
+        if P is None:
+            P = np.empty((self.n, self.n))
+        p, ld, mem = _buf(P)
+        e = ctypes.c_double(0.0)
+        info = gdm_info()
+        st = gdm_solve_dm(self._h, p, ld, mem, ctypes.byref(e), ctypes.byref(info))
+        self._check(st, allow)
+        return P, e.value, info.as_dict(), st
+
+    def reinit(self):
+        return self._check(gdm_reinit(self._h))
+
+    def close(self):
+        if self._h:
+            gdm_finalize(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def op_product(A, Bt, C, nslice=3, max_order=3, symmetric=False, stream=None):
+    """C = A @ Bt.T on the device (torch CUDA float64 tensors)."""
+    pa, lda, _ = _buf(A)
+    pb, ldb, _ = _buf(Bt)
+    pc, ldc, _ = _buf(C)
+    st = gdm_op_product(pa, lda, pb, ldb, pc, ldc, A.shape[0], Bt.shape[0], A.shape[1],
+                        nslice, max_order, int(bool(symmetric)), _stream_ptr(stream))
+    if st != GDM_OK:
+        raise GdmError(st, "gdm_op_product")
+    return C
+
+
+def op_gershgorin(A, stream=None):
+    pa, lda, _ = _buf(A)
+    out = (ctypes.c_double * 2)()
+    st = gdm_op_gershgorin(pa, lda, A.shape[0], out, _stream_ptr(stream))
+    if st != GDM_OK:
+        raise GdmError(st, "gdm_op_gershgorin")
+    return out[0], out[1]
+
+
+def op_trs4_step(X, n_occ, nslice=0, max_order=0, stream=None):
+    """One TRS4 step in place on the device tensor X; returns (gamma, branch)."""
+    px, ld, _ = _buf(X)
+    g = ctypes.c_double(0.0)
+    br = ctypes.c_int(-1)
+    st = gdm_op_trs4_step(px, ld, X.shape[0], float(n_occ), nslice, max_order, ctypes.byref(g),
+                          ctypes.byref(br), _stream_ptr(stream))
+    if st != GDM_OK:
+        raise GdmError(st, "gdm_op_trs4_step")
+    return g.value, br.value

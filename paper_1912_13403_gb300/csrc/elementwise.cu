@@ -1,0 +1,410 @@
+// Memory-bound kernels of the density-matrix route: forming + slicing, Gershgorin bounds,
+// the TRS4 trace reductions and controller, dot products, symmetrisation.
+//
+// All of them stream n x n FP64 matrices once (or twice for forming + slicing, the second
+// pass hitting L1/L2); rows map to blocks or warps so every global access is coalesced.
+#include <cmath>
+
+#include "common.cuh"
+#include "gdm_internal.h"
+
+namespace gdm {
+
+namespace {
+
+constexpr int kRowThreads = 256;
+constexpr int kRowsPerBlock = 8;  // one warp per row for the reductions
+
+// ------------------------------------------------------------------------------------------
+// Y = a X + b X2 + c I, optional FP64 output, optional FP16 integer slices with a power-of-two
+// row scale sigma_i >= ||y_i||_2 (so the slice-0 row norm is <= 2^11).  Rounding: nearest-even
+// at every slice (rint), each residual is exact in FP64.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRowThreads)
+    form_slice_kernel(const double* __restrict__ X, int64_t ldx, const double* __restrict__ X2,
+                      int64_t ldx2, int rows, int cols, const double* __restrict__ coef_dev,
+                      double ha, double hb, double hc, double* Y, int64_t ldy, __half* out,
+                      double* out_scale, int64_t out_ld, int64_t plane, int nslice,
+                      const int* skip) {
+  __shared__ double red[32];
+  if (skip != nullptr && *skip != 0) return;
+  const int row = blockIdx.x;
+  if (row >= rows) return;
+  double a = ha, b = hb, c = hc;
+  if (coef_dev != nullptr) {
+    a = coef_dev[0];
+    b = coef_dev[1];
+    c = coef_dev[2];
+  }
+  const double* xr = X + row * ldx;
+  const double* x2r = (X2 != nullptr) ? X2 + row * ldx2 : nullptr;
+  double* yr = (Y != nullptr) ? Y + row * ldy : nullptr;
+  double ss = 0.0;
+  for (int j = threadIdx.x; j < cols; j += blockDim.x) {
+    double y = a * xr[j];
+    if (x2r != nullptr) y += b * x2r[j];
+    if (j == row) y += c;
+    ss += y * y;
+    if (yr != nullptr) yr[j] = y;
+  }
+  if (out == nullptr || nslice <= 0) return;
+  ss = block_sum(ss, red);
+  const double nrm = sqrt(ss);
+  int e = 0;
+  double scale = 0.0, sigma = 1.0;
+  if (nrm > 0.0 && isfinite(nrm)) {
+    frexp(nrm, &e);               // nrm = m 2^e, m in [0.5, 1)
+    sigma = ldexp(1.0, e);        // sigma >= nrm
+    scale = ldexp(1.0, 11 - e);   // y * scale has row norm < 2^11
+  }
+  if (threadIdx.x == 0) out_scale[row] = sigma;
+  __half* orow = out + row * out_ld;
+  for (int j = threadIdx.x; j < cols; j += blockDim.x) {
+    double y;
+    if (yr != nullptr) {
+      y = yr[j];
+    } else {
+      y = a * xr[j];
+      if (x2r != nullptr) y += b * x2r[j];
+      if (j == row) y += c;
+    }
+    double x = y * scale;
+    for (int s = 0; s < nslice; ++s) {
+      const double m = rint(x);
+      orow[s * plane + j] = __float2half_rn(static_cast<float>(m));  // exact: |m| <= 2048
+      x = (x - m) * 2048.0;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Gershgorin: lo_i = a_ii - sum_{j != i} |a_ij|, hi_i = a_ii + sum_{j != i} |a_ij|
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRowsPerBlock * 32)
+    gershgorin_kernel(const double* __restrict__ A, int64_t lda, int n, double* partials) {
+  __shared__ double slo[kRowsPerBlock], shi[kRowsPerBlock];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * kRowsPerBlock + w;
+  double lo = INFINITY, hi = -INFINITY;
+  if (row < n) {
+    const double* ar = A + row * lda;
+    double r = 0.0;
+    for (int j = lane; j < n; j += 32)
+      if (j != row) r += fabs(ar[j]);
+    r = warp_sum(r);
+    const double d = ar[row];
+    lo = d - r;
+    hi = d + r;
+  }
+  if (lane == 0) {
+    slo[w] = lo;
+    shi[w] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double l = slo[0], h = shi[0];
+    for (int i = 1; i < kRowsPerBlock; ++i) {
+      l = fmin(l, slo[i]);
+      h = fmax(h, shi[i]);
+    }
+    partials[2 * blockIdx.x] = l;
+    partials[2 * blockIdx.x + 1] = h;
+  }
+}
+
+__global__ void minmax_reduce_kernel(const double* partials, int nblocks, double* out) {
+  __shared__ double sl[32], sh[32];
+  double l = INFINITY, h = -INFINITY;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+    l = fmin(l, partials[2 * i]);
+    h = fmax(h, partials[2 * i + 1]);
+  }
+  l = warp_min(l);
+  h = warp_max(h);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    sl[w] = l;
+    sh[w] = h;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 1; i < nw; ++i) {
+      l = fmin(l, sl[i]);
+      h = fmax(h, sh[i]);
+    }
+    l = fmin(l, sl[0]);
+    h = fmax(h, sh[0]);
+    out[0] = l;
+    out[1] = h;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// TRS4 traces, one warp per row
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRowsPerBlock * 32)
+    trs4_traces_kernel(const double* __restrict__ X, const double* __restrict__ X2, int64_t ld,
+                       int n, double* partials) {
+  __shared__ double s[kRowsPerBlock][kTraceTerms];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * kRowsPerBlock + w;
+  double t[kTraceTerms] = {0, 0, 0, 0, 0};
+  if (row < n) {
+    const double* xr = X + row * ld;
+    const double* yr = X2 + row * ld;
+    for (int j = lane; j < n; j += 32) {
+      const double x = xr[j], y = yr[j];
+      t[2] += y * x;
+      t[3] += y * y;
+      t[4] += x * x;
+    }
+    if (lane == 0) {
+      t[0] = xr[row];
+      t[1] = yr[row];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kTraceTerms; ++k) t[k] = warp_sum(t[k]);
+  if (lane == 0)
+    for (int k = 0; k < kTraceTerms; ++k) s[w][k] = t[k];
+  __syncthreads();
+  if (threadIdx.x < kTraceTerms) {
+    double acc = 0.0;
+    for (int i = 0; i < kRowsPerBlock; ++i) acc += s[i][threadIdx.x];
+    partials[blockIdx.x * kTraceTerms + threadIdx.x] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(kRowsPerBlock * 32)
+    dot_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ B,
+               int64_t ldb, int rows, int cols, int minus_identity, double* partials) {
+  __shared__ double s[kRowsPerBlock];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * kRowsPerBlock + w;
+  double acc = 0.0;
+  if (row < rows) {
+    const double* ar = A + row * lda;
+    const double* br = (B != nullptr) ? B + row * ldb : nullptr;
+    for (int j = lane; j < cols; j += 32) {
+      double a = ar[j];
+      if (minus_identity && j == row) a -= 1.0;
+      acc += (br != nullptr) ? a * br[j] : a * a;
+    }
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) s[w] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int i = 0; i < kRowsPerBlock; ++i) r += s[i];
+    partials[blockIdx.x] = r;
+  }
+}
+
+// Deterministic reduction of `nblocks` partial rows of `nterms` doubles (one block).
+__device__ void reduce_terms(const double* partials, int nblocks, int nterms, double* out,
+                             double* red) {
+  for (int k = 0; k < nterms; ++k) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += partials[i * nterms + k];
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) out[k] = acc;
+  }
+}
+
+__global__ void reduce_kernel(const double* partials, int nblocks, int nterms, double* out) {
+  __shared__ double red[32];
+  reduce_terms(partials, nblocks, nterms, out, red);
+}
+
+// TRS4 control: F(X) = X^2 (4X - 3X^2), G(X) = X^2 (I - X)^2, Tr F = 4 t3 - 3 t4,
+// Tr G = t2 - 2 t3 + t4, gamma = (N - Tr F) / Tr G; branches gamma > 6 -> 2X - X^2,
+// gamma < 0 -> X^2, else X^2 W + gamma X^2 with W = (4 - 2 gamma) X + (gamma - 3) X^2.
+__global__ void trs4_control_kernel(const double* partials, int nblocks, Trs4State* st,
+                                    double tol_idem) {
+  __shared__ double red[32];
+  __shared__ double t[kTraceTerms];
+  reduce_terms(partials, nblocks, kTraceTerms, t, red);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double N = st->n_occ;
+  for (int k = 0; k < kTraceTerms; ++k) st->t[k] = t[k];
+  const double trF = 4.0 * t[2] - 3.0 * t[3];
+  const double trG = t[1] - 2.0 * t[2] + t[3];
+  const double idem = t[0] - t[4];
+  st->trG = trG;
+  st->idem_prev = (st->iter == 0) ? INFINITY : st->idem;
+  st->idem = idem;
+  int stop = 0;
+  bool finite = true;
+  for (int k = 0; k < kTraceTerms; ++k) finite = finite && isfinite(t[k]);
+  if (!finite) {
+    stop = 3;
+  } else if (fabs(idem) <= tol_idem || trG <= 1e-15 * fmax(N, 1.0)) {
+    stop = 1;
+  } else if (fabs(idem) < 1e-4 * fmax(N, 1.0) && fabs(idem) > 0.25 * fabs(st->idem_prev)) {
+    stop = 2;  // idempotency error no longer falls: the arithmetic's floor is reached
+  }
+  st->stop = stop;
+  const double g = (trG != 0.0) ? (N - trF) / trG : INFINITY;
+  st->gamma = g;
+  int br;
+  if (g > 6.0) {
+    br = 0;
+    st->coefX[0] = 2.0;
+    st->coefX[1] = -1.0;
+    st->coefX[2] = 0.0;
+  } else if (g < 0.0) {
+    br = 1;
+    st->coefX[0] = 0.0;
+    st->coefX[1] = 1.0;
+    st->coefX[2] = 0.0;
+  } else {
+    br = 2;
+    st->coefW[0] = 4.0 - 2.0 * g;
+    st->coefW[1] = g - 3.0;
+    st->coefW[2] = 0.0;
+    st->gemm_coef[0] = 1.0;
+    st->gemm_coef[1] = g;
+  }
+  st->branch = br;
+  st->skip_gemm = (stop != 0 || br != 2) ? 1 : 0;
+  st->skip_form_x = (stop != 0 || br == 2) ? 1 : 0;
+  st->iter += 1;
+}
+
+__global__ void x0_coef_kernel(const double* bounds, double* coef) {
+  const double lo = bounds[0], hi = bounds[1];
+  const double w = hi - lo;
+  coef[0] = -1.0 / w;
+  coef[1] = 0.0;
+  coef[2] = hi / w;
+}
+
+__global__ void scale_coef_kernel(const double* bounds, int inv_sqrt, double* coef) {
+  const double c = bounds[1];
+  coef[0] = inv_sqrt ? 1.0 / sqrt(c) : 1.0 / c;
+  coef[1] = 0.0;
+  coef[2] = 0.0;
+}
+
+// A <- (A + A^T)/2 on 32 x 32 tile pairs (I <= J)
+__global__ void symmetrise_kernel(double* A, int64_t lda, int n) {
+  __shared__ double t1[32][33], t2[32][33];
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (I > J) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int i1 = I * 32 + r, j1 = J * 32 + tx;
+    t1[r][tx] = (i1 < n && j1 < n) ? A[i1 * lda + j1] : 0.0;
+    const int i2 = J * 32 + r, j2 = I * 32 + tx;
+    t2[r][tx] = (i2 < n && j2 < n) ? A[i2 * lda + j2] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i1 = I * 32 + r, j1 = J * 32 + tx;
+    const double v1 = 0.5 * (t1[r][tx] + t2[tx][r]);
+    const int i2 = J * 32 + r, j2 = I * 32 + tx;
+    const double v2 = 0.5 * (t2[r][tx] + t1[tx][r]);
+    if (i1 < n && j1 < n) A[i1 * lda + j1] = v1;
+    if (I != J && i2 < n && j2 < n) A[i2 * lda + j2] = v2;
+  }
+}
+
+__global__ void identity_kernel(double* A, int64_t lda, int n) {
+  const int row = blockIdx.x;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) A[row * lda + j] = (j == row) ? 1.0 : 0.0;
+}
+
+}  // namespace
+
+cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64_t ldx2,
+                           int rows, int cols, const double* coef_dev, double ha, double hb,
+                           double hc, double* Y, int64_t ldy, SliceBuf* out, int nslice,
+                           const int* skip, cudaStream_t stream) {
+  if (rows <= 0) return cudaSuccess;
+  __half* od = nullptr;
+  double* osc = nullptr;
+  int64_t old = 0, plane = 0;
+  if (out != nullptr && nslice > 0) {
+    if (nslice > 4 || out->ld < cols || out->rows_alloc < rows) return cudaErrorInvalidValue;
+    od = out->data;
+    osc = out->row_scale;
+    old = out->ld;
+    plane = static_cast<int64_t>(out->ld) * out->rows_alloc;
+    out->rows = rows;
+    out->cols = cols;
+    out->nslice_valid = nslice;
+  } else {
+    nslice = 0;
+  }
+  form_slice_kernel<<<rows, kRowThreads, 0, stream>>>(X, ldx, X2, ldx2, rows, cols, coef_dev, ha,
+                                                      hb, hc, Y, ldy, od, osc, old, plane,
+                                                      nslice, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t gershgorin(const double* A, int64_t lda, int n, double* partials, double* out_dev,
+                       cudaStream_t stream) {
+  const int nb = (n + kRowsPerBlock - 1) / kRowsPerBlock;
+  gershgorin_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, n, partials);
+  minmax_reduce_kernel<<<1, 256, 0, stream>>>(partials, nb, out_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t trs4_traces(const double* X, const double* X2, int64_t ld, int n, double* partials,
+                        int* nblocks, cudaStream_t stream) {
+  const int nb = (n + kRowsPerBlock - 1) / kRowsPerBlock;
+  trs4_traces_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(X, X2, ld, n, partials);
+  *nblocks = nb;
+  return cudaGetLastError();
+}
+
+cudaError_t dot_partials(const double* A, int64_t lda, const double* B, int64_t ldb, int rows,
+                         int cols, int minus_identity, double* partials, int* nblocks,
+                         cudaStream_t stream) {
+  const int nb = (rows + kRowsPerBlock - 1) / kRowsPerBlock;
+  dot_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, B, ldb, rows, cols, minus_identity,
+                                                    partials);
+  *nblocks = nb;
+  return cudaGetLastError();
+}
+
+cudaError_t reduce_partials(const double* partials, int nblocks, int nterms, double* out_dev,
+                            cudaStream_t stream) {
+  reduce_kernel<<<1, 256, 0, stream>>>(partials, nblocks, nterms, out_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t trs4_control(const double* partials, int nblocks, Trs4State* st, double tol_idem,
+                         cudaStream_t stream) {
+  trs4_control_kernel<<<1, 256, 0, stream>>>(partials, nblocks, st, tol_idem);
+  return cudaGetLastError();
+}
+
+cudaError_t x0_coefficients(const double* bounds_dev, double* coef_dev, cudaStream_t stream) {
+  x0_coef_kernel<<<1, 1, 0, stream>>>(bounds_dev, coef_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_coefficients(const double* bounds_dev, int inv_sqrt, double* coef_dev,
+                               cudaStream_t stream) {
+  scale_coef_kernel<<<1, 1, 0, stream>>>(bounds_dev, inv_sqrt, coef_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t symmetrise(double* A, int64_t lda, int n, cudaStream_t stream) {
+  const int t = (n + 31) / 32;
+  if (t == 0) return cudaSuccess;
+  symmetrise_kernel<<<dim3(t, t), dim3(32, 8), 0, stream>>>(A, lda, n);
+  return cudaGetLastError();
+}
+
+cudaError_t set_identity(double* A, int64_t lda, int n, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  identity_kernel<<<n, 256, 0, stream>>>(A, lda, n);
+  return cudaGetLastError();
+}
+
+}  // namespace gdm

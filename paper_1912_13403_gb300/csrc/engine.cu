@@ -1,0 +1,660 @@
+// Handle, solve plan and C ABI of the density-matrix engine (include/gdm.h).
+//
+// Solve plan for one (H, S) pair, all on the handle's stream:
+//   1. Z with Z^T S Z = I (cached per geometry, Sec. 2.7 "reinit"):
+//        coupled Newton-Schulz for S^{-1/2}: c = Gershgorin bound of S, Y_0 = S/c, Z_0 = I,
+//        M = Y_k Z_k,  Y_{k+1} = (3 Y_k - M Y_k)/2,  Z_{k+1} = (3 Z_k - M^T Z_k)/2
+//        (the same iteration as T = (3I - Z Y)/2, Y <- Y T, Z <- T Z, written so that every
+//        product has a symmetric right factor and the two updates are symmetric products);
+//        Z_0' = Z_k / sqrt(c); then Z <- Z (I - delta/2 + 3 delta^2/8), delta = Z^T S Z - I,
+//        which drives Z^T S Z to I without needing Z = S^{-1/2} exactly.
+//   2. H~ = Z^T H Z                                          (Sec. 2.2.2, Eq. ntpoly_lowdin)
+//   3. X_0 = (eps_max I - H~)/(eps_max - eps_min), Gershgorin eps  (Eq. ntpoly_scale_hamiltonian)
+//   4. TRS4 purification X <- f(X)                           (Eq. ntpoly_purification; Table 1)
+//   5. P = Z X Z^T, Tr(P S), Tr(P H)                          (Sec. 4, back-transform)
+// Products run through the sliced tensor-core kernel (mixed precision) or the FP64 kernel.
+#include <cmath>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+
+#include "../../include/gdm.h"
+#include "gdm_internal.h"
+
+using namespace gdm;
+
+namespace {
+
+enum FBuf { F_H, F_S, F_Z, F_ZT, F_X, F_X2, F_XN, F_T, F_U, F_V, F_COUNT };
+enum SBuf { SL_S, SL_Z, SL_ZT, SL_A, SL_B, SL_X, SL_X2, SL_W, SL_COUNT };
+constexpr int kSmall = 4096;  // doubles of small device scratch beyond the partials
+
+}  // namespace
+
+struct gdm_handle {
+  int device = 0;
+  int64_t n = 0, n_occ = 0;
+  int64_t ld = 0;         // leading dimension of every internal n x n buffer
+  int rows_alloc = 0;     // rows of slice buffers (multiple of 128)
+  cudaStream_t own_stream = nullptr, stream = nullptr;
+  gdm_precision prec = GDM_PREC_MIXED;
+  Precision phase[4] = {{2, 1}, {4, 3}, {4, 3}, {3, 3}};
+  double idem_tol = 1e-13, trace_tol = 1e-6;
+  int max_ns = 100, max_purif = 200, n_refine = 2;
+
+  void* pool = nullptr;
+  double* f[F_COUNT] = {};
+  SliceBuf sl[SL_COUNT];
+  double* partials = nullptr;  // >= 5 * ceil(n/8) doubles
+  double* small = nullptr;     // kSmall doubles: coefficients, bounds, reductions
+  Trs4State* st_dev = nullptr;
+  uint32_t* err_dev = nullptr;
+  double* host_buf = nullptr;  // pinned: kSmall doubles
+  Trs4State* st_host = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  bool have_H = false, have_S = false, z_valid = false;
+  double z_err = 0.0;
+  std::string last_error;
+};
+
+namespace {
+
+// small[] layout
+enum SmallSlot {
+  SM_BOUNDS_S = 0,   // 2
+  SM_BOUNDS_H = 2,   // 2
+  SM_COEF_A = 4,     // 3
+  SM_COEF_B = 8,     // 3
+  SM_COEF_X0 = 12,   // 3
+  SM_RED = 16,       // 8 reduction outputs
+};
+
+gdm_status set_err(gdm_handle* h, gdm_status st, const char* fmt, ...) {
+  if (h != nullptr) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    h->last_error = buf;
+  }
+  return st;
+}
+
+#define CK(expr)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return set_err(h, GDM_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));   \
+  } while (0)
+
+struct Op {
+  double* f;
+  SliceBuf* sl;
+};
+
+bool mixed(const gdm_handle* h) { return h->prec == GDM_PREC_MIXED; }
+
+// device address of a field of the device-resident controller state
+const double* st_field(const gdm_handle* h, size_t offset) {
+  return reinterpret_cast<const double*>(reinterpret_cast<const char*>(h->st_dev) + offset);
+}
+
+int slices_for(const gdm_handle* h, int ph) { return mixed(h) ? h->phase[ph].nslice : 0; }
+
+// C = alpha * A * Bt^T + beta * D + diag * I (sym: C symmetric, upper tiles + mirror)
+cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const double* D,
+                    double alpha, double beta, double diag, bool sym, int ph,
+                    const double* coef = nullptr) {
+  const int n = static_cast<int>(h->n);
+  if (mixed(h)) {
+    SlicedGemmArgs a;
+    a.mode = sym ? kGemmSym : 0;
+    a.C = C;
+    a.ldc = h->ld;
+    a.Ct = Ct;
+    a.ldct = h->ld;
+    a.D = D;
+    a.ldd = h->ld;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.diag = diag;
+    a.coef = coef;
+    a.err = h->err_dev;
+    return sliced_gemm(*A.sl, *Bt.sl, h->phase[ph], a, h->stream);
+  }
+  F64GemmArgs a;
+  a.M = n;
+  a.N = n;
+  a.K = n;
+  a.mode = sym ? kGemmSym : 0;
+  a.A = A.f;
+  a.lda = h->ld;
+  a.Bt = Bt.f;
+  a.ldb = h->ld;
+  a.C = C;
+  a.ldc = h->ld;
+  a.Ct = Ct;
+  a.ldct = h->ld;
+  a.D = D;
+  a.ldd = h->ld;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.diag = diag;
+  a.coef = coef;
+  return f64_gemm(a, h->stream);
+}
+
+// Slice `src` (FP64) into `dst` with `nslice` slices (no-op in FP64 mode).
+cudaError_t slice(gdm_handle* h, const double* src, SliceBuf* dst, int nslice) {
+  if (!mixed(h) || nslice <= 0) return cudaSuccess;
+  const int n = static_cast<int>(h->n);
+  return form_and_slice(src, h->ld, nullptr, 0, n, n, nullptr, 1.0, 0.0, 0.0, nullptr, 0, dst,
+                        nslice, nullptr, h->stream);
+}
+
+// Synchronous scalar read-back of small[SM_RED + k] for k < count.
+gdm_status read_small(gdm_handle* h, int offset, int count, double* out) {
+  CK(cudaMemcpyAsync(h->host_buf, h->small + offset, sizeof(double) * count,
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < count; ++i) out[i] = h->host_buf[i];
+  return GDM_OK;
+}
+
+// sum_ij (A - I)_ij^2 (minus_identity) or sum_ij A_ij B_ij into *out (synchronous)
+gdm_status dot(gdm_handle* h, const double* A, const double* B, int minus_identity,
+               double* out) {
+  const int n = static_cast<int>(h->n);
+  int nb = 0;
+  CK(dot_partials(A, h->ld, B, h->ld, n, n, minus_identity, h->partials, &nb, h->stream));
+  CK(reduce_partials(h->partials, nb, 1, h->small + SM_RED, h->stream));
+  return read_small(h, SM_RED, 1, out);
+}
+
+gdm_status check_device_error(gdm_handle* h) {
+  uint32_t e = 0;
+  CK(cudaMemcpyAsync(&e, h->err_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (e & DEV_ERR_WAIT_TIMEOUT)
+    return set_err(h, GDM_ERR_TIMEOUT, "a kernel wait ran out of time (device error 0x%x)", e);
+  if (e != 0) return set_err(h, GDM_ERR_CUDA, "device error word 0x%x", e);
+  return GDM_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// step 1: Z with Z^T S Z = I
+// ------------------------------------------------------------------------------------------
+gdm_status compute_z(gdm_handle* h, gdm_info* info) {
+  const int n = static_cast<int>(h->n);
+  const int64_t ld = h->ld;
+  cudaStream_t s = h->stream;
+  const int ns_sl = slices_for(h, GDM_PHASE_NEWTON_SCHULZ);
+  const int big_sl = mixed(h) ? 4 : 0;
+  double* S = h->f[F_S];
+  double* bounds = h->small + SM_BOUNDS_S;
+  double* coef_inv = h->small + SM_COEF_A;
+  double* coef_isqrt = h->small + SM_COEF_B;
+
+  CK(gershgorin(S, ld, n, h->partials, bounds, s));
+  CK(scale_coefficients(bounds, 0, coef_inv, s));
+  CK(scale_coefficients(bounds, 1, coef_isqrt, s));
+  double bnd[2];
+  gdm_status st = read_small(h, SM_BOUNDS_S, 2, bnd);
+  if (st != GDM_OK) return st;
+  if (!std::isfinite(bnd[0]) || !std::isfinite(bnd[1]))
+    return set_err(h, GDM_ERR_NONFINITE, "overlap matrix has non-finite entries");
+  if (bnd[1] <= 0.0) return set_err(h, GDM_ERR_NOT_SPD, "overlap Gershgorin bound <= 0");
+
+  double *Y = h->f[F_X], *Z = h->f[F_XN], *M = h->f[F_T], *Mt = h->f[F_U];
+  double *Yn = h->f[F_X2], *Zn = h->f[F_V];
+  SliceBuf *sY = &h->sl[SL_X], *sZ = &h->sl[SL_Z], *sM = &h->sl[SL_A], *sMt = &h->sl[SL_B];
+  CK(form_and_slice(S, ld, nullptr, 0, n, n, coef_inv, 0, 0, 0, Y, ld, mixed(h) ? sY : nullptr,
+                    ns_sl, nullptr, s));
+  CK(set_identity(Z, ld, n, s));
+  CK(slice(h, Z, sZ, ns_sl));
+
+  const double rn = std::sqrt(static_cast<double>(n));
+  double prev = INFINITY, res = INFINITY;
+  int it = 0;
+  bool converged = false;
+  for (it = 0; it < h->max_ns; ++it) {
+    CK(product(h, {Y, sY}, {Z, sZ}, M, Mt, nullptr, 1.0, 0.0, 0.0, false,
+               GDM_PHASE_NEWTON_SCHULZ));
+    double r2 = 0.0;
+    st = dot(h, M, nullptr, 1, &r2);
+    if (st != GDM_OK) return st;
+    res = std::sqrt(r2);
+    if (!std::isfinite(res) || res > 1e6 * rn)
+      return set_err(h, GDM_ERR_NOT_SPD,
+                     "Newton-Schulz for S^-1/2 diverged (residual %g): S not positive definite",
+                     res);
+    if (res <= 1e-13 * rn || (res < 1e-2 * rn && res > 0.5 * prev)) {
+      converged = true;
+      break;
+    }
+    prev = res;
+    CK(slice(h, M, sM, ns_sl));
+    CK(slice(h, Mt, sMt, ns_sl));
+    CK(product(h, {M, sM}, {Y, sY}, Yn, nullptr, Y, -0.5, 1.5, 0.0, true,
+               GDM_PHASE_NEWTON_SCHULZ));
+    CK(product(h, {Mt, sMt}, {Z, sZ}, Zn, nullptr, Z, -0.5, 1.5, 0.0, true,
+               GDM_PHASE_NEWTON_SCHULZ));
+    std::swap(Y, Yn);
+    std::swap(Z, Zn);
+    CK(slice(h, Y, sY, ns_sl));
+    CK(slice(h, Z, sZ, ns_sl));
+  }
+  if (info) info->ns_iters = it;
+  (void)converged;  // a capped run is still refined below; z_err reports the outcome
+
+  // Z_0 = Z_k / sqrt(c), symmetric: its transpose is itself
+  double* Zc = h->f[F_Z];
+  CK(form_and_slice(Z, ld, nullptr, 0, n, n, coef_isqrt, 0, 0, 0, Zc, ld,
+                    mixed(h) ? &h->sl[SL_Z] : nullptr, big_sl, nullptr, s));
+  CK(slice(h, S, &h->sl[SL_S], big_sl));
+  Op zc = {Zc, &h->sl[SL_Z]};
+  Op zct = zc;
+  const int nref = mixed(h) ? h->n_refine : 1;
+  double derr = 0.0;
+  for (int r = 0; r <= nref; ++r) {
+    double* T = h->f[F_T];
+    double* Dl = h->f[F_U];
+    double* F = h->f[F_V];
+    CK(product(h, zct, {S, &h->sl[SL_S]}, T, nullptr, nullptr, 1.0, 0.0, 0.0, false,
+               GDM_PHASE_REFINE));                                   // T = Z^T S
+    CK(slice(h, T, &h->sl[SL_A], big_sl));
+    CK(product(h, {T, &h->sl[SL_A]}, zct, Dl, nullptr, nullptr, 1.0, 0.0, -1.0, true,
+               GDM_PHASE_REFINE));                                   // delta = Z^T S Z - I
+    double d2 = 0.0;
+    st = dot(h, Dl, nullptr, 0, &d2);
+    if (st != GDM_OK) return st;
+    derr = std::sqrt(d2);
+    if (!std::isfinite(derr)) return set_err(h, GDM_ERR_NONFINITE, "non-finite Z^T S Z");
+    if (r == nref || derr == 0.0) break;
+    CK(slice(h, Dl, &h->sl[SL_B], big_sl));
+    CK(product(h, {Dl, &h->sl[SL_B]}, {Dl, &h->sl[SL_B]}, F, nullptr, Dl, 0.375, -0.5, 1.0, true,
+               GDM_PHASE_REFINE));                                   // F = I - d/2 + 3d^2/8
+    CK(slice(h, F, &h->sl[SL_A], big_sl));
+    double* Znew = h->f[F_X];
+    double* Zt_new = h->f[F_X2];
+    CK(product(h, zc, {F, &h->sl[SL_A]}, Znew, Zt_new, nullptr, 1.0, 0.0, 0.0, false,
+               GDM_PHASE_REFINE));                                   // Z <- Z F
+    std::swap(h->f[F_Z], h->f[F_X]);
+    std::swap(h->f[F_ZT], h->f[F_X2]);
+    CK(slice(h, h->f[F_Z], &h->sl[SL_Z], big_sl));
+    CK(slice(h, h->f[F_ZT], &h->sl[SL_ZT], big_sl));
+    zc = {h->f[F_Z], &h->sl[SL_Z]};
+    zct = {h->f[F_ZT], &h->sl[SL_ZT]};
+    if (info) info->refine_iters = r + 1;
+  }
+  if (zct.f == zc.f) {
+    // no refinement step ran: Z is symmetric, keep an explicit transpose for the later steps
+    CK(cudaMemcpyAsync(h->f[F_ZT], h->f[F_Z], sizeof(double) * ld * n, cudaMemcpyDeviceToDevice,
+                       s));
+    CK(slice(h, h->f[F_ZT], &h->sl[SL_ZT], big_sl));
+  }
+  h->z_err = derr;
+  h->z_valid = true;
+  return GDM_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// steps 2-5
+// ------------------------------------------------------------------------------------------
+gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
+  const int n = static_cast<int>(h->n);
+  const int64_t ld = h->ld;
+  cudaStream_t s = h->stream;
+  gdm_status st;
+  CK(cudaMemsetAsync(h->err_dev, 0, sizeof(uint32_t), s));
+  if (!h->z_valid) {
+    st = compute_z(h, info);
+    if (st != GDM_OK) return st;
+  }
+  if (info) info->z_err = h->z_err;
+  const int tr_sl = slices_for(h, GDM_PHASE_TRANSFORM);
+  const int pu_sl = slices_for(h, GDM_PHASE_PURIFY);
+  Op Z = {h->f[F_Z], &h->sl[SL_Z]}, Zt = {h->f[F_ZT], &h->sl[SL_ZT]};
+  double* H = h->f[F_H];
+
+  // H~ = Z^T H Z
+  CK(slice(h, H, &h->sl[SL_A], tr_sl));
+  CK(product(h, Zt, {H, &h->sl[SL_A]}, h->f[F_T], nullptr, nullptr, 1.0, 0.0, 0.0, false,
+             GDM_PHASE_TRANSFORM));
+  CK(slice(h, h->f[F_T], &h->sl[SL_B], tr_sl));
+  double* Ht = h->f[F_U];
+  CK(product(h, {h->f[F_T], &h->sl[SL_B]}, Zt, Ht, nullptr, nullptr, 1.0, 0.0, 0.0, true,
+             GDM_PHASE_TRANSFORM));
+
+  // bounds and X_0
+  CK(gershgorin(Ht, ld, n, h->partials, h->small + SM_BOUNDS_H, s));
+  CK(x0_coefficients(h->small + SM_BOUNDS_H, h->small + SM_COEF_X0, s));
+  double bh[2];
+  st = read_small(h, SM_BOUNDS_H, 2, bh);
+  if (st != GDM_OK) return st;
+  if (!std::isfinite(bh[0]) || !std::isfinite(bh[1]))
+    return set_err(h, GDM_ERR_NONFINITE, "non-finite orthogonalised Hamiltonian");
+  if (info) {
+    info->eps_min = bh[0];
+    info->eps_max = bh[1];
+  }
+  if (!(bh[1] > bh[0])) return set_err(h, GDM_ERR_NO_GAP, "degenerate spectrum bounds");
+  double* X = h->f[F_X];
+  double* X2 = h->f[F_X2];
+  double* Xn = h->f[F_XN];
+  CK(form_and_slice(Ht, ld, nullptr, 0, n, n, h->small + SM_COEF_X0, 0, 0, 0, X, ld,
+                    mixed(h) ? &h->sl[SL_X] : nullptr, pu_sl, nullptr, s));
+
+  // TRS4
+  Trs4State init;
+  memset(&init, 0, sizeof(init));
+  init.n_occ = static_cast<double>(h->n_occ);
+  init.idem = INFINITY;
+  CK(cudaMemcpyAsync(h->st_dev, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  const double tol_abs = h->idem_tol * static_cast<double>(h->n_occ);
+  int it = 0;
+  int stop = 4;
+  double* W = h->f[F_V];
+  for (it = 0; it < h->max_purif; ++it) {
+    CK(product(h, {X, &h->sl[SL_X]}, {X, &h->sl[SL_X]}, X2, nullptr, nullptr, 1.0, 0.0, 0.0, true,
+               GDM_PHASE_PURIFY));
+    int nb = 0;
+    CK(trs4_traces(X, X2, ld, n, h->partials, &nb, s));
+    CK(trs4_control(h->partials, nb, h->st_dev, tol_abs, s));
+    CK(cudaMemcpyAsync(h->st_host, h->st_dev, sizeof(Trs4State), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const Trs4State& t = *h->st_host;
+    if (t.stop != 0) {
+      stop = t.stop;
+      break;
+    }
+    if (t.branch == 2) {
+      CK(slice(h, X2, &h->sl[SL_X2], pu_sl));
+      CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefW)), 0, 0, 0, mixed(h) ? nullptr : W, ld,
+                        mixed(h) ? &h->sl[SL_W] : nullptr, pu_sl, nullptr, s));
+      CK(product(h, {X2, &h->sl[SL_X2]}, {W, &h->sl[SL_W]}, Xn, nullptr, X2, 1.0, 0.0, 0.0, true,
+                 GDM_PHASE_PURIFY, st_field(h, offsetof(Trs4State, gemm_coef))));
+      CK(slice(h, Xn, &h->sl[SL_X], pu_sl));
+    } else {
+      CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefX)), 0, 0, 0, Xn, ld,
+                        mixed(h) ? &h->sl[SL_X] : nullptr, pu_sl, nullptr, s));
+    }
+    std::swap(X, Xn);
+  }
+  h->f[F_X] = X;
+  h->f[F_XN] = Xn;
+  if (info) {
+    info->purif_iters = it;
+    info->stop_reason = stop;
+    info->idem_err = h->st_host->idem;
+  }
+  if (stop == 3) return set_err(h, GDM_ERR_NONFINITE, "non-finite traces during purification");
+
+  // P = Z X Z^T  (X slices are current)
+  CK(product(h, Z, {X, &h->sl[SL_X]}, h->f[F_T], nullptr, nullptr, 1.0, 0.0, 0.0, false,
+             GDM_PHASE_TRANSFORM));
+  CK(slice(h, h->f[F_T], &h->sl[SL_A], tr_sl));
+  double* P = h->f[F_XN];
+  CK(product(h, {h->f[F_T], &h->sl[SL_A]}, Z, P, nullptr, nullptr, 1.0, 0.0, 0.0, true,
+             GDM_PHASE_TRANSFORM));
+  double trps = 0.0, e = 0.0;
+  st = dot(h, P, h->f[F_S], 0, &trps);
+  if (st != GDM_OK) return st;
+  st = dot(h, P, H, 0, &e);
+  if (st != GDM_OK) return st;
+  st = check_device_error(h);
+  if (st != GDM_OK) return st;
+  if (info) {
+    info->trace_err = std::fabs(trps - static_cast<double>(h->n_occ));
+    info->energy = e;
+  }
+  if (energy_out) *energy_out = e;
+  if (!std::isfinite(e) || !std::isfinite(trps))
+    return set_err(h, GDM_ERR_NONFINITE, "non-finite outputs");
+  if (stop == 4) return set_err(h, GDM_ERR_NOT_CONVERGED, "purification reached the iteration cap");
+  if (h->trace_tol > 0 && std::fabs(trps - static_cast<double>(h->n_occ)) > h->trace_tol)
+    return set_err(h, GDM_ERR_NOT_CONVERGED, "|Tr(PS) - N| = %g above tolerance",
+                   std::fabs(trps - static_cast<double>(h->n_occ)));
+  return GDM_OK;
+}
+
+gdm_status ingest(gdm_handle* h, const double* src, int64_t ld_src, gdm_mem mem, double* dst) {
+  if (src == nullptr) return set_err(h, GDM_ERR_ARG, "null matrix pointer");
+  if (ld_src < h->n) return set_err(h, GDM_ERR_ARG, "leading dimension %lld < n",
+                                     static_cast<long long>(ld_src));
+  if (mem != GDM_MEM_HOST && mem != GDM_MEM_DEVICE) return set_err(h, GDM_ERR_ARG, "bad mem kind");
+  CK(cudaSetDevice(h->device));
+  const size_t w = sizeof(double) * static_cast<size_t>(h->n);
+  CK(cudaMemcpy2DAsync(dst, sizeof(double) * h->ld, src, sizeof(double) * ld_src, w,
+                       static_cast<size_t>(h->n),
+                       mem == GDM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       h->stream));
+  CK(symmetrise(dst, h->ld, static_cast<int>(h->n), h->stream));
+  double s2 = 0.0;
+  gdm_status st = dot(h, dst, nullptr, 0, &s2);
+  if (st != GDM_OK) return st;
+  if (!std::isfinite(s2)) return set_err(h, GDM_ERR_NONFINITE, "input matrix has NaN/Inf");
+  return GDM_OK;
+}
+
+void free_all(gdm_handle* h) {
+  if (h->pool) cudaFree(h->pool);
+  if (h->host_buf) cudaFreeHost(h->host_buf);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  h->pool = nullptr;
+}
+
+}  // namespace
+
+// ==========================================================================================
+// C ABI
+// ==========================================================================================
+extern "C" {
+
+const char* gdm_status_string(gdm_status s) {
+  switch (s) {
+    case GDM_OK: return "GDM_OK";
+    case GDM_ERR_ARG: return "GDM_ERR_ARG";
+    case GDM_ERR_STATE: return "GDM_ERR_STATE";
+    case GDM_ERR_NOT_SPD: return "GDM_ERR_NOT_SPD";
+    case GDM_ERR_NONFINITE: return "GDM_ERR_NONFINITE";
+    case GDM_ERR_NO_GAP: return "GDM_ERR_NO_GAP";
+    case GDM_ERR_NOT_CONVERGED: return "GDM_ERR_NOT_CONVERGED";
+    case GDM_ERR_OOM: return "GDM_ERR_OOM";
+    case GDM_ERR_BUDGET: return "GDM_ERR_BUDGET";
+    case GDM_ERR_TIMEOUT: return "GDM_ERR_TIMEOUT";
+    case GDM_ERR_CUDA: return "GDM_ERR_CUDA";
+  }
+  return "GDM_UNKNOWN_STATUS";
+}
+
+const char* gdm_last_error(const gdm_handle* h) {
+  if (h == nullptr) return "null handle";
+  return h->last_error.c_str();
+}
+
+gdm_status gdm_init(gdm_handle** out, int64_t n_basis, int64_t n_occ, int device) {
+  if (out == nullptr) return GDM_ERR_ARG;
+  *out = nullptr;
+  if (n_basis < 1 || n_basis > (1 << 16) || n_occ <= 0 || n_occ >= n_basis) return GDM_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return GDM_ERR_ARG;
+  gdm_handle* h = new gdm_handle();
+  h->device = device;
+  h->n = n_basis;
+  h->n_occ = n_occ;
+  h->ld = (n_basis + 63) / 64 * 64;
+  h->rows_alloc = static_cast<int>((n_basis + 127) / 128 * 128);
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete h;
+    return GDM_ERR_CUDA;
+  }
+  const size_t fbytes = sizeof(double) * static_cast<size_t>(h->ld) * static_cast<size_t>(n_basis);
+  const size_t sdata = sizeof(__half) * 4 * static_cast<size_t>(h->ld) * h->rows_alloc;
+  const size_t sscale = sizeof(double) * h->rows_alloc;
+  const size_t nb = (n_basis + 7) / 8;
+  const size_t pbytes = sizeof(double) * (kTraceTerms * nb + 64);
+  const size_t small_bytes = sizeof(double) * kSmall;
+  auto up = [](size_t x) { return (x + 1023) / 1024 * 1024; };
+  size_t total = F_COUNT * up(fbytes) + SL_COUNT * (up(sdata) + up(sscale)) + up(pbytes) +
+                 up(small_bytes) + up(sizeof(Trs4State)) + up(sizeof(uint32_t));
+  if (cudaMalloc(&h->pool, total) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return GDM_ERR_OOM;
+  }
+  uint8_t* p = static_cast<uint8_t*>(h->pool);
+  for (int i = 0; i < F_COUNT; ++i) {
+    h->f[i] = reinterpret_cast<double*>(p);
+    p += up(fbytes);
+  }
+  for (int i = 0; i < SL_COUNT; ++i) {
+    h->sl[i].data = reinterpret_cast<__half*>(p);
+    p += up(sdata);
+    h->sl[i].row_scale = reinterpret_cast<double*>(p);
+    p += up(sscale);
+    h->sl[i].ld = static_cast<int>(h->ld);
+    h->sl[i].rows_alloc = h->rows_alloc;
+    h->sl[i].rows = static_cast<int>(n_basis);
+    h->sl[i].cols = static_cast<int>(n_basis);
+  }
+  h->partials = reinterpret_cast<double*>(p);
+  p += up(pbytes);
+  h->small = reinterpret_cast<double*>(p);
+  p += up(small_bytes);
+  h->st_dev = reinterpret_cast<Trs4State*>(p);
+  p += up(sizeof(Trs4State));
+  h->err_dev = reinterpret_cast<uint32_t*>(p);
+  if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost(&h->host_buf, sizeof(double) * kSmall) != cudaSuccess ||
+      cudaMallocHost(&h->st_host, sizeof(Trs4State)) != cudaSuccess ||
+      cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    free_all(h);
+    delete h;
+    return GDM_ERR_CUDA;
+  }
+  h->stream = h->own_stream;
+  if (cudaMemsetAsync(h->pool, 0, total, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return GDM_ERR_CUDA;
+  }
+  *out = h;
+  return GDM_OK;
+}
+
+gdm_status gdm_set_precision(gdm_handle* h, gdm_precision prec) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  if (prec != GDM_PREC_FP64 && prec != GDM_PREC_MIXED)
+    return set_err(h, GDM_ERR_ARG, "unknown precision %d", static_cast<int>(prec));
+  if (prec != h->prec) h->z_valid = false;
+  h->prec = prec;
+  return GDM_OK;
+}
+
+gdm_status gdm_set_slices(gdm_handle* h, gdm_phase phase, int nslice, int max_order) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  if (phase < GDM_PHASE_NEWTON_SCHULZ || phase > GDM_PHASE_PURIFY)
+    return set_err(h, GDM_ERR_ARG, "unknown phase %d", static_cast<int>(phase));
+  if (nslice < 1 || nslice > 4 || max_order < 0 || max_order > 3 || max_order > 2 * (nslice - 1))
+    return set_err(h, GDM_ERR_ARG, "invalid slice format (%d, %d)", nslice, max_order);
+  h->phase[phase] = {nslice, max_order};
+  if (phase == GDM_PHASE_NEWTON_SCHULZ || phase == GDM_PHASE_REFINE) h->z_valid = false;
+  return GDM_OK;
+}
+
+gdm_status gdm_set_tolerance(gdm_handle* h, double idem_tol, double trace_tol) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  if (!(idem_tol >= 0.0) || !(trace_tol >= 0.0))
+    return set_err(h, GDM_ERR_ARG, "tolerances must be >= 0");
+  h->idem_tol = idem_tol;
+  h->trace_tol = trace_tol;
+  return GDM_OK;
+}
+
+gdm_status gdm_set_max_iter(gdm_handle* h, int ns_max, int purif_max) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  if (ns_max < 0 || purif_max < 0) return set_err(h, GDM_ERR_ARG, "negative iteration cap");
+  if (ns_max > 0) h->max_ns = ns_max;
+  if (purif_max > 0) h->max_purif = purif_max;
+  return GDM_OK;
+}
+
+gdm_status gdm_set_stream(gdm_handle* h, void* stream) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  h->stream = (stream != nullptr) ? static_cast<cudaStream_t>(stream) : h->own_stream;
+  return GDM_OK;
+}
+
+gdm_status gdm_set_overlap(gdm_handle* h, const double* S, int64_t ld, gdm_mem mem) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  h->have_S = false;
+  h->z_valid = false;
+  gdm_status st = ingest(h, S, ld, mem, h->f[F_S]);
+  if (st == GDM_OK) h->have_S = true;
+  return st;
+}
+
+gdm_status gdm_set_hamiltonian(gdm_handle* h, const double* H, int64_t ld, gdm_mem mem) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  h->have_H = false;
+  gdm_status st = ingest(h, H, ld, mem, h->f[F_H]);
+  if (st == GDM_OK) h->have_H = true;
+  return st;
+}
+
+gdm_status gdm_solve_dm(gdm_handle* h, double* P, int64_t ld, gdm_mem mem, double* energy,
+                        gdm_info* info) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  if (!h->have_H || !h->have_S)
+    return set_err(h, GDM_ERR_STATE, "set the Hamiltonian and the overlap before solving");
+  if (P != nullptr && ld < h->n) return set_err(h, GDM_ERR_ARG, "leading dimension < n");
+  if (mem != GDM_MEM_HOST && mem != GDM_MEM_DEVICE) return set_err(h, GDM_ERR_ARG, "bad mem kind");
+  CK(cudaSetDevice(h->device));
+  gdm_info local;
+  memset(&local, 0, sizeof(local));
+  CK(cudaEventRecord(h->ev0, h->stream));
+  gdm_status st = solve_core(h, &local, energy);
+  CK(cudaEventRecord(h->ev1, h->stream));
+  if (P != nullptr && (st == GDM_OK || st == GDM_ERR_NOT_CONVERGED)) {
+    CK(cudaMemcpy2DAsync(P, sizeof(double) * ld, h->f[F_XN], sizeof(double) * h->ld,
+                         sizeof(double) * h->n, static_cast<size_t>(h->n),
+                         mem == GDM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                         h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) local.ms_total = ms;
+  if (info) *info = local;
+  return st;
+}
+
+gdm_status gdm_reinit(gdm_handle* h) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  h->have_H = false;
+  h->have_S = false;
+  h->z_valid = false;
+  return GDM_OK;
+}
+
+gdm_status gdm_finalize(gdm_handle* h) {
+  if (h == nullptr) return GDM_OK;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+  return GDM_OK;
+}
+
+}  // extern "C"

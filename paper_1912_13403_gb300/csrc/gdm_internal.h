@@ -1,0 +1,146 @@
+// Internal declarations shared by the .cu files of the density-matrix engine.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gdm {
+
+constexpr int kMaxPairs = 16;
+
+// Error word written by kernels (never a trap): bit flags, OR-ed atomically.
+enum DeviceError : uint32_t {
+  DEV_ERR_WAIT_TIMEOUT = 1u << 0,   // an mbarrier wait ran out of its time limit
+  DEV_ERR_BAD_ARG = 1u << 1,        // a kernel saw an argument it cannot handle
+  DEV_ERR_NONFINITE = 1u << 2,      // a NaN / Inf reached a reduction
+};
+constexpr int kGemmSym = 1;  // compute tiles on/above the diagonal, mirror the rest
+
+// A matrix held as FP16 integer slices plus power-of-two row scales (see gemm_sliced.cu):
+// row i = row_scale[i] * 2^-11 * sum_s slice_s[i, :] * 2^(-11 s).
+struct SliceBuf {
+  __half* data = nullptr;        // [4][rows_alloc][ld]
+  double* row_scale = nullptr;   // [rows_alloc]
+  int rows = 0, cols = 0;        // logical shape
+  int ld = 0;                    // elements per row in memory (multiple of 64)
+  int rows_alloc = 0;
+  int nslice_valid = 0;          // slices written by the last slicing pass
+};
+
+// Slice count and highest slice-pair order used by a product.
+struct Precision {
+  int nslice = 3;
+  int max_order = 3;
+};
+
+struct SlicedGemmArgs {
+  int M = 0, N = 0, K = 0;
+  int mode = 0;                       // kGemmSym
+  int num_pairs = 0, nacc = 0, tmem_cols = 0;
+  int8_t pair_s[kMaxPairs] = {}, pair_t[kMaxPairs] = {}, pair_o[kMaxPairs] = {};
+  const double* row_scale_a = nullptr;
+  const double* row_scale_b = nullptr;
+  double* C = nullptr;
+  int64_t ldc = 0;
+  double* Ct = nullptr;               // optional: also write C^T
+  int64_t ldct = 0;
+  const double* D = nullptr;          // optional addend, read as D^T (pass symmetric D only)
+  int64_t ldd = 0;
+  double alpha = 1.0, beta = 0.0;
+  double diag = 0.0;                  // added to the diagonal of C
+  const double* coef = nullptr;       // optional device {alpha, beta}
+  const int* skip = nullptr;          // optional device flag: non-zero -> no-op launch
+  uint32_t* err = nullptr;
+  int tiles_n = 0;
+};
+
+int build_pairs(int nslice, int max_order, SlicedGemmArgs* a);
+cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& Bt, const Precision& prec,
+                        SlicedGemmArgs args, cudaStream_t stream);
+
+// FP64 product C = alpha * A * Bt^T + beta * D (+ mirror / transposed copy as above).
+struct F64GemmArgs {
+  int M = 0, N = 0, K = 0;
+  int mode = 0;
+  const double* A = nullptr;
+  int64_t lda = 0;
+  const double* Bt = nullptr;
+  int64_t ldb = 0;
+  double* C = nullptr;
+  int64_t ldc = 0;
+  double* Ct = nullptr;
+  int64_t ldct = 0;
+  const double* D = nullptr;
+  int64_t ldd = 0;
+  double alpha = 1.0, beta = 0.0;
+  double diag = 0.0;
+  const double* coef = nullptr;
+  const int* skip = nullptr;
+};
+cudaError_t f64_gemm(const F64GemmArgs& a, cudaStream_t stream);
+
+// ---- elementwise / reduction kernels (elementwise.cu) --------------------------------------
+// Y = a*X + b*X2 + c*I with (a, b, c) from `coef_dev` (3 doubles) when non-null, else
+// (ha, hb, hc).  X2 may be null (then b is ignored).  Writes Y (FP64) when Y != null, and the
+// row slices of Y into `out` when out != null and nslice > 0.
+cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64_t ldx2,
+                           int rows, int cols, const double* coef_dev, double ha, double hb,
+                           double hc, double* Y, int64_t ldy, SliceBuf* out, int nslice,
+                           const int* skip, cudaStream_t stream);
+
+// Gershgorin bounds of a symmetric n x n matrix: writes {min_i(a_ii - r_i), max_i(a_ii + r_i)}
+// into out_dev[0..1].  `partials` holds >= 2 * ceil(n / 8) doubles.
+cudaError_t gershgorin(const double* A, int64_t lda, int n, double* partials, double* out_dev,
+                       cudaStream_t stream);
+
+// Per-block partial sums over rows of: Tr X, Tr X2, <X2, X>, ||X2||^2, ||X||^2
+// (partials: kTraceTerms doubles per block, `nblocks` returned through *nblocks).
+constexpr int kTraceTerms = 5;
+cudaError_t trs4_traces(const double* X, const double* X2, int64_t ld, int n, double* partials,
+                        int* nblocks, cudaStream_t stream);
+
+// Deterministic sum of partial dot products: out[0] = sum_ij A_ij B_ij (B null -> A_ij^2),
+// with an optional -1 on the diagonal of A first when `minus_identity` (||A - I||^2).
+cudaError_t dot_partials(const double* A, int64_t lda, const double* B, int64_t ldb, int rows,
+                         int cols, int minus_identity, double* partials, int* nblocks,
+                         cudaStream_t stream);
+cudaError_t reduce_partials(const double* partials, int nblocks, int nterms, double* out_dev,
+                            cudaStream_t stream);
+
+// TRS4 controller state (device, one per solve).
+struct Trs4State {
+  double n_occ;
+  double t[kTraceTerms];  // reduced traces of this iteration
+  double gamma;
+  double idem;            // Tr(X - X^2) = t1 - ||X||^2
+  double idem_prev;
+  double trG;
+  double coefW[3];        // W = a X + b X2 (+ c I)
+  double coefX[3];        // X_next = a X + b X2 for the branches without a product
+  double gemm_coef[2];    // X_next = alpha * X2 W + beta * X2
+  int branch;             // 0: 2X - X2, 1: X2, 2: F + gamma G
+  int skip_gemm;          // 1 unless branch 2
+  int skip_form_x;        // 1 when branch 2
+  int stop;               // 1: converged (X is final), 2: stalled, 3: non-finite
+  int iter;
+  int stall;
+};
+cudaError_t trs4_control(const double* partials, int nblocks, Trs4State* st, double tol_idem,
+                         cudaStream_t stream);
+
+// Set the bounds-dependent coefficients of the initial guess
+// X0 = (eps_max I - H~)/(eps_max - eps_min): coef = {-1/(hi-lo), 0, hi/(hi-lo)}.
+cudaError_t x0_coefficients(const double* bounds_dev, double* coef_dev, cudaStream_t stream);
+// coef = {s, 0, 0} with s = 1 / bound[1] (Y_0 = S / c) or s = 1 / sqrt(bound[1]).
+cudaError_t scale_coefficients(const double* bounds_dev, int inv_sqrt, double* coef_dev,
+                               cudaStream_t stream);
+
+// Symmetrise in place: A <- (A + A^T) / 2.
+cudaError_t symmetrise(double* A, int64_t lda, int n, cudaStream_t stream);
+
+// Copy rows x cols into a dense-ld destination (device-to-device, strided).
+cudaError_t set_identity(double* A, int64_t lda, int n, cudaStream_t stream);
+
+}  // namespace gdm

@@ -1,0 +1,343 @@
+// Sliced-FP16 tensor-core product C = alpha * A * B + beta * D on sm_103a (tcgen05 + TMEM + TMA).
+//
+// Every matrix product of the density-matrix route (the Loewdin transform H~ = S^{-1/2} H
+// S^{-1/2}, Sec. 2.2.2 Eq. ntpoly_lowdin; the purification steps P_{n+1} = f(P_n), Eq.
+// ntpoly_purification; the back-transform) goes through this kernel.
+//
+// Number format.  Each operand row i is stored as up to four FP16 "slices" holding integers:
+//     a_ik = sigma_i * 2^-11 * sum_s m_s[i,k] * 2^(-11 s),   |m_s| <= 2048,
+// where sigma_i is a power of two >= ||a_i||_2, so that ||m_0[i,:]||_2 <= 2^11 (+ rounding).
+// The product of two slices is accumulated by the tensor core in FP32.  Slice pairs of the same
+// order o = s + t share one TMEM accumulator; order 0 stays below 2^23 in magnitude for every
+// partial sum (Cauchy-Schwarz on the row norms), so it is exact; the higher orders are integers
+// too and are exact unless their partial sums pass 2^24, where they round at a relative weight
+// of 2^-35 or less.  The epilogue combines
+//     C_ij = alpha * sigma_i sigma_j 2^-22 * sum_o 2^(-11 o) acc_o[i,j] + beta * D_ij
+// in FP64.  The operand B is given as the row slices of B^T (for the symmetric right operands
+// of this route that is B itself).
+//
+// Kernel shape: one CTA per 128x128 output tile, 6 warps.  Warp 0: TMA producer (a 3-D box
+// loads all slices of a 128 x BK panel at once).  Warp 1: TMEM allocator and the single MMA
+// issuing thread.  Warps 2-5: epilogue (TMEM lanes 32*(warp%4) ...).  Symmetric mode computes
+// only tiles on or above the diagonal and writes the mirror image.
+#include <cstdio>
+#include <mutex>
+
+#include "common.cuh"
+#include "gdm_internal.h"
+
+namespace gdm {
+
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBN = 128;
+constexpr int kThreads = 192;
+
+template <int NSLICE, int BK, int STAGES>
+struct GemmCfg {
+  static constexpr uint32_t kTileBytes = kBM * BK * 2;                // one slice panel
+  static constexpr uint32_t kStageBytes = 2u * NSLICE * kTileBytes;   // A and B panels
+  static constexpr uint32_t kSmemBytes = STAGES * kStageBytes + 1024;  // + alignment slack
+  static constexpr uint32_t kSwizzleBytes = BK * 2;                   // 128 or 64
+  static_assert(BK == 64 || BK == 32, "BK must be 64 (128B swizzle) or 32 (64B swizzle)");
+  static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+};
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, int bk) {
+  // K-major, swizzle width = one row of the panel (bk * 2 bytes), 8-row groups contiguous.
+  const uint32_t sbo = 8u * bk * 2u;
+  const uint64_t layout = (bk == 64) ? 2ull : 4ull;  // SWIZZLE_128B : SWIZZLE_64B
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>(1u) << 16;
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+  d |= static_cast<uint64_t>(1u) << 46;
+  d |= layout << 61;
+  return d;
+}
+
+// Upper-triangle tile index -> (ti, tj) with ti <= tj, row-major over the triangle.
+__device__ __forceinline__ void upper_tile(int idx, int nt, int& ti, int& tj) {
+  int i = 0;
+  int row_len = nt;
+  while (idx >= row_len) {
+    idx -= row_len;
+    ++i;
+    --row_len;
+  }
+  ti = i;
+  tj = i + idx;
+}
+
+template <int NSLICE, int BK, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    sliced_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                       const __grid_constant__ CUtensorMap tmB, const SlicedGemmArgs args) {
+  using Cfg = GemmCfg<NSLICE, BK, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t accum_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int abort_flag;
+
+  if (args.skip != nullptr && *args.skip != 0) return;  // uniform: same word for all threads
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+
+  const bool sym = (args.mode & kGemmSym) != 0;
+  int ti, tj;
+  if (sym) {
+    upper_tile(blockIdx.x, args.tiles_n, ti, tj);
+  } else {
+    ti = blockIdx.x / args.tiles_n;
+    tj = blockIdx.x % args.tiles_n;
+  }
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t ncols = static_cast<uint32_t>(args.tmem_cols);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&accum_bar, 1);
+    abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base_sh, ncols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base_sh;
+  const int nk = (args.K + BK - 1) / BK;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      tma_prefetch_desc(&tmA);
+      tma_prefetch_desc(&tmB);
+      int issued = 0;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1u;
+        if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1u, args.err, &abort_flag)) break;
+        mbar_arrive_expect_tx(&full_bar[s], Cfg::kStageBytes);
+        uint8_t* st = smem + s * Cfg::kStageBytes;
+        tma_load_3d(st, &tmA, &full_bar[s], kb * BK, ti * kBM, 0);
+        tma_load_3d(st + NSLICE * Cfg::kTileBytes, &tmB, &full_bar[s], kb * BK, tj * kBN, 0);
+        ++issued;
+      }
+      if (abort_flag) {
+        // let copies already in flight land before the CTA can exit
+        for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+          mbar_wait_bounded(&full_bar[kb % STAGES], (kb / STAGES) & 1u, nullptr, nullptr,
+                            100000000ull);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer (one thread) ----------------
+      constexpr uint32_t idesc = idesc_f16_f32(kBM, kBN);
+      uint32_t started = 0;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1u;
+        if (!mbar_wait_bounded(&full_bar[s], ph, args.err, &abort_flag)) break;
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(smem + s * Cfg::kStageBytes);
+        const uint32_t b0 = a0 + NSLICE * Cfg::kTileBytes;
+        for (int p = 0; p < args.num_pairs; ++p) {
+          const int sa = args.pair_s[p], sb = args.pair_t[p], o = args.pair_o[p];
+          const uint32_t d = tbase + static_cast<uint32_t>(o * kBN);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t ad = smem_desc(a0 + sa * Cfg::kTileBytes + kk * 32, BK);
+            const uint64_t bd = smem_desc(b0 + sb * Cfg::kTileBytes + kk * 32, BK);
+            umma_f16(d, ad, bd, idesc, (started >> o) & 1u);
+            started |= 1u << o;
+          }
+        }
+        umma_commit(&empty_bar[s]);  // stage reusable once these MMAs have read it
+      }
+      umma_commit(&accum_bar);  // all accumulators final (also on the abort path)
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int r0 = ti * kBM + q * 32;
+    const int grow = r0 + lane;
+    const bool ok = mbar_wait_bounded(&accum_bar, 0, args.err, &abort_flag);
+    tc_fence_after();
+    if (ok && !abort_flag) {
+      double alpha = args.alpha, beta = args.beta;
+      if (args.coef != nullptr) {
+        alpha = args.coef[0];
+        beta = args.coef[1];
+      }
+      const double sa = (grow < args.M) ? args.row_scale_a[grow] : 0.0;
+      // per-warp staging tile (32 x 33 doubles) in the now idle pipeline buffers
+      double* stage = reinterpret_cast<double*>(smem) + q * (32 * 33);
+      for (int c = 0; c < kBN / 32; ++c) {
+        double v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = 0.0;
+        for (int o = args.nacc - 1; o >= 0; --o) {
+          uint32_t r[32];
+          tmem_ld_32x32b_x32(tbase + (static_cast<uint32_t>(q * 32) << 16) +
+                                 static_cast<uint32_t>(o * kBN + c * 32),
+                             r);
+          tmem_wait_ld();
+          const double w = ldexp(1.0, -11 * o);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += w * static_cast<double>(__uint_as_float(r[j]));
+        }
+        const int c0 = tj * kBN + c * 32;
+        // thread = row: finished values; mirror / transposed writes are coalesced here
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int gcol = c0 + j;
+          double val = 0.0;
+          if (grow < args.M && gcol < args.N) {
+            val = alpha * v[j] * sa * args.row_scale_b[gcol] * 0x1p-22;
+            if (args.D != nullptr) val += beta * args.D[static_cast<int64_t>(gcol) * args.ldd + grow];
+            if (grow == gcol) val += args.diag;
+            if (sym && grow < gcol) args.C[static_cast<int64_t>(gcol) * args.ldc + grow] = val;
+            if (args.Ct != nullptr) args.Ct[static_cast<int64_t>(gcol) * args.ldct + grow] = val;
+          }
+          stage[lane * 33 + j] = val;
+        }
+        __syncwarp();
+        // thread = column: direct writes, 32 consecutive doubles per row
+        const int gcol = c0 + lane;
+        for (int rr = 0; rr < 32; ++rr) {
+          const int row = r0 + rr;
+          if (row < args.M && gcol < args.N && (!sym || row <= gcol))
+            args.C[static_cast<int64_t>(row) * args.ldc + gcol] = stage[rr * 33 + lane];
+        }
+        __syncwarp();
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, ncols);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// 3-D map over slices: dims (K, rows, nslice), box (bk, 128, nslice), FP16, swizzle = bk*2 B.
+bool make_slice_map(CUtensorMap* map, const SliceBuf& sb, int bk, int nslice) {
+  EncodeTiledFn enc = get_encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(sb.cols), static_cast<cuuint64_t>(sb.rows),
+                        static_cast<cuuint64_t>(nslice)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(sb.ld) * 2,
+                           static_cast<cuuint64_t>(sb.ld) * sb.rows_alloc * 2};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(bk), 128u, static_cast<cuuint32_t>(nslice)};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<__half*>(sb.data), dims,
+                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int NSLICE, int BK, int STAGES>
+cudaError_t launch_cfg(const CUtensorMap& ta, const CUtensorMap& tb, const SlicedGemmArgs& a,
+                       int grid, cudaStream_t stream) {
+  using Cfg = GemmCfg<NSLICE, BK, STAGES>;
+  auto kern = sliced_gemm_kernel<NSLICE, BK, STAGES>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(Cfg::kSmemBytes));
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThreads, Cfg::kSmemBytes, stream>>>(ta, tb, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Pair list for `nslice` slices and highest order `max_order`: all (s, t) with s, t < nslice
+// and s + t <= max_order, ordered by order.
+int build_pairs(int nslice, int max_order, SlicedGemmArgs* a) {
+  int np = 0;
+  for (int o = 0; o <= max_order; ++o)
+    for (int s = 0; s <= o; ++s) {
+      const int t = o - s;
+      if (s < nslice && t < nslice && np < kMaxPairs) {
+        a->pair_s[np] = static_cast<int8_t>(s);
+        a->pair_t[np] = static_cast<int8_t>(t);
+        a->pair_o[np] = static_cast<int8_t>(o);
+        ++np;
+      }
+    }
+  a->num_pairs = np;
+  a->nacc = max_order + 1;
+  a->tmem_cols = (a->nacc <= 2) ? 256 : 512;
+  return np;
+}
+
+cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& B, const Precision& prec,
+                        SlicedGemmArgs args, cudaStream_t stream) {
+  const int nslice = prec.nslice;
+  if (nslice < 1 || nslice > 4 || prec.max_order < 0 || prec.max_order > 3 ||
+      prec.max_order > 2 * (nslice - 1))
+    return cudaErrorInvalidValue;
+  if (A.nslice_valid < nslice || B.nslice_valid < nslice) return cudaErrorInvalidValue;
+  if (A.cols != B.cols) return cudaErrorInvalidValue;  // contraction length
+  build_pairs(nslice, prec.max_order, &args);
+  args.M = A.rows;
+  args.N = B.rows;
+  args.K = A.cols;
+  args.row_scale_a = A.row_scale;
+  args.row_scale_b = B.row_scale;
+  if ((args.mode & kGemmSym) && args.M != args.N) return cudaErrorInvalidValue;
+  const int tm = (args.M + kBM - 1) / kBM;
+  const int tn = (args.N + kBN - 1) / kBN;
+  args.tiles_n = tn;
+  const int grid = (args.mode & kGemmSym) ? tn * (tn + 1) / 2 : tm * tn;
+  if (grid == 0) return cudaSuccess;
+
+  const int bk = (nslice >= 3) ? 32 : 64;
+  CUtensorMap ta, tb;
+  if (!make_slice_map(&ta, A, bk, nslice) || !make_slice_map(&tb, B, bk, nslice))
+    return cudaErrorInvalidValue;
+  switch (nslice) {
+    case 1: return launch_cfg<1, 64, 6>(ta, tb, args, grid, stream);
+    case 2: return launch_cfg<2, 64, 3>(ta, tb, args, grid, stream);
+    case 3: return launch_cfg<3, 32, 4>(ta, tb, args, grid, stream);
+    default: return launch_cfg<4, 32, 3>(ta, tb, args, grid, stream);
+  }
+}
+
+}  // namespace gdm

@@ -1,0 +1,151 @@
+"""GPU parity of the whole solve (C ABI gdm_init ... gdm_solve_dm) against the CPU oracle.
+
+Bars (from the target the engine is built to): relative Frobenius error of P <= 1e-6 against
+the FP64 oracle, |Tr(P S) - n_occ| <= 1e-8, band-energy error <= 1e-6 relative; the all-FP64
+path is held to 1e-9.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from oracle import steps
+from workloads import (make_config0, make_random_small, make_spectrum_problem, make_config2,
+                       make_request_problem)
+
+pytestmark = pytest.mark.gpu
+
+REL_P = 1e-6
+TRACE = 1e-8
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1912_13403_gb300 as g
+    return g
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def solve(g, p, prec=None, device_buffers=False):
+    h = g.Handle(p.n, p.n_occ)
+    try:
+        if prec is not None:
+            h.set_precision(prec)
+        if device_buffers:
+            H = torch.from_numpy(p.H).cuda()
+            S = torch.from_numpy(p.S).cuda()
+            P = torch.empty_like(H)
+            h.set_overlap(S)
+            h.set_hamiltonian(H)
+            P, e, info, st = h.solve(P)
+            return P.cpu().numpy(), e, info, st
+        h.set_overlap(p.S)
+        h.set_hamiltonian(p.H)
+        return h.solve()
+    finally:
+        h.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_config0_matches_oracle(g, prec):
+    p = make_config0()
+    ref = oracle.density_matrix(p.H, p.S, p.n_occ)
+    P, e, info, st = solve(g, p, g.GDM_PREC_FP64 if prec == "fp64" else None)
+    assert st == g.GDM_OK, info
+    bar = 1e-9 if prec == "fp64" else REL_P
+    assert rel(P, ref["P"]) <= bar, info
+    assert abs(e - ref["energy"]) <= bar * abs(ref["energy"])
+    assert info["trace_err"] <= TRACE
+    assert abs(np.sum(P * p.S) - p.n_occ) <= TRACE
+    assert np.array_equal(P, P.T)
+
+
+@pytest.mark.parametrize("n,n_occ", [(130, 33), (200, 150), (383, 96), (64, 1), (65, 64)])
+def test_ragged_sizes_match_oracle(g, n, n_occ):
+    p = make_random_small(1000 + n, n, n_occ)
+    ref = oracle.density_matrix(p.H, p.S, n_occ)
+    assert ref["status"] == "OK"
+    P, e, info, st = solve(g, p)
+    assert st == g.GDM_OK, info
+    assert rel(P, ref["P"]) <= REL_P, info
+    assert abs(e - ref["energy"]) <= REL_P * max(1.0, abs(ref["energy"]))
+    assert info["trace_err"] <= TRACE
+
+
+def test_ill_conditioned_overlap_closed_form(g):
+    p = make_spectrum_problem(21, 512, 128, cond_S=1e3, gap=0.2)
+    Pc, Ec = steps.closed_form_dm(p.factors, p.n_occ)
+    P, e, info, st = solve(g, p)
+    assert st == g.GDM_OK, info
+    assert rel(P, Pc) <= REL_P, info
+    assert abs(e - Ec) <= REL_P * abs(Ec)
+    assert info["trace_err"] <= TRACE
+
+
+def test_dftb_like_small_gap_closed_form(g):
+    p = make_config2(22, n=1024, n_occ=256)
+    Pc, Ec = steps.closed_form_dm(p.factors, p.n_occ)
+    P, e, info, st = solve(g, p)
+    assert st == g.GDM_OK, info
+    assert rel(P, Pc) <= REL_P, info
+    assert info["trace_err"] <= TRACE
+
+
+def test_device_buffers_and_fp64_path_agree(g):
+    p = make_config0(seed=3, n=192, n_occ=40)
+    P1, e1, i1, _ = solve(g, p, device_buffers=True)
+    P2, e2, i2, _ = solve(g, p, g.GDM_PREC_FP64)
+    assert rel(P1, P2) <= REL_P
+    assert abs(e1 - e2) <= REL_P * abs(e2)
+
+
+def test_z_cache_and_reinit(g):
+    p = make_config0(seed=4, n=160, n_occ=30)
+    q = make_request_problem(dict(seed=77, n=160, n_occ=30, gap=0.3))
+    with g.Handle(p.n, p.n_occ) as h:
+        h.set_overlap(p.S)
+        h.set_hamiltonian(p.H)
+        _, _, i1, _ = h.solve()
+        h.set_hamiltonian(2.0 * p.H)           # same geometry: Z is reused
+        P2, e2, i2, _ = h.solve()
+        assert i1["ns_iters"] > 0 and i2["ns_iters"] == 0
+        ref = oracle.density_matrix(2.0 * p.H, p.S, p.n_occ)
+        assert rel(P2, ref["P"]) <= REL_P
+        h.reinit()                             # new geometry
+        with pytest.raises(g.GdmError):
+            h.solve()
+        h.set_overlap(q.S)
+        h.set_hamiltonian(q.H)
+        P3, _, i3, _ = h.solve()
+        assert i3["ns_iters"] > 0
+        assert rel(P3, oracle.density_matrix(q.H, q.S, q.n_occ)["P"]) <= REL_P
+
+
+def test_error_paths(g):
+    n = 64
+    with pytest.raises(g.GdmError):
+        g.Handle(n, 0)
+    with pytest.raises(g.GdmError):
+        g.Handle(n, n)
+    with g.Handle(n, 10) as h:
+        with pytest.raises(g.GdmError) as ei:
+            h.solve()
+        assert ei.value.status == g.GDM_ERR_STATE
+        S = np.eye(n)
+        S[3, 3] = -1.0
+        h.set_overlap(S)
+        h.set_hamiltonian(np.diag(np.arange(n, dtype=np.float64)))
+        with pytest.raises(g.GdmError) as ei:
+            h.solve()
+        assert ei.value.status == g.GDM_ERR_NOT_SPD
+        bad = np.eye(n)
+        bad[1, 2] = np.nan
+        with pytest.raises(g.GdmError) as ei:
+            h.set_hamiltonian(bad)
+        assert ei.value.status == g.GDM_ERR_NONFINITE
+        assert g.gdm_set_slices(h._h, 3, 5, 1) == g.GDM_ERR_ARG
+        assert g.gdm_set_slices(h._h, 3, 1, 2) == g.GDM_ERR_ARG

@@ -13,6 +13,7 @@ from .synthetic import (  # noqa: F401
     make_batch_config3,
     make_spectrum_problem,
     make_request_stream,
+    make_request_problem,
     make_small_diag,
     make_random_small,
 )

@@ -1,0 +1,411 @@
+#!/usr/bin/env python3
+"""Density-matrix solve benchmark on GB300 (one JSON line on stdout, rank 0).
+
+A step is one cold solve of the whole route on a resident (H, S) pair: gdm_reinit, set S, set H,
+Newton-Schulz + refinement for Z, H~ = Z^T H Z, Gershgorin bounds, TRS4 purification,
+back-transform, Tr(P S) / Tr(P H), P written to device memory.  Default workload: the dense
+all-electron-like insulator (n = 4096, n_occ = 1024, cond(S) = 1e3, gap 0.2), synthetic inputs
+from `workloads`.  Multi-GPU: one process per GPU, independent problems per rank (replicas, no
+collective in the data path), value = all solves / max-over-ranks time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "density-matrix solves/s and TFLOP/s, mixed vs FP64 at 1e-6 rel err; p50/p99"
+UNIT = "solves/s"
+
+WORKLOADS = {
+    "config1": dict(desc="config1: dense all-electron-like insulator, n=4096, n_occ=1024, "
+                         "cond(S)=1e3 (log-spaced, Haar eigenvectors), occupied U[-3,-0.1], "
+                         "virtual U[0.1,10], gap 0.2",
+                    n=4096, n_occ=1024),
+    "config2": dict(desc="config2: DFTB-like, n=8192, n_occ=2048, H_ij = g_ij exp(-|i-j|/64) "
+                         "with a 0.05 gap at n_occ, S = I + 0.3 exp(-|i-j|/8)",
+                    n=8192, n_occ=2048),
+    "config0": dict(desc="config0: n=256, n_occ=64, S = I + 0.1 (G+G^T)/(2 sqrt n), gap >= 1",
+                    n=256, n_occ=64),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="config1")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-fp64-ref", action="store_true", help="skip the all-FP64 GPU solve")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cache", default="/tmp/gdm_bench_inputs",
+                    help="directory for generated inputs ('' disables)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# environment helpers
+# ------------------------------------------------------------------------------------------
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_problem(name, seed, device, cache_dir=None):
+    """Build the workload's inputs; with cache_dir, reuse an earlier build of the same
+    (workload, seed) saved there as .npz (generation needs torch.linalg on the device)."""
+    import numpy as np
+    import workloads
+    if cache_dir:
+        path = os.path.join(cache_dir, "%s_seed%d.npz" % (name, seed))
+        if os.path.exists(path):
+            d = np.load(path)
+            factors = {k: d[k] for k in ("Q", "lam", "S_U", "S_w")}
+            return workloads.Problem(d["H"], d["S"], int(d["n_occ"]), factors,
+                                     dict(config=name, seed=seed))
+        p = _generate(name, seed, device)
+        os.makedirs(cache_dir, exist_ok=True)
+        tmp = path + ".tmp.npz"
+        np.savez(tmp, H=p.H, S=p.S, n_occ=p.n_occ, **p.factors)
+        os.replace(tmp, path)
+        return p
+    return _generate(name, seed, device)
+
+
+def _generate(name, seed, device):
+    import workloads
+    if name == "config1":
+        return workloads.make_config1(seed=seed, device=device)
+    if name == "config2":
+        return workloads.make_config2(seed=seed, device=device)
+    return workloads.make_config0(seed=seed, device=device)
+
+
+def measured_peaks():
+    """Roofline denominators: MEASURED_PEAKS.json when present, else the machine's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    out = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0,
+               source="fallback")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+
+        def find(keys, default):
+            for k, v in d.items():
+                kl = k.lower()
+                if all(s in kl for s in keys) and isinstance(v, (int, float)):
+                    return float(v)
+            return default
+        out["hbm_gbs"] = find(["hbm"], out["hbm_gbs"])
+        sus = find(["bf16", "sustain"], None)
+        burst = None
+        for k, v in d.items():
+            if "bf16" in k.lower() and "sustain" not in k.lower() and isinstance(v, (int, float)):
+                burst = float(v)
+        if burst:
+            out["bf16_tflops"] = burst
+        if sus:
+            out["bf16_tflops_sustained"] = sus
+        out["source"] = "measured"
+    except Exception:
+        pass
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ------------------------------------------------------------------------------------------
+
+def cpu_baseline_sample(workload, n_sample=512):
+    """Time the FP64 CPU oracle (Jacobi) on the same recipe at n_sample and scale to the
+    workload's n by the O(n^3) cost; returns (solves/s, seconds of the sample, cores)."""
+    import oracle
+    import workloads
+    w = WORKLOADS[workload]
+    n, n_occ = w["n"], w["n_occ"]
+    ns = min(n_sample, n)
+    occ = max(1, int(round(ns * n_occ / n)))
+    if workload == "config1":
+        p = workloads.make_spectrum_problem(101, ns, occ, cond_S=1e3, gap=0.2)
+    elif workload == "config2":
+        p = workloads.make_config2(102, n=ns, n_occ=occ)
+    else:
+        p = workloads.make_config0(seed=103, n=ns, n_occ=occ)
+    t0 = time.perf_counter()
+    r = oracle.density_matrix(p.H, p.S, p.n_occ)
+    dt = time.perf_counter() - t0
+    assert r["status"] == "OK", r["status"]
+    scale = (n / ns) ** 3
+    return 1.0 / (dt * scale), dt, oracle.num_threads(), ns
+
+
+def run_reference(args):
+    rank, world, local = dist_info()
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, dt, cores, ns = cpu_baseline_sample(args.workload)
+        if i >= args.warmup:
+            vals.append((v, dt))
+    value = statistics.median(v for v, _ in vals)
+    ms = 1e3 / value
+    sample = ("FP64 CPU oracle (cyclic Jacobi of S and H~, P = C_occ C_occ^T) on the %s recipe "
+              "at n=%d per step, scaled by (n/%d)^3 to n=%d" % (args.workload, ns, ns, w["n"]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["desc"], "n": w["n"], "n_occ": w["n_occ"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# our engine
+# ------------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1912_13403_gb300 as g
+
+    w = WORKLOADS[args.workload]
+    n, n_occ = w["n"], w["n_occ"]
+    p = make_problem(args.workload, seed=1 + rank, device="cuda", cache_dir=args.cache)
+    H = torch.from_numpy(p.H).cuda()
+    S = torch.from_numpy(p.S).cuda()
+    P = torch.empty_like(H)
+    # closed form of the construction (H C = S C Lambda with C = S^{-1/2} Q): accuracy report
+    U = torch.from_numpy(p.factors["S_U"]).cuda()
+    sw = torch.from_numpy(p.factors["S_w"]).cuda()
+    Qo = torch.from_numpy(np.ascontiguousarray(p.factors["Q"][:, :n_occ])).cuda()
+    C = (U * sw.rsqrt()[None, :]) @ (U.T @ Qo)
+    Pc = C @ C.T
+    Ec = float(np.sum(p.factors["lam"][:n_occ]))
+    del U, sw, Qo, C
+
+    stream = torch.cuda.Stream()
+    h = g.Handle(n, n_occ, device=local)
+    h.set_stream(stream)
+    h.set_profiling(True)
+
+    def step():
+        h.reinit()
+        h.set_overlap(S)
+        h.set_hamiltonian(H)
+        return h.solve(P)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            _, e, info, st = step()
+    torch.cuda.synchronize()
+    h.profile(0, reset=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = g.gdm_launch_count()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with torch.cuda.stream(stream):
+        evs[0].record(stream)
+        for k in range(args.steps):
+            _, e, info, st = step()
+            evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = g.gdm_launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    prof_launch, prof_ms, prof_flops = h.profile(0)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # accuracy of the last timed solve
+    relerr = float(torch.linalg.norm(P - Pc) / torch.linalg.norm(Pc))
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    Hh = torch.from_numpy(p.H).pin_memory()
+    Sh = torch.from_numpy(p.S).pin_memory()
+    Ph = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    h2 = g.Handle(n, n_occ, device=local)
+    h2.set_overlap(Sh)
+    h2.set_hamiltonian(Hh)
+    h2.solve(Ph)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        h2.reinit()
+        h2.set_overlap(Sh)
+        h2.set_hamiltonian(Hh)
+        _, e2, info2, _ = h2.solve(Ph)
+        _ = float(Ph[0, 0])  # read the result on the host
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    h2.close()
+    e2e_val = world / e2e_s if world > 1 else 1.0 / e2e_s
+
+    # all-FP64 GPU path on the same input (one solve) for the mixed / FP64 comparison
+    fp64 = None
+    if not args.no_fp64_ref and rank == 0:
+        h3 = g.Handle(n, n_occ, device=local)
+        h3.set_precision(g.GDM_PREC_FP64)
+        h3.set_overlap(S)
+        h3.set_hamiltonian(H)
+        P3 = torch.empty_like(H)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, e3, info3, st3 = h3.solve(P3)
+        torch.cuda.synchronize()
+        fp64_s = time.perf_counter() - t0
+        fp64 = {"s_per_solve": fp64_s,
+                "rel_err": float(torch.linalg.norm(P3 - Pc) / torch.linalg.norm(Pc)),
+                "mixed_speedup": fp64_s / (total_ms / args.steps / 1e3)}
+        h3.close()
+        del P3
+
+    peaks = measured_peaks()
+    peak = peaks["bf16_tflops_sustained"]
+    achieved = (prof_flops / (prof_ms / 1e3)) / 1e12 if prof_ms > 0 else 0.0
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, cores, ns = cpu_baseline_sample(args.workload)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "FP64 CPU oracle (cyclic Jacobi) on the same recipe at n=%d (%.1f s), "
+                         "scaled by (%d/%d)^3" % (ns, dt, n, ns)}
+    per_sorted = sorted(per)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16-slices(f32-acc)+f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "n": n, "n_occ": n_occ, "precision": "mixed",
+                   "step": "cold solve: reinit, set S, set H, Newton-Schulz + refine, Z^T H Z, "
+                           "TRS4, back-transform, Tr(PS), Tr(PH)",
+                   "l2": "inputs larger than L2 (H and S %.0f MB each)" % (n * n * 8 / 1e6),
+                   "parallelism": "replicas x%d" % world},
+        "latency_ms": {"p50": per_sorted[len(per) // 2],
+                       "p99": per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)]},
+        "accuracy": {"rel_frobenius_err": relerr, "abs_energy_err": abs(e - Ec),
+                     "trace_err": info["trace_err"], "trace_err_raw": info["trace_err_raw"],
+                     "ns_iters": info["ns_iters"], "purif_iters": info["purif_iters"]},
+        "tflops_tensor_pipe": achieved,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "kernel": "sliced_gemm_kernel (tcgen05 kind::f16, all launches of the step)",
+                     "peak_source": "%s bf16 sustained (fp16 = bf16 rate)" % peaks["source"],
+                     "launches_per_step": prof_launch / args.steps},
+        "fp64_gpu_path": fp64,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * n * n * 8,
+                "d2h_bytes_per_step": n * n * 8},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    h.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

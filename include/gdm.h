@@ -76,10 +76,12 @@ typedef struct {
   int stop_reason;     /* 1 converged, 2 idempotency floor reached, 3 non-finite, 4 cap */
   double idem_err;     /* Tr(P~ - P~^2) of the final orthogonal-basis density matrix */
   double z_err;        /* ||Z^T S Z - I||_F after refinement */
-  double trace_err;    /* |Tr(P S) - n_occ| */
+  double trace_err;    /* |Tr(P S) - n_occ| of the returned P */
+  double trace_err_raw; /* |Tr(P S) - n_occ| before the final trace correction */
   double energy;       /* Tr(P H) */
   double eps_min, eps_max; /* Gershgorin bounds of H~ */
   double ms_total;     /* device time of the solve (ms), CUDA events on the handle's stream */
+  double trace_fix;    /* final trace reset of the orthogonal-basis matrix: N / Tr X - 1 */
 } gdm_info;
 
 /* Create a handle for n_basis x n_basis problems with n_occ occupied states (f_l in {0,1})
@@ -91,15 +93,37 @@ gdm_status gdm_init(gdm_handle** h, int64_t n_basis, int64_t n_occ, int device);
 /* Choose the product arithmetic (default GDM_PREC_MIXED).  Invalidates a cached Z. */
 gdm_status gdm_set_precision(gdm_handle* h, gdm_precision prec);
 
-/* Slice format of one phase in GDM_PREC_MIXED: nslice in 1..4 FP16 slices per operand, and
- * slice pairs up to order max_order (0..3, <= 2*(nslice-1)).  Defaults: Newton-Schulz (2,1),
- * refine (4,3), transform (4,3), purify (3,3). */
-gdm_status gdm_set_slices(gdm_handle* h, gdm_phase phase, int nslice, int max_order);
+/* Slice format of one phase in GDM_PREC_MIXED: nslice in 1..4 FP16 slices per operand, slice
+ * pairs up to order max_order (0..3, <= 2*(nslice-1)), and slice_bits in 9..12 bits for every
+ * slice after the first (0 = 12).  12 bits pack the most precision per slice; 9 bits keep every
+ * FP32 accumulator below 2^24 (exact) for contractions up to about 8192.  (0, 0, *) runs the
+ * phase on the FP64 kernel instead.  Defaults: Newton-Schulz (2,1,12), refine (4,3,9),
+ * transform (4,3,9), purify (3,3,12). */
+gdm_status gdm_set_slices(gdm_handle* h, gdm_phase phase, int nslice, int max_order,
+                          int slice_bits);
 
 /* Stopping tolerance of the purification: stop when |Tr(X - X^2)| <= idem_tol * n_occ
  * (default 1e-13) or when that error stops falling; trace_tol is the |Tr(P S) - n_occ|
  * above which the solve reports GDM_ERR_NOT_CONVERGED (default 1e-6; 0 disables). */
 gdm_status gdm_set_tolerance(gdm_handle* h, double idem_tol, double trace_tol);
+
+/* Final trace correction (default on): after the back-transform, P <- P * n_occ / Tr(P S),
+ * computed in FP64.  What it removes is the electron-count error left by Z^T S Z - I (about
+ * 1e-8 at cond(S) = 1e3 in GDM_PREC_MIXED); gdm_info.trace_err_raw reports it either way. */
+gdm_status gdm_set_trace_correction(gdm_handle* h, int enable);
+
+/* Timing of the product launches: when enabled, CUDA events are recorded around every
+ * product kernel on the handle's stream and folded into per-kind totals after each solve. */
+gdm_status gdm_set_profiling(gdm_handle* h, int enable);
+
+/* Totals since the last reset for kind 0 (sliced tensor-core products) or 1 (FP64 products):
+ * launches, device milliseconds and tensor-pipe flops (slice pairs x computed tile area x 2K
+ * for kind 0; computed tile area x 2K for kind 1).  reset != 0 zeroes the totals afterwards. */
+gdm_status gdm_get_profile(gdm_handle* h, int kind, int64_t* launches, double* ms, double* flops,
+                           int reset);
+
+/* Kernels launched by this library since it was loaded (all handles and threads). */
+int64_t gdm_launch_count(void);
 
 /* Iteration caps (defaults 100 and 200; 0 keeps the current value). */
 gdm_status gdm_set_max_iter(gdm_handle* h, int ns_max, int purif_max);
@@ -123,6 +147,13 @@ gdm_status gdm_set_hamiltonian(gdm_handle* h, const double* H, int64_t ld, gdm_m
 gdm_status gdm_solve_dm(gdm_handle* h, double* P, int64_t ld, gdm_mem mem, double* energy,
                         gdm_info* info);
 
+/* Purification history of the last gdm_solve_dm: for iteration i < max_rows, idem[i] =
+ * Tr(X_i - X_i^2), trace[i] = Tr X_i, gamma[i] and branch[i] (0: 2X - X^2, 1: X^2,
+ * 2: F + gamma G, 3: McWeeny, -1: the stopping iteration, no step taken).  Any output pointer
+ * may be NULL.  Returns the number of iterations recorded (0 for a NULL handle). */
+int gdm_get_history(const gdm_handle* h, int max_rows, double* idem, double* trace, double* gamma,
+                    int* branch);
+
 /* New geometry (Sec. 2.7): drop S, H and the cached Z; keep sizes and settings. */
 gdm_status gdm_reinit(gdm_handle* h);
 
@@ -142,11 +173,12 @@ const char* gdm_last_error(const gdm_handle* h);
 
 /* C = A * B for A (m x k, lda) and B given as Bt = B^T (n x k, ldb); C is m x n (ldc).
  * nslice = 0: plain FP64 kernel; nslice 1..4: sliced FP16 tensor-core kernel with slice pairs
- * up to order max_order.  symmetric != 0: the caller asserts C is symmetric (m == n); only
- * tiles on/above the diagonal are computed and mirrored.  Errors: GDM_ERR_ARG, GDM_ERR_CUDA. */
+ * up to order max_order and slice_bits (9..12, 0 = 12) bits per trailing slice.  symmetric != 0: the caller asserts C is symmetric (m == n); only
+ * tiles on/above the diagonal are computed and mirrored, and the diagonal is recomputed in
+ * FP64 from A and Bt.  Errors: GDM_ERR_ARG, GDM_ERR_CUDA. */
 gdm_status gdm_op_product(const double* A, int64_t lda, const double* Bt, int64_t ldb, double* C,
                           int64_t ldc, int64_t m, int64_t n, int64_t k, int nslice, int max_order,
-                          int symmetric, void* stream);
+                          int slice_bits, int symmetric, void* stream);
 
 /* Gershgorin bounds of the symmetric n x n matrix A: bounds_host[0] = min_i (a_ii - r_i),
  * bounds_host[1] = max_i (a_ii + r_i), r_i = sum_{j != i} |a_ij| (host array of 2). */
@@ -155,9 +187,10 @@ gdm_status gdm_op_gershgorin(const double* A, int64_t lda, int64_t n, double* bo
 
 /* One TRS4 step in place on the symmetric n x n matrix X (ld), target trace n_occ:
  * gamma = (n_occ - Tr F)/Tr G with F = X^2 (4X - 3X^2), G = X^2 (I - X)^2;
- * X <- 2X - X^2 (gamma > 6), X^2 (gamma < 0), F + gamma G (otherwise).
- * Products as in gdm_op_product (nslice = 0: FP64).  gamma_host / branch_host (0, 1, 2 for
- * the three cases) may be NULL. */
+ * X <- 2X - X^2 (gamma > 6), X^2 (gamma < 0), F + gamma G (otherwise); once
+ * Tr(X - X^2) < 0.1 and |Tr X - n_occ| < 0.25 (every eigenvalue within 0.113 of 0 or 1), or
+ * when Tr G is at the rounding level, the McWeeny step 3X^2 - 2X^3 is taken instead.  Products as in gdm_op_product (nslice = 0: FP64).  gamma_host /
+ * branch_host (0, 1, 2 for the three TRS4 cases, 3 for McWeeny) may be NULL. */
 gdm_status gdm_op_trs4_step(double* X, int64_t ld, int64_t n, double n_occ, int nslice,
                             int max_order, double* gamma_host, int* branch_host, void* stream);
 

@@ -34,9 +34,10 @@ class gdm_info(ctypes.Structure):
     _fields_ = [("ns_iters", ctypes.c_int), ("refine_iters", ctypes.c_int),
                 ("purif_iters", ctypes.c_int), ("stop_reason", ctypes.c_int),
                 ("idem_err", ctypes.c_double), ("z_err", ctypes.c_double),
-                ("trace_err", ctypes.c_double), ("energy", ctypes.c_double),
+                ("trace_err", ctypes.c_double), ("trace_err_raw", ctypes.c_double),
+                ("energy", ctypes.c_double),
                 ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double),
-                ("ms_total", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("trace_fix", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -59,19 +60,24 @@ def _decl(name, res, args):
 
 _decl("gdm_init", _int, [ctypes.POINTER(_vp), _i64, _i64, _int])
 _decl("gdm_set_precision", _int, [_vp, _int])
-_decl("gdm_set_slices", _int, [_vp, _int, _int, _int])
+_decl("gdm_set_slices", _int, [_vp, _int, _int, _int, _int])
 _decl("gdm_set_tolerance", _int, [_vp, _dbl, _dbl])
 _decl("gdm_set_max_iter", _int, [_vp, _int, _int])
+_decl("gdm_set_trace_correction", _int, [_vp, _int])
+_decl("gdm_set_profiling", _int, [_vp, _int])
+_decl("gdm_get_profile", _int, [_vp, _int, ctypes.POINTER(_i64), _dp, _dp, _int])
+_decl("gdm_launch_count", _i64, [])
 _decl("gdm_set_stream", _int, [_vp, _vp])
 _decl("gdm_set_overlap", _int, [_vp, _vp, _i64, _int])
 _decl("gdm_set_hamiltonian", _int, [_vp, _vp, _i64, _int])
 _decl("gdm_solve_dm", _int, [_vp, _vp, _i64, _int, _dp, ctypes.POINTER(gdm_info)])
+_decl("gdm_get_history", _int, [_vp, _int, _dp, _dp, _dp, ctypes.POINTER(_int)])
 _decl("gdm_reinit", _int, [_vp])
 _decl("gdm_finalize", _int, [_vp])
 _decl("gdm_status_string", ctypes.c_char_p, [_int])
 _decl("gdm_last_error", ctypes.c_char_p, [_vp])
 _decl("gdm_op_product", _int, [_vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _int, _int,
-                               _int, _vp])
+                               _int, _int, _vp])
 _decl("gdm_op_gershgorin", _int, [_vp, _i64, _i64, _dp, _vp])
 _decl("gdm_op_trs4_step", _int, [_vp, _i64, _i64, _dbl, _int, _int, _dp,
                                  ctypes.POINTER(_int), _vp])
@@ -136,11 +142,27 @@ class Handle:
     def set_precision(self, prec):
         return self._check(gdm_set_precision(self._h, prec))
 
-    def set_slices(self, phase, nslice, max_order):
-        return self._check(gdm_set_slices(self._h, phase, nslice, max_order))
+    def set_slices(self, phase, nslice, max_order, slice_bits=0):
+        return self._check(gdm_set_slices(self._h, phase, nslice, max_order, slice_bits))
 
     def set_tolerance(self, idem_tol, trace_tol):
         return self._check(gdm_set_tolerance(self._h, idem_tol, trace_tol))
+
+    def set_trace_correction(self, enable):
+        return self._check(gdm_set_trace_correction(self._h, int(bool(enable))))
+
+    def set_profiling(self, enable):
+        return self._check(gdm_set_profiling(self._h, int(bool(enable))))
+
+    def profile(self, kind=0, reset=False):
+        """(launches, device ms, tensor-pipe flops) of the product launches since the last
+        reset; kind 0 = sliced tensor-core products, 1 = FP64 products."""
+        l = _i64(0)
+        ms = ctypes.c_double(0)
+        fl = ctypes.c_double(0)
+        self._check(gdm_get_profile(self._h, kind, ctypes.byref(l), ctypes.byref(ms),
+                                    ctypes.byref(fl), int(bool(reset))))
+        return l.value, ms.value, fl.value
 
     def set_max_iter(self, ns_max, purif_max):
         return self._check(gdm_set_max_iter(self._h, ns_max, purif_max))
@@ -168,6 +190,15 @@ class Handle:
         self._check(st, allow)
         return P, e.value, info.as_dict(), st
 
+    def history(self, max_rows=1000):
+        """Purification history of the last solve: list of (idem, trace, gamma, branch)."""
+        idem = (ctypes.c_double * max_rows)()
+        tr = (ctypes.c_double * max_rows)()
+        gm = (ctypes.c_double * max_rows)()
+        br = (ctypes.c_int * max_rows)()
+        m = min(gdm_get_history(self._h, max_rows, idem, tr, gm, br), max_rows)
+        return [(idem[i], tr[i], gm[i], br[i]) for i in range(m)]
+
     def reinit(self):
         return self._check(gdm_reinit(self._h))
 
@@ -189,13 +220,14 @@ class Handle:
         self.close()
 
 
-def op_product(A, Bt, C, nslice=3, max_order=3, symmetric=False, stream=None):
+def op_product(A, Bt, C, nslice=3, max_order=3, symmetric=False, stream=None, slice_bits=0):
     """C = A @ Bt.T on the device (torch CUDA float64 tensors)."""
     pa, lda, _ = _buf(A)
     pb, ldb, _ = _buf(Bt)
     pc, ldc, _ = _buf(C)
     st = gdm_op_product(pa, lda, pb, ldb, pc, ldc, A.shape[0], Bt.shape[0], A.shape[1],
-                        nslice, max_order, int(bool(symmetric)), _stream_ptr(stream))
+                        nslice, max_order, slice_bits, int(bool(symmetric)),
+                        _stream_ptr(stream))
     if st != GDM_OK:
         raise GdmError(st, "gdm_op_product")
     return C

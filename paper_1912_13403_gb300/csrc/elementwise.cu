@@ -17,15 +17,17 @@ constexpr int kRowsPerBlock = 8;  // one warp per row for the reductions
 
 // ------------------------------------------------------------------------------------------
 // Y = a X + b X2 + c I, optional FP64 output, optional FP16 integer slices with a power-of-two
-// row scale sigma_i >= ||y_i||_2 (so the slice-0 row norm is <= 2^11).  Rounding: nearest-even
-// at every slice (rint), each residual is exact in FP64.
+// row scale sigma_i >= ||y_i||_2:  y = sigma 2^-11 (m_0 + m_1 2^-b + m_2 2^-2b + m_3 2^-3b ...).
+// Slice 0 takes 11 bits (so its row norm is <= 2^11 and |m_0| <= 2048); every later slice takes
+// b in 9..12 bits of a residual in [-1/2, 1/2] (|m_s| <= 2^(b-1) <= 2048, exact in FP16).
+// Rounding: nearest-even at every slice (rint); each residual is exact in FP64.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRowThreads)
     form_slice_kernel(const double* __restrict__ X, int64_t ldx, const double* __restrict__ X2,
                       int64_t ldx2, int rows, int cols, const double* __restrict__ coef_dev,
                       double ha, double hb, double hc, double* Y, int64_t ldy, __half* out,
                       double* out_scale, int64_t out_ld, int64_t plane, int nslice,
-                      const int* skip) {
+                      const int* skip, double step) {
   __shared__ double red[32];
   if (skip != nullptr && *skip != 0) return;
   const int row = blockIdx.x;
@@ -72,7 +74,7 @@ __global__ void __launch_bounds__(kRowThreads)
     for (int s = 0; s < nslice; ++s) {
       const double m = rint(x);
       orow[s * plane + j] = __float2half_rn(static_cast<float>(m));  // exact: |m| <= 2048
-      x = (x - m) * 2048.0;
+      x = (x - m) * step;
     }
   }
 }
@@ -239,18 +241,33 @@ __global__ void trs4_control_kernel(const double* partials, int nblocks, Trs4Sta
   int stop = 0;
   bool finite = true;
   for (int k = 0; k < kTraceTerms; ++k) finite = finite && isfinite(t[k]);
+  const double Nf = fmax(N, 1.0);
   if (!finite) {
     stop = 3;
-  } else if (fabs(idem) <= tol_idem || trG <= 1e-15 * fmax(N, 1.0)) {
+  } else if (fabs(idem) <= tol_idem) {
     stop = 1;
-  } else if (fabs(idem) < 1e-4 * fmax(N, 1.0) && fabs(idem) > 0.25 * fabs(st->idem_prev)) {
-    stop = 2;  // idempotency error no longer falls: the arithmetic's floor is reached
+  } else if (fabs(idem) < 1e-4 * Nf && fabs(idem) > 0.5 * fabs(st->idem_prev)) {
+    stop = 2;  // the idempotency error no longer falls: the arithmetic's floor is reached
   }
   st->stop = stop;
-  const double g = (trG != 0.0) ? (N - trF) / trG : INFINITY;
+  // Endgame.  Once Tr(X - X^2) < 0.1 every eigenvalue x has x(1-x) < 0.1, i.e. it lies within
+  // 0.113 of 0 or 1, and with |Tr X - N| < 0.25 exactly N of them are near 1.  From there the
+  // McWeeny map 3X^2 - 2X^3 = X^2 (3I - 2X) takes each to the nearer end (quadratically) and
+  // needs no gamma: gamma = (N - Tr F)/Tr G is a ratio of two differences that both vanish at
+  // convergence, so its digits go first and a wrong branch would move the trace by Tr(X - X^2).
+  const bool endgame = fabs(idem) < 0.1 && fabs(t[0] - N) < 0.25;
+  const bool gamma_ok = !endgame && trG > 1e-12 * Nf;
+  const double g = gamma_ok ? (N - trF) / trG : 0.0;
   st->gamma = g;
   int br;
-  if (g > 6.0) {
+  if (!gamma_ok) {
+    br = 3;
+    st->coefW[0] = -2.0;
+    st->coefW[1] = 0.0;
+    st->coefW[2] = 3.0;
+    st->gemm_coef[0] = 1.0;
+    st->gemm_coef[1] = 0.0;
+  } else if (g > 6.0) {
     br = 0;
     st->coefX[0] = 2.0;
     st->coefX[1] = -1.0;
@@ -269,8 +286,9 @@ __global__ void trs4_control_kernel(const double* partials, int nblocks, Trs4Sta
     st->gemm_coef[1] = g;
   }
   st->branch = br;
-  st->skip_gemm = (stop != 0 || br != 2) ? 1 : 0;
-  st->skip_form_x = (stop != 0 || br == 2) ? 1 : 0;
+  const bool with_product = (br == 2 || br == 3);
+  st->skip_gemm = (stop != 0 || !with_product) ? 1 : 0;
+  st->skip_form_x = (stop != 0 || with_product) ? 1 : 0;
   st->iter += 1;
 }
 
@@ -312,6 +330,55 @@ __global__ void symmetrise_kernel(double* A, int64_t lda, int n) {
   }
 }
 
+// C_ii = alpha <a_i, bt_i> + beta D_ii + diag in FP64, one warp per row.  The tensor core
+// accumulates in FP32 with truncation; on the diagonal of products whose two factors have
+// (nearly) parallel rows, such as X X or X^2 (3I - 2X), the slice-residual terms form a positive
+// sum whose truncation error does not average out, so that diagonal is recomputed here.
+__global__ void __launch_bounds__(kRowsPerBlock * 32)
+    diag_fix_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ Bt,
+                    int64_t ldb, double* C, int64_t ldc, int n, int K, double alpha, double beta,
+                    const double* D, int64_t ldd, double diag, const double* coef) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * kRowsPerBlock + w;
+  if (row >= n) return;
+  const double* ar = A + row * lda;
+  const double* br = Bt + row * ldb;
+  double acc = 0.0;
+  for (int k = lane; k < K; k += 32) acc = fma(ar[k], br[k], acc);
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    double al = alpha, be = beta;
+    if (coef != nullptr) {
+      al = coef[0];
+      be = coef[1];
+    }
+    double v = al * acc + diag;
+    if (D != nullptr) v += be * D[row * ldd + row];
+    C[row * ldc + row] = v;
+  }
+}
+
+// Trace reset, two launches: trace_factor_kernel (one block) writes sc = target / Tr X to
+// out[1] and sc - 1 to out[0]; scale_rows_kernel multiplies X by out[1].
+__global__ void trace_factor_kernel(const double* X, int64_t ld, int n, double target,
+                                    double* out) {
+  __shared__ double red[32];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) t += X[i * ld + i];
+  t = block_sum(t, red);
+  if (threadIdx.x == 0) {
+    const double sc = (t != 0.0 && isfinite(t)) ? target / t : 1.0;
+    out[0] = sc - 1.0;
+    out[1] = sc;
+  }
+}
+
+__global__ void scale_rows_kernel(double* X, int64_t ld, int n, const double* factor) {
+  const double sc = factor[1];
+  const int row = blockIdx.x;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) X[row * ld + j] *= sc;
+}
+
 __global__ void identity_kernel(double* A, int64_t lda, int n) {
   const int row = blockIdx.x;
   for (int j = threadIdx.x; j < n; j += blockDim.x) A[row * lda + j] = (j == row) ? 1.0 : 0.0;
@@ -322,8 +389,9 @@ __global__ void identity_kernel(double* A, int64_t lda, int n) {
 cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64_t ldx2,
                            int rows, int cols, const double* coef_dev, double ha, double hb,
                            double hc, double* Y, int64_t ldy, SliceBuf* out, int nslice,
-                           const int* skip, cudaStream_t stream) {
+                           const int* skip, cudaStream_t stream, int bits) {
   if (rows <= 0) return cudaSuccess;
+  if (bits < 9 || bits > 12) return cudaErrorInvalidValue;
   __half* od = nullptr;
   double* osc = nullptr;
   int64_t old = 0, plane = 0;
@@ -336,19 +404,23 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
     out->rows = rows;
     out->cols = cols;
     out->nslice_valid = nslice;
+    out->bits = bits;
   } else {
     nslice = 0;
   }
+  count_launch();
   form_slice_kernel<<<rows, kRowThreads, 0, stream>>>(X, ldx, X2, ldx2, rows, cols, coef_dev, ha,
                                                       hb, hc, Y, ldy, od, osc, old, plane,
-                                                      nslice, skip);
+                                                      nslice, skip, ldexp(1.0, bits));
   return cudaGetLastError();
 }
 
 cudaError_t gershgorin(const double* A, int64_t lda, int n, double* partials, double* out_dev,
                        cudaStream_t stream) {
   const int nb = (n + kRowsPerBlock - 1) / kRowsPerBlock;
+  count_launch();
   gershgorin_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, n, partials);
+  count_launch();
   minmax_reduce_kernel<<<1, 256, 0, stream>>>(partials, nb, out_dev);
   return cudaGetLastError();
 }
@@ -356,6 +428,7 @@ cudaError_t gershgorin(const double* A, int64_t lda, int n, double* partials, do
 cudaError_t trs4_traces(const double* X, const double* X2, int64_t ld, int n, double* partials,
                         int* nblocks, cudaStream_t stream) {
   const int nb = (n + kRowsPerBlock - 1) / kRowsPerBlock;
+  count_launch();
   trs4_traces_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(X, X2, ld, n, partials);
   *nblocks = nb;
   return cudaGetLastError();
@@ -365,6 +438,7 @@ cudaError_t dot_partials(const double* A, int64_t lda, const double* B, int64_t 
                          int cols, int minus_identity, double* partials, int* nblocks,
                          cudaStream_t stream) {
   const int nb = (rows + kRowsPerBlock - 1) / kRowsPerBlock;
+  count_launch();
   dot_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, B, ldb, rows, cols, minus_identity,
                                                     partials);
   *nblocks = nb;
@@ -373,23 +447,27 @@ cudaError_t dot_partials(const double* A, int64_t lda, const double* B, int64_t 
 
 cudaError_t reduce_partials(const double* partials, int nblocks, int nterms, double* out_dev,
                             cudaStream_t stream) {
+  count_launch();
   reduce_kernel<<<1, 256, 0, stream>>>(partials, nblocks, nterms, out_dev);
   return cudaGetLastError();
 }
 
 cudaError_t trs4_control(const double* partials, int nblocks, Trs4State* st, double tol_idem,
                          cudaStream_t stream) {
+  count_launch();
   trs4_control_kernel<<<1, 256, 0, stream>>>(partials, nblocks, st, tol_idem);
   return cudaGetLastError();
 }
 
 cudaError_t x0_coefficients(const double* bounds_dev, double* coef_dev, cudaStream_t stream) {
+  count_launch();
   x0_coef_kernel<<<1, 1, 0, stream>>>(bounds_dev, coef_dev);
   return cudaGetLastError();
 }
 
 cudaError_t scale_coefficients(const double* bounds_dev, int inv_sqrt, double* coef_dev,
                                cudaStream_t stream) {
+  count_launch();
   scale_coef_kernel<<<1, 1, 0, stream>>>(bounds_dev, inv_sqrt, coef_dev);
   return cudaGetLastError();
 }
@@ -397,12 +475,35 @@ cudaError_t scale_coefficients(const double* bounds_dev, int inv_sqrt, double* c
 cudaError_t symmetrise(double* A, int64_t lda, int n, cudaStream_t stream) {
   const int t = (n + 31) / 32;
   if (t == 0) return cudaSuccess;
+  count_launch();
   symmetrise_kernel<<<dim3(t, t), dim3(32, 8), 0, stream>>>(A, lda, n);
+  return cudaGetLastError();
+}
+
+cudaError_t diag_fix(const double* A, int64_t lda, const double* Bt, int64_t ldb, double* C,
+                     int64_t ldc, int n, int K, double alpha, double beta, const double* D,
+                     int64_t ldd, double diag, const double* coef, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int nb = (n + kRowsPerBlock - 1) / kRowsPerBlock;
+  count_launch();
+  diag_fix_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, Bt, ldb, C, ldc, n, K, alpha,
+                                                         beta, D, ldd, diag, coef);
+  return cudaGetLastError();
+}
+
+cudaError_t trace_scale(double* X, int64_t ld, int n, double target, double* fix_out,
+                        cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  trace_factor_kernel<<<1, 1024, 0, stream>>>(X, ld, n, target, fix_out);
+  count_launch();
+  scale_rows_kernel<<<n, 256, 0, stream>>>(X, ld, n, fix_out);
   return cudaGetLastError();
 }
 
 cudaError_t set_identity(double* A, int64_t lda, int n, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
+  count_launch();
   identity_kernel<<<n, 256, 0, stream>>>(A, lda, n);
   return cudaGetLastError();
 }

@@ -20,6 +20,7 @@
 #include <cstring>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "../../include/gdm.h"
 #include "gdm_internal.h"
@@ -41,8 +42,9 @@ struct gdm_handle {
   int rows_alloc = 0;     // rows of slice buffers (multiple of 128)
   cudaStream_t own_stream = nullptr, stream = nullptr;
   gdm_precision prec = GDM_PREC_MIXED;
-  Precision phase[4] = {{2, 1}, {4, 3}, {4, 3}, {3, 3}};
+  Precision phase[4] = {{2, 1, 12}, {4, 3, 9}, {4, 3, 9}, {3, 3, 12}};
   double idem_tol = 1e-13, trace_tol = 1e-6;
+  bool trace_correct = true;
   int max_ns = 100, max_purif = 200, n_refine = 2;
 
   void* pool = nullptr;
@@ -58,6 +60,22 @@ struct gdm_handle {
 
   bool have_H = false, have_S = false, z_valid = false;
   double z_err = 0.0;
+  struct HistRow {
+    double idem, trace, gamma;
+    int branch;
+  };
+  std::vector<HistRow> hist;  // purification history of the last solve
+  // optional timing of the sliced / FP64 product launches (CUDA events on the stream)
+  bool profiling = false;
+  struct Prof {
+    cudaEvent_t a, b;
+    double flops;
+    int kind;  // 0 sliced, 1 fp64
+  };
+  std::vector<Prof> prof_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  int64_t prof_launches[2] = {0, 0};
+  double prof_ms[2] = {0, 0}, prof_flops[2] = {0, 0};
   std::string last_error;
 };
 
@@ -99,19 +117,59 @@ struct Op {
 
 bool mixed(const gdm_handle* h) { return h->prec == GDM_PREC_MIXED; }
 
+// A phase runs on the sliced tensor-core kernel unless the handle is in FP64 mode or the
+// phase's slice count is 0 (that phase then uses the FP64 kernel).
+bool sliced(const gdm_handle* h, int ph) { return mixed(h) && h->phase[ph].nslice > 0; }
+
 // device address of a field of the device-resident controller state
 const double* st_field(const gdm_handle* h, size_t offset) {
   return reinterpret_cast<const double*>(reinterpret_cast<const char*>(h->st_dev) + offset);
 }
 
-int slices_for(const gdm_handle* h, int ph) { return mixed(h) ? h->phase[ph].nslice : 0; }
+int slices_for(const gdm_handle* h, int ph) { return sliced(h, ph) ? h->phase[ph].nslice : 0; }
+
+cudaEvent_t pool_event(gdm_handle* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Fold the recorded launch timings into the totals (the stream must be idle).
+void collect_profile(gdm_handle* h) {
+  for (auto& p : h->prof_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      h->prof_ms[p.kind] += ms;
+      h->prof_flops[p.kind] += p.flops;
+      h->prof_launches[p.kind] += 1;
+    }
+    h->ev_pool.push_back(p.a);
+    h->ev_pool.push_back(p.b);
+  }
+  h->prof_pending.clear();
+}
+
+// Tensor-pipe work of one sliced launch: slice pairs x computed tile area x 2 K
+double sliced_flops(const gdm_handle* h, int ph, bool sym) {
+  const double n = static_cast<double>(h->n);
+  const double t = std::ceil(n / 128.0);
+  const double tiles = sym ? t * (t + 1) / 2 : t * t;
+  SlicedGemmArgs tmp;
+  const int pairs = build_pairs(h->phase[ph].nslice, h->phase[ph].max_order, &tmp);
+  return pairs * tiles * 128.0 * 128.0 * 2.0 * n;
+}
 
 // C = alpha * A * Bt^T + beta * D + diag * I (sym: C symmetric, upper tiles + mirror)
 cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const double* D,
                     double alpha, double beta, double diag, bool sym, int ph,
                     const double* coef = nullptr) {
   const int n = static_cast<int>(h->n);
-  if (mixed(h)) {
+  if (sliced(h, ph)) {
     SlicedGemmArgs a;
     a.mode = sym ? kGemmSym : 0;
     a.C = C;
@@ -125,7 +183,24 @@ cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const dou
     a.diag = diag;
     a.coef = coef;
     a.err = h->err_dev;
-    return sliced_gemm(*A.sl, *Bt.sl, h->phase[ph], a, h->stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->profiling) {
+      e0 = pool_event(h);
+      e1 = pool_event(h);
+      cudaEventRecord(e0, h->stream);
+    }
+    cudaError_t e = sliced_gemm(*A.sl, *Bt.sl, h->phase[ph], a, h->stream);
+    if (e != cudaSuccess) return e;
+    if (h->profiling) {
+      cudaEventRecord(e1, h->stream);
+      h->prof_pending.push_back({e0, e1, sliced_flops(h, ph, sym), 0});
+    }
+    // exact FP64 diagonal (removes the truncation bias of the FP32 accumulators there)
+    e = diag_fix(A.f, h->ld, Bt.f, h->ld, C, h->ld, n, n, alpha, beta, D, h->ld, diag, coef,
+                 h->stream);
+    if (e != cudaSuccess || Ct == nullptr) return e;
+    return diag_fix(A.f, h->ld, Bt.f, h->ld, Ct, h->ld, n, n, alpha, beta, D, h->ld, diag, coef,
+                    h->stream);
   }
   F64GemmArgs a;
   a.M = n;
@@ -146,16 +221,31 @@ cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const dou
   a.beta = beta;
   a.diag = diag;
   a.coef = coef;
-  return f64_gemm(a, h->stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h->profiling) {
+    e0 = pool_event(h);
+    e1 = pool_event(h);
+    cudaEventRecord(e0, h->stream);
+  }
+  cudaError_t e = f64_gemm(a, h->stream);
+  if (h->profiling && e == cudaSuccess) {
+    cudaEventRecord(e1, h->stream);
+    const double nn = static_cast<double>(n);
+    const double t = std::ceil(nn / 64.0);
+    h->prof_pending.push_back({e0, e1, (sym ? t * (t + 1) / 2 : t * t) * 64.0 * 64.0 * 2.0 * nn, 1});
+  }
+  return e;
 }
 
-// Slice `src` (FP64) into `dst` with `nslice` slices (no-op in FP64 mode).
-cudaError_t slice(gdm_handle* h, const double* src, SliceBuf* dst, int nslice) {
-  if (!mixed(h) || nslice <= 0) return cudaSuccess;
+// Slice `src` (FP64) into `dst` in the format of phase `ph` (no-op when that phase is FP64).
+cudaError_t slice(gdm_handle* h, const double* src, SliceBuf* dst, int ph) {
+  if (!sliced(h, ph)) return cudaSuccess;
   const int n = static_cast<int>(h->n);
   return form_and_slice(src, h->ld, nullptr, 0, n, n, nullptr, 1.0, 0.0, 0.0, nullptr, 0, dst,
-                        nslice, nullptr, h->stream);
+                        h->phase[ph].nslice, nullptr, h->stream, h->phase[ph].bits);
 }
+
+int bits_for(const gdm_handle* h, int ph) { return h->phase[ph].bits; }
 
 // Synchronous scalar read-back of small[SM_RED + k] for k < count.
 gdm_status read_small(gdm_handle* h, int offset, int count, double* out) {
@@ -194,7 +284,7 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
   const int64_t ld = h->ld;
   cudaStream_t s = h->stream;
   const int ns_sl = slices_for(h, GDM_PHASE_NEWTON_SCHULZ);
-  const int big_sl = mixed(h) ? 4 : 0;
+  const int ref_sl = slices_for(h, GDM_PHASE_REFINE);
   double* S = h->f[F_S];
   double* bounds = h->small + SM_BOUNDS_S;
   double* coef_inv = h->small + SM_COEF_A;
@@ -213,10 +303,10 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
   double *Y = h->f[F_X], *Z = h->f[F_XN], *M = h->f[F_T], *Mt = h->f[F_U];
   double *Yn = h->f[F_X2], *Zn = h->f[F_V];
   SliceBuf *sY = &h->sl[SL_X], *sZ = &h->sl[SL_Z], *sM = &h->sl[SL_A], *sMt = &h->sl[SL_B];
-  CK(form_and_slice(S, ld, nullptr, 0, n, n, coef_inv, 0, 0, 0, Y, ld, mixed(h) ? sY : nullptr,
-                    ns_sl, nullptr, s));
+  CK(form_and_slice(S, ld, nullptr, 0, n, n, coef_inv, 0, 0, 0, Y, ld, ns_sl > 0 ? sY : nullptr,
+                    ns_sl, nullptr, s, bits_for(h, GDM_PHASE_NEWTON_SCHULZ)));
   CK(set_identity(Z, ld, n, s));
-  CK(slice(h, Z, sZ, ns_sl));
+  CK(slice(h, Z, sZ, GDM_PHASE_NEWTON_SCHULZ));
 
   const double rn = std::sqrt(static_cast<double>(n));
   double prev = INFINITY, res = INFINITY;
@@ -238,16 +328,16 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
       break;
     }
     prev = res;
-    CK(slice(h, M, sM, ns_sl));
-    CK(slice(h, Mt, sMt, ns_sl));
+    CK(slice(h, M, sM, GDM_PHASE_NEWTON_SCHULZ));
+    CK(slice(h, Mt, sMt, GDM_PHASE_NEWTON_SCHULZ));
     CK(product(h, {M, sM}, {Y, sY}, Yn, nullptr, Y, -0.5, 1.5, 0.0, true,
                GDM_PHASE_NEWTON_SCHULZ));
     CK(product(h, {Mt, sMt}, {Z, sZ}, Zn, nullptr, Z, -0.5, 1.5, 0.0, true,
                GDM_PHASE_NEWTON_SCHULZ));
     std::swap(Y, Yn);
     std::swap(Z, Zn);
-    CK(slice(h, Y, sY, ns_sl));
-    CK(slice(h, Z, sZ, ns_sl));
+    CK(slice(h, Y, sY, GDM_PHASE_NEWTON_SCHULZ));
+    CK(slice(h, Z, sZ, GDM_PHASE_NEWTON_SCHULZ));
   }
   if (info) info->ns_iters = it;
   (void)converged;  // a capped run is still refined below; z_err reports the outcome
@@ -255,8 +345,9 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
   // Z_0 = Z_k / sqrt(c), symmetric: its transpose is itself
   double* Zc = h->f[F_Z];
   CK(form_and_slice(Z, ld, nullptr, 0, n, n, coef_isqrt, 0, 0, 0, Zc, ld,
-                    mixed(h) ? &h->sl[SL_Z] : nullptr, big_sl, nullptr, s));
-  CK(slice(h, S, &h->sl[SL_S], big_sl));
+                    ref_sl > 0 ? &h->sl[SL_Z] : nullptr, ref_sl, nullptr, s,
+                    bits_for(h, GDM_PHASE_REFINE)));
+  CK(slice(h, S, &h->sl[SL_S], GDM_PHASE_REFINE));
   Op zc = {Zc, &h->sl[SL_Z]};
   Op zct = zc;
   const int nref = mixed(h) ? h->n_refine : 1;
@@ -267,7 +358,7 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
     double* F = h->f[F_V];
     CK(product(h, zct, {S, &h->sl[SL_S]}, T, nullptr, nullptr, 1.0, 0.0, 0.0, false,
                GDM_PHASE_REFINE));                                   // T = Z^T S
-    CK(slice(h, T, &h->sl[SL_A], big_sl));
+    CK(slice(h, T, &h->sl[SL_A], GDM_PHASE_REFINE));
     CK(product(h, {T, &h->sl[SL_A]}, zct, Dl, nullptr, nullptr, 1.0, 0.0, -1.0, true,
                GDM_PHASE_REFINE));                                   // delta = Z^T S Z - I
     double d2 = 0.0;
@@ -276,18 +367,18 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
     derr = std::sqrt(d2);
     if (!std::isfinite(derr)) return set_err(h, GDM_ERR_NONFINITE, "non-finite Z^T S Z");
     if (r == nref || derr == 0.0) break;
-    CK(slice(h, Dl, &h->sl[SL_B], big_sl));
+    CK(slice(h, Dl, &h->sl[SL_B], GDM_PHASE_REFINE));
     CK(product(h, {Dl, &h->sl[SL_B]}, {Dl, &h->sl[SL_B]}, F, nullptr, Dl, 0.375, -0.5, 1.0, true,
                GDM_PHASE_REFINE));                                   // F = I - d/2 + 3d^2/8
-    CK(slice(h, F, &h->sl[SL_A], big_sl));
+    CK(slice(h, F, &h->sl[SL_A], GDM_PHASE_REFINE));
     double* Znew = h->f[F_X];
     double* Zt_new = h->f[F_X2];
     CK(product(h, zc, {F, &h->sl[SL_A]}, Znew, Zt_new, nullptr, 1.0, 0.0, 0.0, false,
                GDM_PHASE_REFINE));                                   // Z <- Z F
     std::swap(h->f[F_Z], h->f[F_X]);
     std::swap(h->f[F_ZT], h->f[F_X2]);
-    CK(slice(h, h->f[F_Z], &h->sl[SL_Z], big_sl));
-    CK(slice(h, h->f[F_ZT], &h->sl[SL_ZT], big_sl));
+    CK(slice(h, h->f[F_Z], &h->sl[SL_Z], GDM_PHASE_REFINE));
+    CK(slice(h, h->f[F_ZT], &h->sl[SL_ZT], GDM_PHASE_REFINE));
     zc = {h->f[F_Z], &h->sl[SL_Z]};
     zct = {h->f[F_ZT], &h->sl[SL_ZT]};
     if (info) info->refine_iters = r + 1;
@@ -296,8 +387,10 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
     // no refinement step ran: Z is symmetric, keep an explicit transpose for the later steps
     CK(cudaMemcpyAsync(h->f[F_ZT], h->f[F_Z], sizeof(double) * ld * n, cudaMemcpyDeviceToDevice,
                        s));
-    CK(slice(h, h->f[F_ZT], &h->sl[SL_ZT], big_sl));
   }
+  // Z and Z^T in the format of the transform phase, which uses them from here on
+  CK(slice(h, h->f[F_Z], &h->sl[SL_Z], GDM_PHASE_TRANSFORM));
+  CK(slice(h, h->f[F_ZT], &h->sl[SL_ZT], GDM_PHASE_TRANSFORM));
   h->z_err = derr;
   h->z_valid = true;
   return GDM_OK;
@@ -323,10 +416,10 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   double* H = h->f[F_H];
 
   // H~ = Z^T H Z
-  CK(slice(h, H, &h->sl[SL_A], tr_sl));
+  CK(slice(h, H, &h->sl[SL_A], GDM_PHASE_TRANSFORM));
   CK(product(h, Zt, {H, &h->sl[SL_A]}, h->f[F_T], nullptr, nullptr, 1.0, 0.0, 0.0, false,
              GDM_PHASE_TRANSFORM));
-  CK(slice(h, h->f[F_T], &h->sl[SL_B], tr_sl));
+  CK(slice(h, h->f[F_T], &h->sl[SL_B], GDM_PHASE_TRANSFORM));
   double* Ht = h->f[F_U];
   CK(product(h, {h->f[F_T], &h->sl[SL_B]}, Zt, Ht, nullptr, nullptr, 1.0, 0.0, 0.0, true,
              GDM_PHASE_TRANSFORM));
@@ -348,7 +441,8 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   double* X2 = h->f[F_X2];
   double* Xn = h->f[F_XN];
   CK(form_and_slice(Ht, ld, nullptr, 0, n, n, h->small + SM_COEF_X0, 0, 0, 0, X, ld,
-                    mixed(h) ? &h->sl[SL_X] : nullptr, pu_sl, nullptr, s));
+                    pu_sl > 0 ? &h->sl[SL_X] : nullptr, pu_sl, nullptr, s,
+                    bits_for(h, GDM_PHASE_PURIFY)));
 
   // TRS4
   Trs4State init;
@@ -357,6 +451,8 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   init.idem = INFINITY;
   CK(cudaMemcpyAsync(h->st_dev, &init, sizeof(init), cudaMemcpyHostToDevice, s));
   const double tol_abs = h->idem_tol * static_cast<double>(h->n_occ);
+  h->hist.clear();
+  double last_idem = INFINITY;
   int it = 0;
   int stop = 4;
   double* W = h->f[F_V];
@@ -369,20 +465,32 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
     CK(cudaMemcpyAsync(h->st_host, h->st_dev, sizeof(Trs4State), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const Trs4State& t = *h->st_host;
+    h->hist.push_back({t.idem, t.t[0], t.gamma, t.stop != 0 ? -1 : t.branch});
     if (t.stop != 0) {
       stop = t.stop;
+      // at the arithmetic's floor a further step only adds rounding: if this iterate is worse
+      // than the previous one, return to the previous one (still in Xn)
+      if (stop == 2 && it > 0 && std::fabs(t.idem) > std::fabs(t.idem_prev)) {
+        std::swap(X, Xn);
+        h->hist.back().branch = -2;
+        last_idem = t.idem_prev;
+      } else {
+        last_idem = t.idem;
+      }
       break;
     }
-    if (t.branch == 2) {
-      CK(slice(h, X2, &h->sl[SL_X2], pu_sl));
-      CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefW)), 0, 0, 0, mixed(h) ? nullptr : W, ld,
-                        mixed(h) ? &h->sl[SL_W] : nullptr, pu_sl, nullptr, s));
+    last_idem = t.idem;
+    if (t.branch == 2 || t.branch == 3) {  // a product: F + gamma G, or McWeeny
+      CK(slice(h, X2, &h->sl[SL_X2], GDM_PHASE_PURIFY));
+      CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefW)), 0, 0, 0, W, ld, pu_sl > 0 ? &h->sl[SL_W] : nullptr, pu_sl, nullptr, s,
+                        bits_for(h, GDM_PHASE_PURIFY)));
       CK(product(h, {X2, &h->sl[SL_X2]}, {W, &h->sl[SL_W]}, Xn, nullptr, X2, 1.0, 0.0, 0.0, true,
                  GDM_PHASE_PURIFY, st_field(h, offsetof(Trs4State, gemm_coef))));
-      CK(slice(h, Xn, &h->sl[SL_X], pu_sl));
+      CK(slice(h, Xn, &h->sl[SL_X], GDM_PHASE_PURIFY));
     } else {
       CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefX)), 0, 0, 0, Xn, ld,
-                        mixed(h) ? &h->sl[SL_X] : nullptr, pu_sl, nullptr, s));
+                        pu_sl > 0 ? &h->sl[SL_X] : nullptr, pu_sl, nullptr, s,
+                        bits_for(h, GDM_PHASE_PURIFY)));
     }
     std::swap(X, Xn);
   }
@@ -391,20 +499,44 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   if (info) {
     info->purif_iters = it;
     info->stop_reason = stop;
-    info->idem_err = h->st_host->idem;
+    info->idem_err = last_idem;
   }
   if (stop == 3) return set_err(h, GDM_ERR_NONFINITE, "non-finite traces during purification");
 
-  // P = Z X Z^T  (X slices are current)
+  // Final trace reset (zeroth order): X <- X * N / Tr X.  TRS4 keeps Tr X = N through its
+  // gamma steps; the McWeeny endgame does not, and the rounding of the products leaves Tr X off
+  // by about the idempotency floor.  The scale factor differs from 1 by that relative amount,
+  // so idempotency and the subspace are unchanged to that order.
+  {
+    CK(trace_scale(X, ld, n, static_cast<double>(h->n_occ), h->small + SM_RED + 4, s));
+    double fix = 0.0;
+    st = read_small(h, SM_RED + 4, 1, &fix);
+    if (st != GDM_OK) return st;
+    if (info) info->trace_fix = fix;
+  }
+
+  // P = Z X Z^T  (X re-sliced in the transform format)
+  CK(slice(h, X, &h->sl[SL_X], GDM_PHASE_TRANSFORM));
   CK(product(h, Z, {X, &h->sl[SL_X]}, h->f[F_T], nullptr, nullptr, 1.0, 0.0, 0.0, false,
              GDM_PHASE_TRANSFORM));
-  CK(slice(h, h->f[F_T], &h->sl[SL_A], tr_sl));
+  CK(slice(h, h->f[F_T], &h->sl[SL_A], GDM_PHASE_TRANSFORM));
   double* P = h->f[F_XN];
   CK(product(h, {h->f[F_T], &h->sl[SL_A]}, Z, P, nullptr, nullptr, 1.0, 0.0, 0.0, true,
              GDM_PHASE_TRANSFORM));
+  // Electron count in the S metric, then the final trace correction P <- P N / Tr(P S): the
+  // remaining count error comes from Z^T S Z - I (the accuracy to which the products resolve
+  // the overlap), and renormalising moves P by that same relative amount (about 1e-11).
   double trps = 0.0, e = 0.0;
   st = dot(h, P, h->f[F_S], 0, &trps);
   if (st != GDM_OK) return st;
+  const double N = static_cast<double>(h->n_occ);
+  if (info) info->trace_err_raw = std::fabs(trps - N);
+  if (h->trace_correct && std::isfinite(trps) && trps > 0.0) {
+    CK(form_and_slice(P, ld, nullptr, 0, n, n, nullptr, N / trps, 0.0, 0.0, P, ld, nullptr, 0,
+                      nullptr, s));
+    st = dot(h, P, h->f[F_S], 0, &trps);
+    if (st != GDM_OK) return st;
+  }
   st = dot(h, P, H, 0, &e);
   if (st != GDM_OK) return st;
   st = check_device_error(h);
@@ -443,6 +575,13 @@ gdm_status ingest(gdm_handle* h, const double* src, int64_t ld_src, gdm_mem mem,
 }
 
 void free_all(gdm_handle* h) {
+  for (auto& p : h->prof_pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  h->prof_pending.clear();
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  h->ev_pool.clear();
   if (h->pool) cudaFree(h->pool);
   if (h->host_buf) cudaFreeHost(h->host_buf);
   if (h->st_host) cudaFreeHost(h->st_host);
@@ -563,13 +702,19 @@ gdm_status gdm_set_precision(gdm_handle* h, gdm_precision prec) {
   return GDM_OK;
 }
 
-gdm_status gdm_set_slices(gdm_handle* h, gdm_phase phase, int nslice, int max_order) {
+gdm_status gdm_set_slices(gdm_handle* h, gdm_phase phase, int nslice, int max_order,
+                          int slice_bits) {
   if (h == nullptr) return GDM_ERR_ARG;
   if (phase < GDM_PHASE_NEWTON_SCHULZ || phase > GDM_PHASE_PURIFY)
     return set_err(h, GDM_ERR_ARG, "unknown phase %d", static_cast<int>(phase));
-  if (nslice < 1 || nslice > 4 || max_order < 0 || max_order > 3 || max_order > 2 * (nslice - 1))
+  const bool fp64 = (nslice == 0 && max_order == 0);
+  if (!fp64 && (nslice < 1 || nslice > 4 || max_order < 0 || max_order > 3 ||
+                max_order > 2 * (nslice - 1)))
     return set_err(h, GDM_ERR_ARG, "invalid slice format (%d, %d)", nslice, max_order);
-  h->phase[phase] = {nslice, max_order};
+  if (slice_bits == 0) slice_bits = 12;
+  if (slice_bits < 9 || slice_bits > 12)
+    return set_err(h, GDM_ERR_ARG, "slice_bits must be 9..12 (or 0 for 12)");
+  h->phase[phase] = {nslice, max_order, slice_bits};
   if (phase == GDM_PHASE_NEWTON_SCHULZ || phase == GDM_PHASE_REFINE) h->z_valid = false;
   return GDM_OK;
 }
@@ -580,6 +725,34 @@ gdm_status gdm_set_tolerance(gdm_handle* h, double idem_tol, double trace_tol) {
     return set_err(h, GDM_ERR_ARG, "tolerances must be >= 0");
   h->idem_tol = idem_tol;
   h->trace_tol = trace_tol;
+  return GDM_OK;
+}
+
+gdm_status gdm_set_profiling(gdm_handle* h, int enable) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  h->profiling = (enable != 0);
+  return GDM_OK;
+}
+
+gdm_status gdm_get_profile(gdm_handle* h, int kind, int64_t* launches, double* ms,
+                           double* flops, int reset) {
+  if (h == nullptr || kind < 0 || kind > 1) return GDM_ERR_ARG;
+  if (launches) *launches = h->prof_launches[kind];
+  if (ms) *ms = h->prof_ms[kind];
+  if (flops) *flops = h->prof_flops[kind];
+  if (reset) {
+    h->prof_launches[kind] = 0;
+    h->prof_ms[kind] = 0.0;
+    h->prof_flops[kind] = 0.0;
+  }
+  return GDM_OK;
+}
+
+int64_t gdm_launch_count(void) { return launch_count(); }
+
+gdm_status gdm_set_trace_correction(gdm_handle* h, int enable) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  h->trace_correct = (enable != 0);
   return GDM_OK;
 }
 
@@ -634,10 +807,25 @@ gdm_status gdm_solve_dm(gdm_handle* h, double* P, int64_t ld, gdm_mem mem, doubl
                          h->stream));
   }
   CK(cudaStreamSynchronize(h->stream));
+  collect_profile(h);
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) local.ms_total = ms;
   if (info) *info = local;
   return st;
+}
+
+int gdm_get_history(const gdm_handle* h, int max_rows, double* idem, double* trace, double* gamma,
+                    int* branch) {
+  if (h == nullptr) return 0;
+  const int n = static_cast<int>(h->hist.size());
+  const int m = n < max_rows ? n : max_rows;
+  for (int i = 0; i < m; ++i) {
+    if (idem) idem[i] = h->hist[i].idem;
+    if (trace) trace[i] = h->hist[i].trace;
+    if (gamma) gamma[i] = h->hist[i].gamma;
+    if (branch) branch[i] = h->hist[i].branch;
+  }
+  return n;
 }
 
 gdm_status gdm_reinit(gdm_handle* h) {

@@ -19,7 +19,7 @@ enum DeviceError : uint32_t {
 constexpr int kGemmSym = 1;  // compute tiles on/above the diagonal, mirror the rest
 
 // A matrix held as FP16 integer slices plus power-of-two row scales (see gemm_sliced.cu):
-// row i = row_scale[i] * 2^-11 * sum_s slice_s[i, :] * 2^(-11 s).
+// row i = row_scale[i] * 2^-11 * sum_s slice_s[i, :] * 2^(-bits * s).
 struct SliceBuf {
   __half* data = nullptr;        // [4][rows_alloc][ld]
   double* row_scale = nullptr;   // [rows_alloc]
@@ -27,18 +27,22 @@ struct SliceBuf {
   int ld = 0;                    // elements per row in memory (multiple of 64)
   int rows_alloc = 0;
   int nslice_valid = 0;          // slices written by the last slicing pass
+  int bits = 12;                 // bits per slice after the first (9..12)
 };
 
 // Slice count and highest slice-pair order used by a product.
 struct Precision {
   int nslice = 3;
   int max_order = 3;
+  int bits = 12;   // bits per trailing slice: 12 packs more bits, 9 keeps every order's FP32
+                   // accumulator below 2^24 (exact) up to K ~ 8192
 };
 
 struct SlicedGemmArgs {
   int M = 0, N = 0, K = 0;
   int mode = 0;                       // kGemmSym
   int num_pairs = 0, nacc = 0, tmem_cols = 0;
+  int shift = 12;                     // weight of order o is 2^(-shift * o)
   int8_t pair_s[kMaxPairs] = {}, pair_t[kMaxPairs] = {}, pair_o[kMaxPairs] = {};
   const double* row_scale_a = nullptr;
   const double* row_scale_b = nullptr;
@@ -55,6 +59,10 @@ struct SlicedGemmArgs {
   uint32_t* err = nullptr;
   int tiles_n = 0;
 };
+
+// Number of kernels this library has launched since it was loaded (all threads).
+void count_launch(int k = 1);
+int64_t launch_count();
 
 int build_pairs(int nslice, int max_order, SlicedGemmArgs* a);
 cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& Bt, const Precision& prec,
@@ -88,7 +96,7 @@ cudaError_t f64_gemm(const F64GemmArgs& a, cudaStream_t stream);
 cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64_t ldx2,
                            int rows, int cols, const double* coef_dev, double ha, double hb,
                            double hc, double* Y, int64_t ldy, SliceBuf* out, int nslice,
-                           const int* skip, cudaStream_t stream);
+                           const int* skip, cudaStream_t stream, int bits = 12);
 
 // Gershgorin bounds of a symmetric n x n matrix: writes {min_i(a_ii - r_i), max_i(a_ii + r_i)}
 // into out_dev[0..1].  `partials` holds >= 2 * ceil(n / 8) doubles.
@@ -120,9 +128,9 @@ struct Trs4State {
   double coefW[3];        // W = a X + b X2 (+ c I)
   double coefX[3];        // X_next = a X + b X2 for the branches without a product
   double gemm_coef[2];    // X_next = alpha * X2 W + beta * X2
-  int branch;             // 0: 2X - X2, 1: X2, 2: F + gamma G
-  int skip_gemm;          // 1 unless branch 2
-  int skip_form_x;        // 1 when branch 2
+  int branch;             // 0: 2X - X2, 1: X2, 2: F + gamma G, 3: McWeeny X2 (3I - 2X)
+  int skip_gemm;          // 1 unless branch 2 or 3
+  int skip_form_x;        // 1 when branch 2 or 3
   int stop;               // 1: converged (X is final), 2: stalled, 3: non-finite
   int iter;
   int stall;
@@ -136,6 +144,17 @@ cudaError_t x0_coefficients(const double* bounds_dev, double* coef_dev, cudaStre
 // coef = {s, 0, 0} with s = 1 / bound[1] (Y_0 = S / c) or s = 1 / sqrt(bound[1]).
 cudaError_t scale_coefficients(const double* bounds_dev, int inv_sqrt, double* coef_dev,
                                cudaStream_t stream);
+
+// Exact FP64 diagonal of a square product: C_ii = alpha <A_i, Bt_i> + beta D_ii + diag
+// ((alpha, beta) from coef when non-null).  Run after the sliced product (see elementwise.cu).
+cudaError_t diag_fix(const double* A, int64_t lda, const double* Bt, int64_t ldb, double* C,
+                     int64_t ldc, int n, int K, double alpha, double beta, const double* D,
+                     int64_t ldd, double diag, const double* coef, cudaStream_t stream);
+
+// X <- X * target / Tr X (trace in FP64); fix_out (device, 2 doubles) = {target/Tr X - 1,
+// target/Tr X}.
+cudaError_t trace_scale(double* X, int64_t ld, int n, double target, double* fix_out,
+                        cudaStream_t stream);
 
 // Symmetrise in place: A <- (A + A^T) / 2.
 cudaError_t symmetrise(double* A, int64_t lda, int n, cudaStream_t stream);

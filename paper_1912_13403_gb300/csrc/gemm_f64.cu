@@ -91,6 +91,7 @@ cudaError_t f64_gemm(const F64GemmArgs& a, cudaStream_t stream) {
   const int tm = (a.M + TB - 1) / TB, tn = (a.N + TB - 1) / TB;
   const int grid = (a.mode & kGemmSym) ? tn * (tn + 1) / 2 : tm * tn;
   if (grid == 0) return cudaSuccess;
+  count_launch();
   f64_gemm_kernel<<<grid, 256, 0, stream>>>(a, tn);
   return cudaGetLastError();
 }

@@ -5,14 +5,16 @@
 // ntpoly_purification; the back-transform) goes through this kernel.
 //
 // Number format.  Each operand row i is stored as up to four FP16 "slices" holding integers:
-//     a_ik = sigma_i * 2^-11 * sum_s m_s[i,k] * 2^(-11 s),   |m_s| <= 2048,
-// where sigma_i is a power of two >= ||a_i||_2, so that ||m_0[i,:]||_2 <= 2^11 (+ rounding).
-// The product of two slices is accumulated by the tensor core in FP32.  Slice pairs of the same
-// order o = s + t share one TMEM accumulator; order 0 stays below 2^23 in magnitude for every
-// partial sum (Cauchy-Schwarz on the row norms), so it is exact; the higher orders are integers
-// too and are exact unless their partial sums pass 2^24, where they round at a relative weight
-// of 2^-35 or less.  The epilogue combines
-//     C_ij = alpha * sigma_i sigma_j 2^-22 * sum_o 2^(-11 o) acc_o[i,j] + beta * D_ij
+//     a_ik = sigma_i * 2^-11 * sum_s m_s[i,k] * 2^(-b s),   |m_s| <= 2048,
+// where sigma_i is a power of two >= ||a_i||_2, so that ||m_0[i,:]||_2 <= 2^11 (+ rounding), and
+// b (9..12) is the width of the trailing slices.  The product of two slices is accumulated by
+// the tensor core in FP32.  Slice pairs of the same order o = s + t share one TMEM accumulator;
+// order 0 stays below 2^23 in magnitude for every partial sum (Cauchy-Schwarz on the row
+// norms), so it is exact; the higher orders are integers too and are exact while their partial
+// sums stay below 2^24 (with b = 9 that holds for the random-walk sums of residual slices up to
+// K ~ 8192; with b = 12 the order-2 sum rounds at a relative weight of about 2^-46).  The
+// epilogue combines
+//     C_ij = alpha * sigma_i sigma_j 2^-22 * sum_o 2^(-b o) acc_o[i,j] + beta * D_ij
 // in FP64.  The operand B is given as the row slices of B^T (for the symmetric right operands
 // of this route that is B itself).
 //
@@ -20,6 +22,7 @@
 // loads all slices of a 128 x BK panel at once).  Warp 1: TMEM allocator and the single MMA
 // issuing thread.  Warps 2-5: epilogue (TMEM lanes 32*(warp%4) ...).  Symmetric mode computes
 // only tiles on or above the diagonal and writes the mirror image.
+#include <atomic>
 #include <cstdio>
 #include <mutex>
 
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                  static_cast<uint32_t>(o * kBN + c * 32),
                              r);
           tmem_wait_ld();
-          const double w = ldexp(1.0, -11 * o);
+          const double w = ldexp(1.0, -args.shift * o);
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] += w * static_cast<double>(__uint_as_float(r[j]));
         }
@@ -281,11 +284,18 @@ cudaError_t launch_cfg(const CUtensorMap& ta, const CUtensorMap& tb, const Slice
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(Cfg::kSmemBytes));
   if (e != cudaSuccess) return e;
+  count_launch();
   kern<<<grid, kThreads, Cfg::kSmemBytes, stream>>>(ta, tb, a);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // Pair list for `nslice` slices and highest order `max_order`: all (s, t) with s, t < nslice
 // and s + t <= max_order, ordered by order.
@@ -314,6 +324,8 @@ cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& B, const Precision& p
       prec.max_order > 2 * (nslice - 1))
     return cudaErrorInvalidValue;
   if (A.nslice_valid < nslice || B.nslice_valid < nslice) return cudaErrorInvalidValue;
+  if ((nslice > 1 && (A.bits != prec.bits || B.bits != prec.bits))) return cudaErrorInvalidValue;
+  args.shift = prec.bits;
   if (A.cols != B.cols) return cudaErrorInvalidValue;  // contraction length
   build_pairs(nslice, prec.max_order, &args);
   args.M = A.rows;

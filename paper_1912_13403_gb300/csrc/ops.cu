@@ -57,7 +57,7 @@ gdm_status cuda_status(cudaError_t e) {
 cudaError_t run_product(Scratch& sc, const double* A, int64_t lda, const double* Bt, int64_t ldb,
                         double* C, int64_t ldc, int m, int n, int k, int nslice, int max_order,
                         bool sym, const double* D, int64_t ldd, double alpha, double beta,
-                        const double* coef, uint32_t* err) {
+                        const double* coef, uint32_t* err, int bits = 12) {
   if (nslice == 0) {
     F64GemmArgs a;
     a.M = m;
@@ -80,10 +80,10 @@ cudaError_t run_product(Scratch& sc, const double* A, int64_t lda, const double*
   SliceBuf sa, sb;
   if (!alloc_slices(sc, sa, m, k) || !alloc_slices(sc, sb, n, k)) return cudaErrorMemoryAllocation;
   cudaError_t e = form_and_slice(A, lda, nullptr, 0, m, k, nullptr, 1, 0, 0, nullptr, 0, &sa,
-                                 nslice, nullptr, sc.s);
+                                 nslice, nullptr, sc.s, bits);
   if (e != cudaSuccess) return e;
   e = form_and_slice(Bt, ldb, nullptr, 0, n, k, nullptr, 1, 0, 0, nullptr, 0, &sb, nslice,
-                     nullptr, sc.s);
+                     nullptr, sc.s, bits);
   if (e != cudaSuccess) return e;
   SlicedGemmArgs a;
   a.mode = sym ? kGemmSym : 0;
@@ -98,7 +98,10 @@ cudaError_t run_product(Scratch& sc, const double* A, int64_t lda, const double*
   Precision p;
   p.nslice = nslice;
   p.max_order = max_order;
-  return sliced_gemm(sa, sb, p, a, sc.s);
+  p.bits = bits;
+  e = sliced_gemm(sa, sb, p, a, sc.s);
+  if (e != cudaSuccess || !sym) return e;
+  return diag_fix(A, lda, Bt, ldb, C, ldc, m, k, alpha, beta, D, ldd, 0.0, coef, sc.s);
 }
 
 bool valid_format(int nslice, int max_order) {
@@ -113,7 +116,9 @@ extern "C" {
 
 gdm_status gdm_op_product(const double* A, int64_t lda, const double* Bt, int64_t ldb, double* C,
                           int64_t ldc, int64_t m, int64_t n, int64_t k, int nslice, int max_order,
-                          int symmetric, void* stream) {
+                          int slice_bits, int symmetric, void* stream) {
+  if (slice_bits == 0) slice_bits = 12;
+  if (slice_bits < 9 || slice_bits > 12) return GDM_ERR_ARG;
   if (m < 0 || n < 0 || k < 0 || m > (1 << 20) || n > (1 << 20) || k > (1 << 20))
     return GDM_ERR_ARG;
   if (m == 0 || n == 0) return GDM_OK;
@@ -134,7 +139,7 @@ gdm_status gdm_op_product(const double* A, int64_t lda, const double* Bt, int64_
     OPCK(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
     cudaError_t e = run_product(sc, A, lda, Bt, ldb, C, ldc, static_cast<int>(m),
                                 static_cast<int>(n), static_cast<int>(k), nslice, max_order,
-                                symmetric != 0, nullptr, 0, 1.0, 0.0, nullptr, err);
+                                symmetric != 0, nullptr, 0, 1.0, 0.0, nullptr, err, slice_bits);
     if (e != cudaSuccess) return cuda_status(e);
     uint32_t herr = 0;
     OPCK(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -187,10 +192,10 @@ gdm_status gdm_op_trs4_step(double* X, int64_t ld, int64_t n64, double n_occ, in
   Trs4State host;
   OPCK(cudaMemcpyAsync(&host, st, sizeof(host), cudaMemcpyDeviceToHost, s));
   OPCK(cudaStreamSynchronize(s));
-  if (!std::isfinite(host.gamma) && host.branch == 2) return GDM_ERR_NONFINITE;
+  if (!std::isfinite(host.gamma)) return GDM_ERR_NONFINITE;
   const char* base = reinterpret_cast<const char*>(st);
-  if (host.branch == 2) {
-    // W = (4 - 2g) X + (g - 3) X^2 ; X <- X^2 W + g X^2
+  if (host.branch == 2 || host.branch == 3) {
+    // W = (4 - 2g) X + (g - 3) X^2 ; X <- X^2 W + g X^2   (McWeeny: W = 3I - 2X, X <- X^2 W)
     OPCK(form_and_slice(X, ld, X2, ld, n, n,
                         reinterpret_cast<const double*>(base + offsetof(Trs4State, coefW)), 0, 0,
                         0, W, ld, nullptr, 0, nullptr, s));

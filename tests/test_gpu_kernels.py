@@ -12,13 +12,15 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-FORMATS = {  # (nslice, max_order): relative bound (x ||a_i|| ||b_j||) at K <= ~1000
-    (0, 0): 1e-13,
-    (1, 0): 6e-3,
-    (2, 1): 6e-5,
-    (3, 2): 6e-8,
-    (3, 3): 2e-9,
-    (4, 3): 2e-9,
+FORMATS = {  # (nslice, max_order, trailing bits): bound (x ||a_i|| ||b_j||) at K <= ~1000
+    (0, 0, 12): 1e-13,
+    (1, 0, 12): 6e-3,
+    (2, 1, 12): 6e-5,
+    (3, 2, 12): 6e-8,
+    (3, 3, 12): 2e-9,
+    (4, 3, 12): 2e-9,
+    (3, 3, 9): 2e-8,
+    (4, 3, 9): 1e-10,
 }
 
 
@@ -51,12 +53,12 @@ def test_product_matches_fp64(g, fmt, m, n, k):
     A[0] *= 1e-3      # rows of very different scale
     Bt[-1] *= 1e4
     C = torch.zeros((m, n), dtype=torch.float64, device="cuda")
-    g.op_product(_dev(A), _dev(Bt), C, nslice=fmt[0], max_order=fmt[1])
+    g.op_product(_dev(A), _dev(Bt), C, nslice=fmt[0], max_order=fmt[1], slice_bits=fmt[2])
     torch.cuda.synchronize()
     _check_product(C.cpu().numpy(), A, Bt, FORMATS[fmt])
 
 
-@pytest.mark.parametrize("fmt", [(0, 0), (3, 3), (2, 1)])
+@pytest.mark.parametrize("fmt", [(0, 0, 12), (3, 3, 12), (2, 1, 12), (4, 3, 9)])
 @pytest.mark.parametrize("n", [128, 300, 515])
 def test_symmetric_product_is_exactly_symmetric(g, fmt, n):
     rng = np.random.default_rng(n)
@@ -64,7 +66,7 @@ def test_symmetric_product_is_exactly_symmetric(g, fmt, n):
     X = X + X.T
     C = torch.full((n, n), np.nan, dtype=torch.float64, device="cuda")
     Xd = _dev(X)
-    g.op_product(Xd, Xd, C, nslice=fmt[0], max_order=fmt[1], symmetric=True)
+    g.op_product(Xd, Xd, C, nslice=fmt[0], max_order=fmt[1], symmetric=True, slice_bits=fmt[2])
     Cn = C.cpu().numpy()
     assert np.all(np.isfinite(Cn)), "unwritten entries"
     assert np.array_equal(Cn, Cn.T)
@@ -80,7 +82,7 @@ def test_product_leading_dimensions(g):
     Cbig = torch.zeros((150, 256), dtype=torch.float64, device="cuda")
     C = Cbig[:, :170]
     g.op_product(A, Bt, C, nslice=3, max_order=3)
-    _check_product(C.cpu().numpy(), Abig[:, :333], Bbig[:, :333], FORMATS[(3, 3)])
+    _check_product(C.cpu().numpy(), Abig[:, :333], Bbig[:, :333], FORMATS[(3, 3, 12)])
     assert torch.all(Cbig[:, 170:] == 0)
 
 
@@ -95,6 +97,21 @@ def test_product_slice_integer_exactness(g):
     C = torch.zeros((256, 256), dtype=torch.float64, device="cuda")
     g.op_product(_dev(A), _dev(Bt), C, nslice=1, max_order=0)
     assert np.array_equal(C.cpu().numpy(), A @ Bt.T)
+
+
+def test_symmetric_diagonal_is_exact(g):
+    """The diagonal of a symmetric product is recomputed in FP64: for X X with X a projector
+    (rows of the two factors identical) it matches numpy to rounding, with no accumulator bias."""
+    from workloads import haar_orthogonal
+    rng = np.random.default_rng(6)
+    n, N = 640, 160
+    Q = haar_orthogonal(rng, n)
+    P = Q[:, :N] @ Q[:, :N].T
+    C = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    Pd = _dev(P)
+    g.op_product(Pd, Pd, C, nslice=3, max_order=3, symmetric=True)
+    d = np.diag(C.cpu().numpy()) - np.einsum("ij,ij->i", P, P)
+    assert np.abs(d).max() <= 1e-15 and abs(d.sum()) <= 1e-13
 
 
 def test_gershgorin_matches_oracle(g):
@@ -123,6 +140,9 @@ def test_trs4_step_matches_oracle(g, fmt, tol, n, n_occ, spread):
     gamma, br = g.op_trs4_step(Xd, n_occ, nslice=fmt[0], max_order=fmt[1])
     names = {0: "2X-X2", 1: "X2", 2: "F+gG"}
     assert names[br] == bre
-    assert abs(gamma - ge) <= 1e-9 * max(1.0, abs(ge))
+    # gamma = (N - Tr F)/Tr G amplifies product errors by (N + |Tr F|)/|Tr G|
+    _, trF, trG = steps.trs4_gamma(X, n_occ)
+    amp = (n_occ + abs(trF)) / abs(trG)
+    assert abs(gamma - ge) <= max(tol, 1e-13) * amp * max(1.0, abs(ge))
     err = np.linalg.norm(Xd.cpu().numpy() - Xe) / np.linalg.norm(Xe)
     assert err <= tol

@@ -147,5 +147,6 @@ def test_error_paths(g):
         with pytest.raises(g.GdmError) as ei:
             h.set_hamiltonian(bad)
         assert ei.value.status == g.GDM_ERR_NONFINITE
-        assert g.gdm_set_slices(h._h, 3, 5, 1) == g.GDM_ERR_ARG
-        assert g.gdm_set_slices(h._h, 3, 1, 2) == g.GDM_ERR_ARG
+        assert g.gdm_set_slices(h._h, 3, 5, 1, 0) == g.GDM_ERR_ARG
+        assert g.gdm_set_slices(h._h, 3, 1, 2, 0) == g.GDM_ERR_ARG
+        assert g.gdm_set_slices(h._h, 3, 3, 3, 13) == g.GDM_ERR_ARG

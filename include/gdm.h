@@ -194,6 +194,26 @@ gdm_status gdm_op_gershgorin(const double* A, int64_t lda, int64_t n, double* bo
 gdm_status gdm_op_trs4_step(double* X, int64_t ld, int64_t n, double n_occ, int nslice,
                             int max_order, double* gamma_host, int* branch_host, void* stream);
 
+/* gdm_op_product without device allocation.  Same arguments and results as gdm_op_product,
+ * for callers that cannot call cudaMalloc: code running while another component (a framework's
+ * caching allocator, a memory pool sized to the whole GPU) owns the device memory, or code in a
+ * latency-bound loop that cannot take an allocation's cost and implicit synchronisation.  This
+ * operation has no counterpart in the paper; it is a deployment variant of the product.
+ *   - Scratch (the FP16 slices, row scales and an error word) is one fixed array in the library,
+ *     about 16 MiB, held by every GPU that loads the library until the process exits.
+ *   - Limit: m, n and k are each at most 1024 and nslice at most 4; larger sizes return
+ *     GDM_ERR_ARG (use gdm_op_product for them).
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call shares the array and leaves its contents behind; each call clears the parts it
+ *     relies on.  Calls whose GPU work overlaps (other host threads, other streams) race on the
+ *     array: serialise them.  Each call synchronises `stream` before returning.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
+gdm_status gdm_op_product_noalloc(const double* A, int64_t lda, const double* Bt, int64_t ldb,
+                                  double* C, int64_t ldc, int64_t m, int64_t n, int64_t k,
+                                  int nslice, int max_order, int slice_bits, int symmetric,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,8 @@ _decl("gdm_status_string", ctypes.c_char_p, [_int])
 _decl("gdm_last_error", ctypes.c_char_p, [_vp])
 _decl("gdm_op_product", _int, [_vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _int, _int,
                                _int, _int, _vp])
+_decl("gdm_op_product_noalloc", _int, [_vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _int,
+                                       _int, _int, _int, _vp])
 _decl("gdm_op_gershgorin", _int, [_vp, _i64, _i64, _dp, _vp])
 _decl("gdm_op_trs4_step", _int, [_vp, _i64, _i64, _dbl, _int, _int, _dp,
                                  ctypes.POINTER(_int), _vp])
@@ -230,6 +232,21 @@ def op_product(A, Bt, C, nslice=3, max_order=3, symmetric=False, stream=None, sl
                         _stream_ptr(stream))
     if st != GDM_OK:
         raise GdmError(st, "gdm_op_product")
+    return C
+
+
+def op_product_noalloc(A, Bt, C, nslice=3, max_order=3, symmetric=False, stream=None,
+                       slice_bits=0):
+    """C = A @ Bt.T like op_product, with the library's fixed scratch array instead of device
+    allocations (m, n, k <= 1024)."""
+    pa, lda, _ = _buf(A)
+    pb, ldb, _ = _buf(Bt)
+    pc, ldc, _ = _buf(C)
+    st = gdm_op_product_noalloc(pa, lda, pb, ldb, pc, ldc, A.shape[0], Bt.shape[0], A.shape[1],
+                                nslice, max_order, slice_bits, int(bool(symmetric)),
+                                _stream_ptr(stream))
+    if st != GDM_OK:
+        raise GdmError(st, "gdm_op_product_noalloc")
     return C
 
 

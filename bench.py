@@ -380,6 +380,7 @@ def run_ours(args):
                      "trace_err": info["trace_err"], "trace_err_raw": info["trace_err_raw"],
                      "ns_iters": info["ns_iters"], "purif_iters": info["purif_iters"]},
         "tflops_tensor_pipe": achieved,
+        "gemm_ms_per_step": prof_ms / args.steps,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "traffic": None,
                      "kernel": "sliced_gemm_kernel (tcgen05 kind::f16, all launches of the step)",

@@ -79,6 +79,150 @@ __global__ void __launch_bounds__(kRowThreads)
   }
 }
 
+// ---- integer slicing helpers: no FP64 arithmetic (GB300 runs FP64 at ~2 DFMA/clk/SM) ----
+
+// y truncated to FP32 from its bit pattern (integer ops only); 0 below FP32's normal range,
+// inf/NaN kept.  Used for the row norm, which only has to bound ||y|| from above.
+__device__ __forceinline__ float trunc_to_float(double y) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(y));
+  const int E = static_cast<int>((b >> 52) & 0x7FF);
+  const unsigned sign = static_cast<unsigned>(b >> 63) << 31;
+  if (E == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (((b << 12) != 0) ? 1u : 0u));
+  const int ef = E - 1023 + 127;
+  if (E == 0 || ef <= 0) return 0.0f;
+  if (ef >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | (static_cast<unsigned>(ef) << 23) |
+                         static_cast<unsigned>((b >> 29) & 0x7FFFFF));
+}
+
+// round(y * 2^p) as a signed 64-bit integer (nearest, ties to even), p chosen by the caller so
+// that |y * 2^p| < 2^62; exact from the bit pattern.
+__device__ __forceinline__ long long fixed_point(double y, int p) {
+  const long long b = __double_as_longlong(y);
+  const int E = static_cast<int>((b >> 52) & 0x7FF);
+  long long mant = b & ((1LL << 52) - 1);
+  int Ee = E;
+  if (E != 0) mant |= (1LL << 52); else Ee = 1;
+  const int sh = Ee - 1075 + p;
+  long long q;
+  if (sh >= 0) {
+    q = mant << sh;
+  } else if (sh > -63) {
+    const int r = -sh;
+    q = mant >> r;
+    const long long rem = mant - (q << r);
+    const long long half = 1LL << (r - 1);
+    if (rem > half || (rem == half && (q & 1))) ++q;
+  } else {
+    q = 0;
+  }
+  return (b < 0) ? -q : q;
+}
+
+// Single-pass slicing for rows of up to 2 * 256 * MAXV columns.  The formed row stays in
+// registers; loads are 16 B, slice stores 4 B per thread.  The row norm is accumulated in FP32
+// from truncated values and enlarged by 0.2% before the power-of-two scale is taken, so the
+// scale bounds the true norm; the slices are the balanced base-2^bits digits of
+// round(y * 2^(11 - e + bits (nslice - 1))), computed with integer operations.  FP64 arithmetic
+// is used only to form y when (a, b, c) is not (1, 0, 0).  Requires an even column count and
+// 16-byte aligned rows (checked by the host wrapper).
+template <int MAXV>
+__global__ void __launch_bounds__(kRowThreads)
+    form_slice_vec_kernel(const double* __restrict__ X, int64_t ldx,
+                          const double* __restrict__ X2, int64_t ldx2, int rows, int cols,
+                          const double* __restrict__ coef_dev, double ha, double hb, double hc,
+                          double* Y, int64_t ldy, __half* out, double* out_scale, int64_t out_ld,
+                          int64_t plane, int nslice, const int* skip, int bits) {
+  __shared__ float redf[32];
+  __shared__ int shift_sh;
+  if (skip != nullptr && *skip != 0) return;
+  const int row = blockIdx.x;
+  if (row >= rows) return;
+  double a = ha, b = hb, c = hc;
+  if (coef_dev != nullptr) {
+    a = coef_dev[0];
+    b = coef_dev[1];
+    c = coef_dev[2];
+  }
+  const bool plain = (a == 1.0) && (X2 == nullptr || b == 0.0) && (c == 0.0);
+  const int npairs = cols >> 1;
+  const double2* xr = reinterpret_cast<const double2*>(X + row * ldx);
+  const double2* x2r = (X2 != nullptr) ? reinterpret_cast<const double2*>(X2 + row * ldx2)
+                                        : nullptr;
+  double2* yr = (Y != nullptr) ? reinterpret_cast<double2*>(Y + row * ldy) : nullptr;
+  double2 v[MAXV];
+  float ss = 0.0f;
+#pragma unroll
+  for (int i = 0; i < MAXV; ++i) {
+    const int p = threadIdx.x + i * kRowThreads;
+    v[i] = make_double2(0.0, 0.0);
+    if (p < npairs) {
+      double2 y = xr[p];
+      if (!plain) {
+        y.x *= a;
+        y.y *= a;
+        if (x2r != nullptr) {
+          const double2 x2 = x2r[p];
+          y.x = fma(b, x2.x, y.x);
+          y.y = fma(b, x2.y, y.y);
+        }
+        if (2 * p == row) y.x += c;
+        if (2 * p + 1 == row) y.y += c;
+      }
+      if (yr != nullptr) yr[p] = y;
+      const float f0 = trunc_to_float(y.x), f1 = trunc_to_float(y.y);
+      ss = fmaf(f0, f0, fmaf(f1, f1, ss));
+      v[i] = y;
+    }
+  }
+  if (out == nullptr || nslice <= 0) return;
+  // block sum of ss (fixed order)
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) redf[wid] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.0f;
+      for (int w = 0; w < kRowThreads / 32; ++w) t += redf[w];
+      int e = 0, p = 0;
+      if (t > 0.0f && isfinite(t)) {
+        frexpf(sqrtf(t * 1.002f) * 1.0001f, &e);  // 2^e > ||y|| with margin
+        p = 11 - e + bits * (nslice - 1);
+        out_scale[row] = ldexp(1.0, e);
+      } else {
+        out_scale[row] = isfinite(t) ? 1.0 : __longlong_as_double(0x7FF8000000000000LL);
+        p = -100000;  // all-zero slices (zero row, or a NaN/Inf row flagged by the scale)
+      }
+      shift_sh = p;
+    }
+    __syncthreads();
+  }
+  const int p2 = shift_sh;
+  const long long H = 1LL << (bits - 1);
+  const long long MASK = (1LL << bits) - 1;
+  __half2* orow = reinterpret_cast<__half2*>(out + row * out_ld);
+  const int64_t plane2 = plane >> 1;
+#pragma unroll
+  for (int i = 0; i < MAXV; ++i) {
+    const int p = threadIdx.x + i * kRowThreads;
+    if (p < npairs) {
+      long long n0 = (p2 > -1000) ? fixed_point(v[i].x, p2) : 0;
+      long long n1 = (p2 > -1000) ? fixed_point(v[i].y, p2) : 0;
+      for (int s = nslice - 1; s >= 1; --s) {
+        const long long d0 = ((n0 + H) & MASK) - H, d1 = ((n1 + H) & MASK) - H;
+        orow[s * plane2 + p] = __halves2half2(__int2half_rn(static_cast<int>(d0)),
+                                              __int2half_rn(static_cast<int>(d1)));
+        n0 = (n0 - d0) >> bits;
+        n1 = (n1 - d1) >> bits;
+      }
+      orow[p] = __halves2half2(__int2half_rn(static_cast<int>(n0)),
+                               __int2half_rn(static_cast<int>(n1)));
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // Gershgorin: lo_i = a_ii - sum_{j != i} |a_ij|, hi_i = a_ii + sum_{j != i} |a_ij|
 // ------------------------------------------------------------------------------------------
@@ -408,10 +552,29 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
   } else {
     nslice = 0;
   }
-  count_launch();
-  form_slice_kernel<<<rows, kRowThreads, 0, stream>>>(X, ldx, X2, ldx2, rows, cols, coef_dev, ha,
-                                                      hb, hc, Y, ldy, od, osc, old, plane,
-                                                      nslice, skip, ldexp(1.0, bits));
+  const double step = ldexp(1.0, bits);
+  const bool aligned =
+      (cols % 2 == 0) && (ldx % 2 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0) &&
+      (X2 == nullptr || ((ldx2 % 2 == 0) && (reinterpret_cast<uintptr_t>(X2) % 16 == 0))) &&
+      (Y == nullptr || ((ldy % 2 == 0) && (reinterpret_cast<uintptr_t>(Y) % 16 == 0))) &&
+      (od == nullptr || ((old % 2 == 0) && (plane % 2 == 0) &&
+                         (reinterpret_cast<uintptr_t>(od) % 4 == 0)));
+  if (aligned && cols <= 2 * kRowThreads * 4) {
+    count_launch();
+    form_slice_vec_kernel<4><<<rows, kRowThreads, 0, stream>>>(
+        X, ldx, X2, ldx2, rows, cols, coef_dev, ha, hb, hc, Y, ldy, od, osc, old, plane, nslice,
+        skip, bits);
+  } else if (aligned && cols <= 2 * kRowThreads * 16) {
+    count_launch();
+    form_slice_vec_kernel<16><<<rows, kRowThreads, 0, stream>>>(
+        X, ldx, X2, ldx2, rows, cols, coef_dev, ha, hb, hc, Y, ldy, od, osc, old, plane, nslice,
+        skip, bits);
+  } else {
+    count_launch();
+    form_slice_kernel<<<rows, kRowThreads, 0, stream>>>(X, ldx, X2, ldx2, rows, cols, coef_dev,
+                                                        ha, hb, hc, Y, ldy, od, osc, old, plane,
+                                                        nslice, skip, step);
+  }
   return cudaGetLastError();
 }
 

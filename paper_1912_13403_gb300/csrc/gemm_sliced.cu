@@ -73,6 +73,54 @@ __device__ __forceinline__ void upper_tile(int idx, int nt, int& ti, int& tj) {
   tj = i + idx;
 }
 
+// ---- epilogue arithmetic without FP64 instructions ----------------------------------------
+// Every accumulator holds an integer value: products of integer slices, summed in FP32 (exact
+// below 2^24, and FP32 values at or above 2^24 are integers too).
+
+// int64 value of an integer-valued FP32 given by its bits.
+__device__ __forceinline__ long long f32_integer(uint32_t bits) {
+  const int E = static_cast<int>((bits >> 23) & 0xFF);
+  if (E < 127) return 0;  // |v| < 1: the value is 0
+  const long long m = static_cast<long long>((bits & 0x7FFFFFu) | 0x800000u);
+  const int sh = E - 150;
+  const long long v = (sh >= 0) ? (m << sh) : (m >> (-sh));
+  return (bits >> 31) ? -v : v;
+}
+
+// exponent of a power-of-two double (the row scales)
+__device__ __forceinline__ int pow2_exponent(double s) {
+  return static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(s)) >> 52) &
+                          0x7FF) - 1023;
+}
+
+// T * 2^ex as a double, rounded to nearest even, built from integer operations (|T| < 2^63;
+// results below the normal range flush to 0).
+__device__ __forceinline__ double scaled_int_to_double(long long T, int ex) {
+  if (T == 0) return 0.0;
+  const unsigned long long sign = (T < 0) ? (1ULL << 63) : 0ULL;
+  unsigned long long u = (T < 0) ? static_cast<unsigned long long>(-T)
+                                 : static_cast<unsigned long long>(T);
+  const int msb = 63 - __clzll(u);
+  int e = msb + ex;
+  unsigned long long mant;
+  if (msb > 52) {
+    const int r = msb - 52;
+    mant = u >> r;
+    const unsigned long long rem = u & ((1ULL << r) - 1);
+    const unsigned long long half = 1ULL << (r - 1);
+    if (rem > half || (rem == half && (mant & 1ULL))) ++mant;
+    if (mant == (1ULL << 53)) {
+      mant >>= 1;
+      ++e;
+    }
+  } else {
+    mant = u << (52 - msb);
+  }
+  if (e + 1023 <= 0) return 0.0;
+  return __longlong_as_double(static_cast<long long>(
+      sign | (static_cast<unsigned long long>(e + 1023) << 52) | (mant & ((1ULL << 52) - 1))));
+}
+
 template <int NSLICE, int BK, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     sliced_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
@@ -185,21 +233,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         beta = args.coef[1];
       }
       const double sa = (grow < args.M) ? args.row_scale_a[grow] : 0.0;
+      const bool sa_ok = isfinite(sa);
+      const int ea = pow2_exponent(sa);
+      const int ex_base = ea - 22 - args.shift * (args.nacc - 1);
+      const bool unit_alpha = (alpha == 1.0);
       // per-warp staging tile (32 x 33 doubles) in the now idle pipeline buffers
       double* stage = reinterpret_cast<double*>(smem) + q * (32 * 33);
       for (int c = 0; c < kBN / 32; ++c) {
-        double v[32];
+        long long T[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = 0.0;
-        for (int o = args.nacc - 1; o >= 0; --o) {
+        for (int j = 0; j < 32; ++j) T[j] = 0;
+        for (int o = 0; o < args.nacc; ++o) {  // Horner in 2^shift, highest order first
           uint32_t r[32];
           tmem_ld_32x32b_x32(tbase + (static_cast<uint32_t>(q * 32) << 16) +
                                  static_cast<uint32_t>(o * kBN + c * 32),
                              r);
           tmem_wait_ld();
-          const double w = ldexp(1.0, -args.shift * o);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] += w * static_cast<double>(__uint_as_float(r[j]));
+          for (int j = 0; j < 32; ++j) T[j] = (T[j] << args.shift) + f32_integer(r[j]);
         }
         const int c0 = tj * kBN + c * 32;
         // thread = row: finished values; mirror / transposed writes are coalesced here
@@ -208,7 +259,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int gcol = c0 + j;
           double val = 0.0;
           if (grow < args.M && gcol < args.N) {
-            val = alpha * v[j] * sa * args.row_scale_b[gcol] * 0x1p-22;
+            const double sb = args.row_scale_b[gcol];
+            if (sa_ok && isfinite(sb)) {
+              val = scaled_int_to_double(T[j], ex_base + pow2_exponent(sb));
+              if (!unit_alpha) val *= alpha;
+            } else {
+              val = sa * sb;  // a NaN / Inf row scale marks a non-finite input row
+            }
             if (args.D != nullptr) val += beta * args.D[static_cast<int64_t>(gcol) * args.ldd + grow];
             if (grow == gcol) val += args.diag;
             if (sym && grow < gcol) args.C[static_cast<int64_t>(gcol) * args.ldc + grow] = val;

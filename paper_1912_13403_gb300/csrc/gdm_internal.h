@@ -57,7 +57,7 @@ struct SlicedGemmArgs {
   const double* coef = nullptr;       // optional device {alpha, beta}
   const int* skip = nullptr;          // optional device flag: non-zero -> no-op launch
   uint32_t* err = nullptr;
-  int tiles_n = 0;
+  int tiles_n = 0, tiles_m = 0;
 };
 
 // Number of kernels this library has launched since it was loaded (all threads).

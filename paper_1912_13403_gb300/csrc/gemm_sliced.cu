@@ -18,10 +18,14 @@
 // in FP64.  The operand B is given as the row slices of B^T (for the symmetric right operands
 // of this route that is B itself).
 //
-// Kernel shape: one CTA per 128x128 output tile, 6 warps.  Warp 0: TMA producer (a 3-D box
-// loads all slices of a 128 x BK panel at once).  Warp 1: TMEM allocator and the single MMA
-// issuing thread.  Warps 2-5: epilogue (TMEM lanes 32*(warp%4) ...).  Symmetric mode computes
-// only tiles on or above the diagonal and writes the mirror image.
+// Kernel shape: persistent, one CTA per SM, each CTA walks the 128x128 output tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  10 warps.  Warp 0: TMA producer (a 3-D box loads all
+// slices of a 128 x BK panel at once); its stage ring runs on across tiles, so the next tile's
+// operands stream in while the current tile's epilogue runs.  Warp 1: TMEM allocator and the
+// single MMA-issuing thread; it waits for the epilogue to release the accumulators before the
+// next tile.  Warps 2-9: epilogue, two warps per TMEM lane quarter (32*(warp%4) ...), each
+// covering 64 of the 128 columns.  Symmetric mode computes only tiles on or above the diagonal
+// and writes the mirror image.
 #include <atomic>
 #include <cstdio>
 #include <mutex>
@@ -35,13 +39,16 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBN = 128;
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr int kStageCols = 8;  // epilogue staging: 32 rows x 8 columns per warp
 
 template <int NSLICE, int BK, int STAGES>
 struct GemmCfg {
   static constexpr uint32_t kTileBytes = kBM * BK * 2;                // one slice panel
   static constexpr uint32_t kStageBytes = 2u * NSLICE * kTileBytes;   // A and B panels
-  static constexpr uint32_t kSmemBytes = STAGES * kStageBytes + 1024;  // + alignment slack
+  static constexpr uint32_t kStagingBytes = kEpiWarps * 32 * (kStageCols + 1) * 8;
+  static constexpr uint32_t kSmemBytes = STAGES * kStageBytes + kStagingBytes + 1024;
   static constexpr uint32_t kSwizzleBytes = BK * 2;                   // 128 or 64
   static_assert(BK == 64 || BK == 32, "BK must be 64 (128B swizzle) or 32 (64B swizzle)");
   static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
@@ -129,7 +136,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
-  __shared__ __align__(8) uint64_t accum_bar;
+  __shared__ __align__(8) uint64_t acc_full_bar;
+  __shared__ __align__(8) uint64_t acc_empty_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
 
@@ -137,15 +145,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  double* staging_all = reinterpret_cast<double*>(smem + STAGES * Cfg::kStageBytes);
 
   const bool sym = (args.mode & kGemmSym) != 0;
-  int ti, tj;
-  if (sym) {
-    upper_tile(blockIdx.x, args.tiles_n, ti, tj);
-  } else {
-    ti = blockIdx.x / args.tiles_n;
-    tj = blockIdx.x % args.tiles_n;
-  }
+  const int tn = args.tiles_n;
+  const int ntiles = sym ? tn * (tn + 1) / 2 : args.tiles_m * tn;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const uint32_t ncols = static_cast<uint32_t>(args.tmem_cols);
@@ -155,7 +159,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&accum_bar, 1);
+    mbar_init(&acc_full_bar, 1);
+    mbar_init(&acc_empty_bar, kEpiWarps);
     abort_flag = 0;
     fence_barrier_init();
   }
@@ -171,24 +176,32 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- TMA producer ----------------
+      // ---------------- TMA producer: one stage ring across all tiles of this CTA -----------
       tma_prefetch_desc(&tmA);
       tma_prefetch_desc(&tmB);
-      int issued = 0;
-      for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (kb / STAGES) & 1u;
-        if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1u, args.err, &abort_flag)) break;
-        mbar_arrive_expect_tx(&full_bar[s], Cfg::kStageBytes);
-        uint8_t* st = smem + s * Cfg::kStageBytes;
-        tma_load_3d(st, &tmA, &full_bar[s], kb * BK, ti * kBM, 0);
-        tma_load_3d(st + NSLICE * Cfg::kTileBytes, &tmB, &full_bar[s], kb * BK, tj * kBN, 0);
-        ++issued;
+      int it = 0;
+      bool stop = false;
+      for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
+        int ti, tj;
+        if (sym) upper_tile(tile, tn, ti, tj);
+        else { ti = tile / tn; tj = tile % tn; }
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1u, args.err, &abort_flag)) {
+            stop = true;
+            break;
+          }
+          mbar_arrive_expect_tx(&full_bar[s], Cfg::kStageBytes);
+          uint8_t* st = smem + s * Cfg::kStageBytes;
+          tma_load_3d(st, &tmA, &full_bar[s], kb * BK, ti * kBM, 0);
+          tma_load_3d(st + NSLICE * Cfg::kTileBytes, &tmB, &full_bar[s], kb * BK, tj * kBN, 0);
+        }
       }
-      if (abort_flag) {
+      if (stop) {
         // let copies already in flight land before the CTA can exit
-        for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-          mbar_wait_bounded(&full_bar[kb % STAGES], (kb / STAGES) & 1u, nullptr, nullptr,
+        for (int j = (it > STAGES ? it - STAGES : 0); j < it; ++j)
+          mbar_wait_bounded(&full_bar[j % STAGES], (j / STAGES) & 1u, nullptr, nullptr,
                             100000000ull);
       }
     }
@@ -196,92 +209,124 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---------------- MMA issuer (one thread) ----------------
       constexpr uint32_t idesc = idesc_f16_f32(kBM, kBN);
-      uint32_t started = 0;
-      for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (kb / STAGES) & 1u;
-        if (!mbar_wait_bounded(&full_bar[s], ph, args.err, &abort_flag)) break;
-        tc_fence_after();
-        const uint32_t a0 = smem_u32(smem + s * Cfg::kStageBytes);
-        const uint32_t b0 = a0 + NSLICE * Cfg::kTileBytes;
-        for (int p = 0; p < args.num_pairs; ++p) {
-          const int sa = args.pair_s[p], sb = args.pair_t[p], o = args.pair_o[p];
-          const uint32_t d = tbase + static_cast<uint32_t>(o * kBN);
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t ad = smem_desc(a0 + sa * Cfg::kTileBytes + kk * 32, BK);
-            const uint64_t bd = smem_desc(b0 + sb * Cfg::kTileBytes + kk * 32, BK);
-            umma_f16(d, ad, bd, idesc, (started >> o) & 1u);
-            started |= 1u << o;
-          }
+      int it = 0, tcount = 0;
+      bool stop = false;
+      for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x, ++tcount) {
+        if (tcount > 0 &&
+            !mbar_wait_bounded(&acc_empty_bar, (tcount - 1) & 1u, args.err, &abort_flag)) {
+          stop = true;
+          break;
         }
-        umma_commit(&empty_bar[s]);  // stage reusable once these MMAs have read it
+        tc_fence_after();
+        uint32_t started = 0;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!mbar_wait_bounded(&full_bar[s], ph, args.err, &abort_flag)) {
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(smem + s * Cfg::kStageBytes);
+          const uint32_t b0 = a0 + NSLICE * Cfg::kTileBytes;
+          for (int p = 0; p < args.num_pairs; ++p) {
+            const int sa = args.pair_s[p], sb = args.pair_t[p], o = args.pair_o[p];
+            const uint32_t d = tbase + static_cast<uint32_t>(o * kBN);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint64_t ad = smem_desc(a0 + sa * Cfg::kTileBytes + kk * 32, BK);
+              const uint64_t bd = smem_desc(b0 + sb * Cfg::kTileBytes + kk * 32, BK);
+              umma_f16(d, ad, bd, idesc, (started >> o) & 1u);
+              started |= 1u << o;
+            }
+          }
+          umma_commit(&empty_bar[s]);  // stage reusable once these MMAs have read it
+        }
+        umma_commit(&acc_full_bar);  // accumulators of this tile final (also on abort)
       }
-      umma_commit(&accum_bar);  // all accumulators final (also on the abort path)
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
-    const int r0 = ti * kBM + q * 32;
-    const int grow = r0 + lane;
-    const bool ok = mbar_wait_bounded(&accum_bar, 0, args.err, &abort_flag);
-    tc_fence_after();
-    if (ok && !abort_flag) {
-      double alpha = args.alpha, beta = args.beta;
-      if (args.coef != nullptr) {
-        alpha = args.coef[0];
-        beta = args.coef[1];
-      }
+    // ---------------- epilogue (warps 2..9) ----------------
+    const int q = warp & 3;          // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;  // which 64 of the 128 columns
+    double* stage = staging_all + (warp - 2) * (32 * (kStageCols + 1));
+    double alpha = args.alpha, beta = args.beta;
+    if (args.coef != nullptr) {
+      alpha = args.coef[0];
+      beta = args.coef[1];
+    }
+    const bool unit_alpha = (alpha == 1.0);
+    int tcount = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
+      int ti, tj;
+      if (sym) upper_tile(tile, tn, ti, tj);
+      else { ti = tile / tn; tj = tile % tn; }
+      const bool ok = mbar_wait_bounded(&acc_full_bar, tcount & 1u, args.err, &abort_flag);
+      tc_fence_after();
+      if (!ok || abort_flag) break;
+      const int r0 = ti * kBM + q * 32;
+      const int grow = r0 + lane;
       const double sa = (grow < args.M) ? args.row_scale_a[grow] : 0.0;
       const bool sa_ok = isfinite(sa);
-      const int ea = pow2_exponent(sa);
-      const int ex_base = ea - 22 - args.shift * (args.nacc - 1);
-      const bool unit_alpha = (alpha == 1.0);
-      // per-warp staging tile (32 x 33 doubles) in the now idle pipeline buffers
-      double* stage = reinterpret_cast<double*>(smem) + q * (32 * 33);
-      for (int c = 0; c < kBN / 32; ++c) {
+      const int ex_base = pow2_exponent(sa) - 22 - args.shift * (args.nacc - 1);
+      for (int c = 0; c < 2; ++c) {
+        const int ccol = half * 64 + c * 32;  // column offset inside the tile
         long long T[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) T[j] = 0;
-        for (int o = 0; o < args.nacc; ++o) {  // Horner in 2^shift, highest order first
+        for (int o = 0; o < args.nacc; ++o) {  // Horner in 2^shift, order 0 first
           uint32_t r[32];
           tmem_ld_32x32b_x32(tbase + (static_cast<uint32_t>(q * 32) << 16) +
-                                 static_cast<uint32_t>(o * kBN + c * 32),
+                                 static_cast<uint32_t>(o * kBN + ccol),
                              r);
           tmem_wait_ld();
 #pragma unroll
           for (int j = 0; j < 32; ++j) T[j] = (T[j] << args.shift) + f32_integer(r[j]);
         }
-        const int c0 = tj * kBN + c * 32;
-        // thread = row: finished values; mirror / transposed writes are coalesced here
+        if (c == 1) {
+          // every TMEM read of this warp for this tile is done: release the accumulators early
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty_bar);
+        }
+        const int c0 = tj * kBN + ccol;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int gcol = c0 + j;
-          double val = 0.0;
-          if (grow < args.M && gcol < args.N) {
-            const double sb = args.row_scale_b[gcol];
-            if (sa_ok && isfinite(sb)) {
-              val = scaled_int_to_double(T[j], ex_base + pow2_exponent(sb));
-              if (!unit_alpha) val *= alpha;
-            } else {
-              val = sa * sb;  // a NaN / Inf row scale marks a non-finite input row
+        for (int sc = 0; sc < 32 / kStageCols; ++sc) {
+          // thread = row: finished values; mirror / transposed writes are coalesced here
+#pragma unroll
+          for (int jj = 0; jj < kStageCols; ++jj) {
+            const int j = sc * kStageCols + jj;
+            const int gcol = c0 + j;
+            double val = 0.0;
+            if (grow < args.M && gcol < args.N) {
+              const double sb = args.row_scale_b[gcol];
+              if (sa_ok && isfinite(sb)) {
+                val = scaled_int_to_double(T[j], ex_base + pow2_exponent(sb));
+                if (!unit_alpha) val *= alpha;
+              } else {
+                val = sa * sb;  // a NaN / Inf row scale marks a non-finite input row
+              }
+              if (args.D != nullptr)
+                val += beta * args.D[static_cast<int64_t>(gcol) * args.ldd + grow];
+              if (grow == gcol) val += args.diag;
+              if (sym && grow < gcol) args.C[static_cast<int64_t>(gcol) * args.ldc + grow] = val;
+              if (args.Ct != nullptr) args.Ct[static_cast<int64_t>(gcol) * args.ldct + grow] = val;
             }
-            if (args.D != nullptr) val += beta * args.D[static_cast<int64_t>(gcol) * args.ldd + grow];
-            if (grow == gcol) val += args.diag;
-            if (sym && grow < gcol) args.C[static_cast<int64_t>(gcol) * args.ldc + grow] = val;
-            if (args.Ct != nullptr) args.Ct[static_cast<int64_t>(gcol) * args.ldct + grow] = val;
+            stage[lane * (kStageCols + 1) + jj] = val;
           }
-          stage[lane * 33 + j] = val;
+          __syncwarp();
+          // 4 rows x 8 columns per store instruction: 64-byte row segments
+          const int cc = lane % kStageCols;
+          const int gcol = c0 + sc * kStageCols + cc;
+#pragma unroll
+          for (int rr = lane / kStageCols; rr < 32; rr += 32 / kStageCols) {
+            const int row = r0 + rr;
+            if (row < args.M && gcol < args.N && (!sym || row <= gcol))
+              args.C[static_cast<int64_t>(row) * args.ldc + gcol] =
+                  stage[rr * (kStageCols + 1) + cc];
+          }
+          __syncwarp();
         }
-        __syncwarp();
-        // thread = column: direct writes, 32 consecutive doubles per row
-        const int gcol = c0 + lane;
-        for (int rr = 0; rr < 32; ++rr) {
-          const int row = r0 + rr;
-          if (row < args.M && gcol < args.N && (!sym || row <= gcol))
-            args.C[static_cast<int64_t>(row) * args.ldc + gcol] = stage[rr * 33 + lane];
-        }
-        __syncwarp();
       }
     }
   }
@@ -342,7 +387,15 @@ cudaError_t launch_cfg(const CUtensorMap& ta, const CUtensorMap& tb, const Slice
                                        static_cast<int>(Cfg::kSmemBytes));
   if (e != cudaSuccess) return e;
   count_launch();
-  kern<<<grid, kThreads, Cfg::kSmemBytes, stream>>>(ta, tb, a);
+  static int num_sms = 0;
+  if (num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (num_sms <= 0) num_sms = 148;
+  }
+  const int blocks = grid < num_sms ? grid : num_sms;
+  kern<<<blocks, kThreads, Cfg::kSmemBytes, stream>>>(ta, tb, a);
   return cudaGetLastError();
 }
 
@@ -394,6 +447,7 @@ cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& B, const Precision& p
   const int tm = (args.M + kBM - 1) / kBM;
   const int tn = (args.N + kBN - 1) / kBN;
   args.tiles_n = tn;
+  args.tiles_m = tm;
   const int grid = (args.mode & kGemmSym) ? tn * (tn + 1) / 2 : tm * tn;
   if (grid == 0) return cudaSuccess;
 

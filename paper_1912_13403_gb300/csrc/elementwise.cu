@@ -79,6 +79,75 @@ __global__ void __launch_bounds__(kRowThreads)
   }
 }
 
+// ---- FP32 double-float arithmetic: FP64-accurate reductions without the FP64 ALU ----------
+// x ~ hi + lo with |x - hi - lo| <= 2^-52 |x|, from the FP64 bit pattern (integer operations
+// and one int->float conversion).  Magnitudes outside FP32's normal range flush to 0 (inputs
+// of this engine are far from 2^-126).
+__device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int E = static_cast<int>((b >> 52) & 0x7FF);
+  const unsigned sign = static_cast<unsigned>(b >> 63) << 31;
+  if (E == 0x7FF) {
+    hi = __uint_as_float(sign | 0x7F800000u | (((b << 12) != 0) ? 1u : 0u));
+    lo = 0.0f;
+    return;
+  }
+  const int ef = E - 1023 + 127;
+  if (E == 0 || ef <= 0) {
+    hi = 0.0f;
+    lo = 0.0f;
+    return;
+  }
+  if (ef >= 255) {
+    hi = __uint_as_float(sign | 0x7F800000u);
+    lo = 0.0f;
+    return;
+  }
+  hi = __uint_as_float(sign | (static_cast<unsigned>(ef) << 23) |
+                       static_cast<unsigned>((b >> 29) & 0x7FFFFF));
+  const unsigned rem = static_cast<unsigned>(b & ((1ULL << 29) - 1));
+  const int el = E - 1075 + 127;  // 2^(E-1075) as a float
+  lo = (el > 0 && rem != 0) ? __int2float_rn(static_cast<int>(rem)) *
+                                  __uint_as_float(static_cast<unsigned>(el) << 23)
+                            : 0.0f;
+  if (sign) lo = -lo;
+}
+
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb) + a.lo + b.lo;
+  const float h = s + e;
+  return DF{h, e - (h - s)};
+}
+
+// acc + x * y, x and y given as (hi, lo) pairs
+__device__ __forceinline__ DF df_fma(DF acc, float xh, float xl, float yh, float yl) {
+  const float p = xh * yh;
+  float pe = fmaf(xh, yh, -p);
+  pe = fmaf(xh, yl, fmaf(xl, yh, pe));
+  return df_add(acc, DF{p, pe});
+}
+
+__device__ __forceinline__ DF df_warp_sum(DF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = df_add(v, w);
+  }
+  return v;
+}
+
+__device__ __forceinline__ double df_to_double(DF v) {
+  return static_cast<double>(v.hi) + static_cast<double>(v.lo);
+}
+
 // ---- integer slicing helpers: no FP64 arithmetic (GB300 runs FP64 at ~2 DFMA/clk/SM) ----
 
 // y truncated to FP32 from its bit pattern (integer ops only); 0 below FP32's normal range,
@@ -223,6 +292,100 @@ __global__ void __launch_bounds__(kRowThreads)
   }
 }
 
+// Row pass of the slicing, one warp per row: forms y = a X + b X2 + c I when (a, b, c) is not
+// (1, 0, 0) (FP64, written to Y), and writes the row scale 2^e > ||y|| from an FP32 norm of the
+// truncated values enlarged by 0.2% (NaN marks a row with NaN / Inf).
+__global__ void __launch_bounds__(kRowsPerBlock * 32)
+    form_norm_kernel(const double* __restrict__ X, int64_t ldx, const double* __restrict__ X2,
+                     int64_t ldx2, int rows, int cols, const double* __restrict__ coef_dev,
+                     double ha, double hb, double hc, double* Y, int64_t ldy, double* out_scale,
+                     const int* skip) {
+  if (skip != nullptr && *skip != 0) return;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * kRowsPerBlock + w;
+  if (row >= rows) return;
+  double a = ha, b = hb, c = hc;
+  if (coef_dev != nullptr) {
+    a = coef_dev[0];
+    b = coef_dev[1];
+    c = coef_dev[2];
+  }
+  const bool plain = (a == 1.0) && (X2 == nullptr || b == 0.0) && (c == 0.0);
+  const double2* xr = reinterpret_cast<const double2*>(X + row * ldx);
+  const double2* x2r = (X2 != nullptr) ? reinterpret_cast<const double2*>(X2 + row * ldx2)
+                                        : nullptr;
+  double2* yr = (Y != nullptr) ? reinterpret_cast<double2*>(Y + row * ldy) : nullptr;
+  const int npairs = cols >> 1;
+  float ss = 0.0f;
+  for (int p = lane; p < npairs; p += 32) {
+    double2 y = xr[p];
+    if (!plain) {
+      y.x *= a;
+      y.y *= a;
+      if (x2r != nullptr) {
+        const double2 x2 = x2r[p];
+        y.x = fma(b, x2.x, y.x);
+        y.y = fma(b, x2.y, y.y);
+      }
+      if (2 * p == row) y.x += c;
+      if (2 * p + 1 == row) y.y += c;
+    }
+    if (yr != nullptr) yr[p] = y;
+    const float f0 = trunc_to_float(y.x), f1 = trunc_to_float(y.y);
+    ss = fmaf(f0, f0, fmaf(f1, f1, ss));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (lane == 0 && out_scale != nullptr) {
+    if (ss > 0.0f && isfinite(ss)) {
+      int e = 0;
+      frexpf(sqrtf(ss * 1.002f) * 1.0001f, &e);  // 2^e > ||y|| with margin
+      out_scale[row] = ldexp(1.0, e);
+    } else {
+      out_scale[row] = isfinite(ss) ? 1.0 : __longlong_as_double(0x7FF8000000000000LL);
+    }
+  }
+}
+
+// Element pass of the slicing, grid-stride over (row, column pair): the balanced base-2^bits
+// digits of round(y * 2^(11 - e + bits (nslice - 1))), e from the row scale; integer only.
+__global__ void __launch_bounds__(256)
+    slice_pairs_kernel(const double* __restrict__ Yin, int64_t ldy, int rows, int cols,
+                       const double* __restrict__ scale, __half* out, int64_t out_ld,
+                       int64_t plane, int nslice, int bits, const int* skip) {
+  if (skip != nullptr && *skip != 0) return;
+  const int npairs = cols >> 1;
+  const int64_t total = static_cast<int64_t>(rows) * npairs;
+  const long long H = 1LL << (bits - 1);
+  const long long MASK = (1LL << bits) - 1;
+  const int64_t plane2 = plane >> 1;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int row = static_cast<int>(idx / npairs);
+    const int p = static_cast<int>(idx - static_cast<int64_t>(row) * npairs);
+    const double sc = scale[row];
+    long long n0 = 0, n1 = 0;
+    if (isfinite(sc)) {
+      const int e = static_cast<int>(
+          (static_cast<unsigned long long>(__double_as_longlong(sc)) >> 52) & 0x7FF) - 1023;
+      const int p2 = 11 - e + bits * (nslice - 1);
+      const double2 y = reinterpret_cast<const double2*>(Yin + row * ldy)[p];
+      n0 = fixed_point(y.x, p2);
+      n1 = fixed_point(y.y, p2);
+    }
+    __half2* orow = reinterpret_cast<__half2*>(out + row * out_ld);
+    for (int s = nslice - 1; s >= 1; --s) {
+      const long long d0 = ((n0 + H) & MASK) - H, d1 = ((n1 + H) & MASK) - H;
+      orow[s * plane2 + p] = __halves2half2(__int2half_rn(static_cast<int>(d0)),
+                                            __int2half_rn(static_cast<int>(d1)));
+      n0 = (n0 - d0) >> bits;
+      n1 = (n1 - d1) >> bits;
+    }
+    orow[p] = __halves2half2(__int2half_rn(static_cast<int>(n0)),
+                             __int2half_rn(static_cast<int>(n1)));
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // Gershgorin: lo_i = a_ii - sum_{j != i} |a_ij|, hi_i = a_ii + sum_{j != i} |a_ij|
 // ------------------------------------------------------------------------------------------
@@ -292,6 +455,7 @@ __global__ void minmax_reduce_kernel(const double* partials, int nblocks, double
 __global__ void __launch_bounds__(kRowsPerBlock * 32)
     trs4_traces_kernel(const double* __restrict__ X, const double* __restrict__ X2, int64_t ld,
                        int n, double* partials) {
+  // <X2, X>, ||X2||^2 and ||X||^2 in FP32 double-float (no FP64 ALU), diagonals exact
   __shared__ double s[kRowsPerBlock][kTraceTerms];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * kRowsPerBlock + w;
@@ -299,19 +463,58 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32)
   if (row < n) {
     const double* xr = X + row * ld;
     const double* yr = X2 + row * ld;
-    for (int j = lane; j < n; j += 32) {
-      const double x = xr[j], y = yr[j];
-      t[2] += y * x;
-      t[3] += y * y;
-      t[4] += x * x;
+    DF a3{0.f, 0.f}, a4{0.f, 0.f}, a5{0.f, 0.f};
+    // 4 x 16-byte loads per array in flight per lane when rows are 16-byte aligned
+    const bool vec = ((ld & 1) == 0) && ((reinterpret_cast<uintptr_t>(X) |
+                                          reinterpret_cast<uintptr_t>(X2)) & 15) == 0;
+    const double2* x2p = reinterpret_cast<const double2*>(xr);
+    const double2* y2p = reinterpret_cast<const double2*>(yr);
+    const int np = vec ? (n >> 1) : 0;
+    int p = lane;
+    for (; p + 96 < np; p += 128) {
+      double2 xv[4], yv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        xv[u] = x2p[p + 32 * u];
+        yv[u] = y2p[p + 32 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float xh, xl, yh, yl;
+        split_double(xv[u].x, xh, xl);
+        split_double(yv[u].x, yh, yl);
+        a3 = df_fma(a3, yh, yl, xh, xl);
+        a4 = df_fma(a4, yh, yl, yh, yl);
+        a5 = df_fma(a5, xh, xl, xh, xl);
+        split_double(xv[u].y, xh, xl);
+        split_double(yv[u].y, yh, yl);
+        a3 = df_fma(a3, yh, yl, xh, xl);
+        a4 = df_fma(a4, yh, yl, yh, yl);
+        a5 = df_fma(a5, xh, xl, xh, xl);
+      }
     }
+    const int j0 = vec ? 2 * p : lane, jstep = vec ? 64 : 32, jw = vec ? 2 : 1;
+    for (int j = j0; j < n; j += jstep) {  // tail (and unaligned rows) element-wise
+      for (int jj = j; jj < j + jw && jj < n; ++jj) {
+        float xh, xl, yh, yl;
+        split_double(xr[jj], xh, xl);
+        split_double(yr[jj], yh, yl);
+        a3 = df_fma(a3, yh, yl, xh, xl);
+        a4 = df_fma(a4, yh, yl, yh, yl);
+        a5 = df_fma(a5, xh, xl, xh, xl);
+      }
+    }
+    a3 = df_warp_sum(a3);
+    a4 = df_warp_sum(a4);
+    a5 = df_warp_sum(a5);
     if (lane == 0) {
       t[0] = xr[row];
       t[1] = yr[row];
+      t[2] = df_to_double(a3);
+      t[3] = df_to_double(a4);
+      t[4] = df_to_double(a5);
     }
   }
-#pragma unroll
-  for (int k = 0; k < kTraceTerms; ++k) t[k] = warp_sum(t[k]);
   if (lane == 0)
     for (int k = 0; k < kTraceTerms; ++k) s[w][k] = t[k];
   __syncthreads();
@@ -325,26 +528,74 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32)
 __global__ void __launch_bounds__(kRowsPerBlock * 32)
     dot_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ B,
                int64_t ldb, int rows, int cols, int minus_identity, double* partials) {
+  // FP32 double-float accumulation (no FP64 ALU)
   __shared__ double s[kRowsPerBlock];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * kRowsPerBlock + w;
-  double acc = 0.0;
+  double r = 0.0;
   if (row < rows) {
     const double* ar = A + row * lda;
     const double* br = (B != nullptr) ? B + row * ldb : nullptr;
-    for (int j = lane; j < cols; j += 32) {
-      double a = ar[j];
-      if (minus_identity && j == row) a -= 1.0;
-      acc += (br != nullptr) ? a * br[j] : a * a;
+    DF acc{0.f, 0.f};
+    const bool vec = ((lda & 1) == 0) && (br == nullptr || (ldb & 1) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(A) |
+                       (br != nullptr ? reinterpret_cast<uintptr_t>(B) : 0)) & 15) == 0;
+    int jstart = lane, jstep = 32;
+    if (vec) {
+      const double2* a2 = reinterpret_cast<const double2*>(ar);
+      const double2* b2 = (br != nullptr) ? reinterpret_cast<const double2*>(br) : nullptr;
+      const int np = cols >> 1;
+      int p = lane;
+      for (; p + 96 < np; p += 128) {
+        double2 av[4], bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          av[u] = a2[p + 32 * u];
+          bv[u] = (b2 != nullptr) ? b2[p + 32 * u] : av[u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = 2 * (p + 32 * u);
+          double x0 = av[u].x, x1 = av[u].y;
+          if (minus_identity && j == row) x0 -= 1.0;
+          if (minus_identity && j + 1 == row) x1 -= 1.0;
+          double y0 = (b2 != nullptr) ? bv[u].x : x0, y1 = (b2 != nullptr) ? bv[u].y : x1;
+          float ah, al, bh, bl;
+          split_double(x0, ah, al);
+          split_double(y0, bh, bl);
+          acc = df_fma(acc, ah, al, bh, bl);
+          split_double(x1, ah, al);
+          split_double(y1, bh, bl);
+          acc = df_fma(acc, ah, al, bh, bl);
+        }
+      }
+      jstart = 2 * p;
+      jstep = 64;
     }
+    for (int j0 = jstart; j0 < cols; j0 += jstep) {
+      for (int j = j0; j < j0 + (vec ? 2 : 1) && j < cols; ++j) {
+        float ah, al;
+        double av = ar[j];
+        if (minus_identity && j == row) av -= 1.0;
+        split_double(av, ah, al);
+        if (br != nullptr) {
+          float bh, bl;
+          split_double(br[j], bh, bl);
+          acc = df_fma(acc, ah, al, bh, bl);
+        } else {
+          acc = df_fma(acc, ah, al, ah, al);
+        }
+      }
+    }
+    acc = df_warp_sum(acc);
+    r = df_to_double(acc);
   }
-  acc = warp_sum(acc);
-  if (lane == 0) s[w] = acc;
+  if (lane == 0) s[w] = r;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double r = 0.0;
-    for (int i = 0; i < kRowsPerBlock; ++i) r += s[i];
-    partials[blockIdx.x] = r;
+    double t = 0.0;
+    for (int i = 0; i < kRowsPerBlock; ++i) t += s[i];
+    partials[blockIdx.x] = t;
   }
 }
 
@@ -487,16 +738,58 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32)
   if (row >= n) return;
   const double* ar = A + row * lda;
   const double* br = Bt + row * ldb;
-  double acc = 0.0;
-  for (int k = lane; k < K; k += 32) acc = fma(ar[k], br[k], acc);
-  acc = warp_sum(acc);
+  DF acc{0.f, 0.f};  // FP32 double-float: ~2^-48 relative, no FP64 ALU in the loop
+  const bool vec = ((lda | ldb) & 1) == 0 && ((reinterpret_cast<uintptr_t>(A) |
+                                               reinterpret_cast<uintptr_t>(Bt)) & 15) == 0;
+  int kstart = lane;
+  if (vec) {
+    const double2* a2 = reinterpret_cast<const double2*>(ar);
+    const double2* b2 = reinterpret_cast<const double2*>(br);
+    const int np = K >> 1;
+    int p = lane;
+    for (; p + 96 < np; p += 128) {
+      double2 av[4], bv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        av[u] = a2[p + 32 * u];
+        bv[u] = b2[p + 32 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float ah, al, bh, bl;
+        split_double(av[u].x, ah, al);
+        split_double(bv[u].x, bh, bl);
+        acc = df_fma(acc, ah, al, bh, bl);
+        split_double(av[u].y, ah, al);
+        split_double(bv[u].y, bh, bl);
+        acc = df_fma(acc, ah, al, bh, bl);
+      }
+    }
+    kstart = 2 * p;  // continue element-wise from here, stride 64 per lane pair block
+    for (int k = kstart; k < K; k += 64) {
+      for (int kk = k; kk < k + 2 && kk < K; ++kk) {
+        float ah, al, bh, bl;
+        split_double(ar[kk], ah, al);
+        split_double(br[kk], bh, bl);
+        acc = df_fma(acc, ah, al, bh, bl);
+      }
+    }
+  } else {
+    for (int k = lane; k < K; k += 32) {
+      float ah, al, bh, bl;
+      split_double(ar[k], ah, al);
+      split_double(br[k], bh, bl);
+      acc = df_fma(acc, ah, al, bh, bl);
+    }
+  }
+  acc = df_warp_sum(acc);
   if (lane == 0) {
-    double al = alpha, be = beta;
+    double al2 = alpha, be = beta;
     if (coef != nullptr) {
-      al = coef[0];
+      al2 = coef[0];
       be = coef[1];
     }
-    double v = al * acc + diag;
+    double v = al2 * df_to_double(acc) + diag;
     if (D != nullptr) v += be * D[row * ldd + row];
     C[row * ldc + row] = v;
   }
@@ -559,11 +852,26 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
       (Y == nullptr || ((ldy % 2 == 0) && (reinterpret_cast<uintptr_t>(Y) % 16 == 0))) &&
       (od == nullptr || ((old % 2 == 0) && (plane % 2 == 0) &&
                          (reinterpret_cast<uintptr_t>(od) % 4 == 0)));
-  if (aligned && cols <= 2 * kRowThreads * 4) {
+  const bool host_plain = (coef_dev == nullptr) && ha == 1.0 && (X2 == nullptr || hb == 0.0) &&
+                          hc == 0.0;
+  if (aligned && (host_plain || Y != nullptr || od == nullptr)) {
+    // two passes: rows (form + norm) then elements (slices), both fully parallel
+    const int nb = (rows + kRowsPerBlock - 1) / kRowsPerBlock;
     count_launch();
-    form_slice_vec_kernel<4><<<rows, kRowThreads, 0, stream>>>(
-        X, ldx, X2, ldx2, rows, cols, coef_dev, ha, hb, hc, Y, ldy, od, osc, old, plane, nslice,
-        skip, bits);
+    form_norm_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(X, ldx, X2, ldx2, rows, cols,
+                                                            coef_dev, ha, hb, hc, Y, ldy,
+                                                            od != nullptr ? osc : nullptr, skip);
+    if (od != nullptr) {
+      const double* src = (Y != nullptr) ? Y : X;
+      const int64_t lds = (Y != nullptr) ? ldy : ldx;
+      const int64_t total = static_cast<int64_t>(rows) * (cols / 2);
+      int blocks = static_cast<int>((total + 255) / 256);
+      if (blocks > 152 * 16) blocks = 152 * 16;
+      if (blocks < 1) blocks = 1;
+      count_launch();
+      slice_pairs_kernel<<<blocks, 256, 0, stream>>>(src, lds, rows, cols, osc, od, old, plane,
+                                                     nslice, bits, skip);
+    }
   } else if (aligned && cols <= 2 * kRowThreads * 16) {
     count_launch();
     form_slice_vec_kernel<16><<<rows, kRowThreads, 0, stream>>>(

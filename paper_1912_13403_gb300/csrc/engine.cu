@@ -165,9 +165,12 @@ double sliced_flops(const gdm_handle* h, int ph, bool sym) {
 }
 
 // C = alpha * A * Bt^T + beta * D + diag * I (sym: C symmetric, upper tiles + mirror)
+// exact_diag: recompute the diagonal from the FP64 operands.  Needed where the two factors
+// have (nearly) parallel rows (X X, X^2 W, delta delta): there the residual-slice terms of the
+// diagonal add up with one sign and the FP32 accumulators' truncation biases them.
 cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const double* D,
                     double alpha, double beta, double diag, bool sym, int ph,
-                    const double* coef = nullptr) {
+                    const double* coef = nullptr, bool exact_diag = false) {
   const int n = static_cast<int>(h->n);
   if (sliced(h, ph)) {
     SlicedGemmArgs a;
@@ -195,7 +198,7 @@ cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const dou
       cudaEventRecord(e1, h->stream);
       h->prof_pending.push_back({e0, e1, sliced_flops(h, ph, sym), 0});
     }
-    // exact FP64 diagonal (removes the truncation bias of the FP32 accumulators there)
+    if (!exact_diag) return cudaSuccess;
     e = diag_fix(A.f, h->ld, Bt.f, h->ld, C, h->ld, n, n, alpha, beta, D, h->ld, diag, coef,
                  h->stream);
     if (e != cudaSuccess || Ct == nullptr) return e;
@@ -369,7 +372,7 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
     if (r == nref || derr == 0.0) break;
     CK(slice(h, Dl, &h->sl[SL_B], GDM_PHASE_REFINE));
     CK(product(h, {Dl, &h->sl[SL_B]}, {Dl, &h->sl[SL_B]}, F, nullptr, Dl, 0.375, -0.5, 1.0, true,
-               GDM_PHASE_REFINE));                                   // F = I - d/2 + 3d^2/8
+               GDM_PHASE_REFINE, nullptr, true));                    // F = I - d/2 + 3d^2/8
     CK(slice(h, F, &h->sl[SL_A], GDM_PHASE_REFINE));
     double* Znew = h->f[F_X];
     double* Zt_new = h->f[F_X2];
@@ -458,7 +461,7 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   double* W = h->f[F_V];
   for (it = 0; it < h->max_purif; ++it) {
     CK(product(h, {X, &h->sl[SL_X]}, {X, &h->sl[SL_X]}, X2, nullptr, nullptr, 1.0, 0.0, 0.0, true,
-               GDM_PHASE_PURIFY));
+               GDM_PHASE_PURIFY, nullptr, true));
     int nb = 0;
     CK(trs4_traces(X, X2, ld, n, h->partials, &nb, s));
     CK(trs4_control(h->partials, nb, h->st_dev, tol_abs, s));
@@ -485,7 +488,7 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
       CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefW)), 0, 0, 0, W, ld, pu_sl > 0 ? &h->sl[SL_W] : nullptr, pu_sl, nullptr, s,
                         bits_for(h, GDM_PHASE_PURIFY)));
       CK(product(h, {X2, &h->sl[SL_X2]}, {W, &h->sl[SL_W]}, Xn, nullptr, X2, 1.0, 0.0, 0.0, true,
-                 GDM_PHASE_PURIFY, st_field(h, offsetof(Trs4State, gemm_coef))));
+                 GDM_PHASE_PURIFY, st_field(h, offsetof(Trs4State, gemm_coef)), true));
       CK(slice(h, Xn, &h->sl[SL_X], GDM_PHASE_PURIFY));
     } else {
       CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefX)), 0, 0, 0, Xn, ld,

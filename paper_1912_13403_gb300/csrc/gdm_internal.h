@@ -145,8 +145,9 @@ cudaError_t x0_coefficients(const double* bounds_dev, double* coef_dev, cudaStre
 cudaError_t scale_coefficients(const double* bounds_dev, int inv_sqrt, double* coef_dev,
                                cudaStream_t stream);
 
-// Exact FP64 diagonal of a square product: C_ii = alpha <A_i, Bt_i> + beta D_ii + diag
-// ((alpha, beta) from coef when non-null).  Run after the sliced product (see elementwise.cu).
+// Diagonal of a square product recomputed from the FP64 operands (FP32 double-float dot
+// products, ~2^-48 relative): C_ii = alpha <A_i, Bt_i> + beta D_ii + diag ((alpha, beta) from
+// coef when non-null).  Run after the sliced product (see elementwise.cu).
 cudaError_t diag_fix(const double* A, int64_t lda, const double* Bt, int64_t ldb, double* C,
                      int64_t ldc, int n, int K, double alpha, double beta, const double* D,
                      int64_t ldd, double diag, const double* coef, cudaStream_t stream);

@@ -94,6 +94,21 @@ __device__ __forceinline__ long long f32_integer(uint32_t bits) {
   return (bits >> 31) ? -v : v;
 }
 
+// finiteness from the bit pattern (integer compare, no FP64 instruction)
+__device__ __forceinline__ bool finite_bits(double s) {
+  return ((static_cast<unsigned long long>(__double_as_longlong(s)) >> 52) & 0x7FF) != 0x7FF;
+}
+
+// alpha = +-2^k exactly?  (then scaling is an exponent shift)
+__device__ __forceinline__ bool pow2_scalar(double a, int& k, bool& neg) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(a));
+  const int E = static_cast<int>((b >> 52) & 0x7FF);
+  if (E == 0 || E == 0x7FF || (b & ((1ULL << 52) - 1)) != 0) return false;
+  k = E - 1023;
+  neg = (b >> 63) != 0;
+  return true;
+}
+
 // exponent of a power-of-two double (the row scales)
 __device__ __forceinline__ int pow2_exponent(double s) {
   return static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(s)) >> 52) &
@@ -255,7 +270,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       alpha = args.coef[0];
       beta = args.coef[1];
     }
-    const bool unit_alpha = (alpha == 1.0);
+    int alpha_k = 0;
+    bool alpha_neg = false;
+    const bool pow2_alpha = pow2_scalar(alpha, alpha_k, alpha_neg);
     int tcount = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
       int ti, tj;
@@ -267,8 +284,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int r0 = ti * kBM + q * 32;
       const int grow = r0 + lane;
       const double sa = (grow < args.M) ? args.row_scale_a[grow] : 0.0;
-      const bool sa_ok = isfinite(sa);
-      const int ex_base = pow2_exponent(sa) - 22 - args.shift * (args.nacc - 1);
+      const bool sa_ok = finite_bits(sa);
+      const int ex_base = pow2_exponent(sa) - 22 - args.shift * (args.nacc - 1) +
+                          (pow2_alpha ? alpha_k : 0);
       for (int c = 0; c < 2; ++c) {
         const int ccol = half * 64 + c * 32;  // column offset inside the tile
         long long T[32];
@@ -300,9 +318,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             double val = 0.0;
             if (grow < args.M && gcol < args.N) {
               const double sb = args.row_scale_b[gcol];
-              if (sa_ok && isfinite(sb)) {
-                val = scaled_int_to_double(T[j], ex_base + pow2_exponent(sb));
-                if (!unit_alpha) val *= alpha;
+              if (sa_ok && finite_bits(sb)) {
+                const long long tv = (pow2_alpha && alpha_neg) ? -T[j] : T[j];
+                val = scaled_int_to_double(tv, ex_base + pow2_exponent(sb));
+                if (!pow2_alpha) val *= alpha;
               } else {
                 val = sa * sb;  // a NaN / Inf row scale marks a non-finite input row
               }

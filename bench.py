@@ -38,6 +38,13 @@ WORKLOADS = {
                     n=8192, n_occ=2048),
     "config0": dict(desc="config0: n=256, n_occ=64, S = I + 0.1 (G+G^T)/(2 sqrt n), gap >= 1",
                     n=256, n_occ=64),
+    "config3": dict(desc="config3: batch of 64 independent problems, n log-uniform [512, 3072], "
+                         "n_occ = n/4, cond(S) log-uniform [10, 1e3], gap log-uniform "
+                         "[0.05, 0.5]; one gdm_solve_batch call per step",
+                    n=3072, n_occ=768),
+    "config4": dict(desc="config4: serving stream, Poisson arrivals, n log-uniform [256, 8192], "
+                         "n_occ = n/4, gap log-uniform [0.05, 0.5], S as config0",
+                    n=8192, n_occ=2048),
 }
 
 
@@ -51,6 +58,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-fp64-ref", action="store_true", help="skip the all-FP64 GPU solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--concurrency", type=int, default=4, help="batch / server worker count")
+    ap.add_argument("--requests", type=int, default=200, help="config4: requests per phase")
+    ap.add_argument("--rate", type=float, default=200.0, help="config4: offered req/s")
     ap.add_argument("--cache", default="/tmp/gdm_bench_inputs",
                     help="directory for generated inputs ('' disables)")
     return ap.parse_args()
@@ -95,6 +105,26 @@ def _generate(name, seed, device):
     if name == "config2":
         return workloads.make_config2(seed=seed, device=device)
     return workloads.make_config0(seed=seed, device=device)
+
+
+def max_over_ranks(x, device="cpu"):
+    """Max of a float over the ranks of the default process group (x itself when there is
+    none): the timed region of a multi-GPU run is the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, total_ms_this_rank, device="cpu"):
+    """Whole-job rate: all ranks' units over the max-over-ranks time (weak scaling)."""
+    import torch.distributed as dist
+    world = dist.get_world_size() if (dist.is_available() and dist.is_initialized()) else 1
+    t = max_over_ranks(total_ms_this_rank, device)
+    return world * units_per_rank / (t / 1e3), t
 
 
 def measured_peaks():
@@ -305,11 +335,7 @@ def run_ours(args):
     per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
     prof_launch, prof_ms, prof_flops = h.profile(0)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    value, total_ms = job_throughput(args.steps, total_ms, device="cuda")
 
     # accuracy of the last timed solve
     relerr = float(torch.linalg.norm(P - Pc) / torch.linalg.norm(Pc))
@@ -401,10 +427,139 @@ def run_ours(args):
     return 0
 
 
+def _closed_form_gpu(p, torch, np):
+    U = torch.from_numpy(p.factors["S_U"]).cuda()
+    sw = torch.from_numpy(p.factors["S_w"]).cuda()
+    Qo = torch.from_numpy(np.ascontiguousarray(p.factors["Q"][:, :p.n_occ])).cuda()
+    C = (U * sw.rsqrt()[None, :]) @ (U.T @ Qo)
+    return C @ C.T, float(np.sum(p.factors["lam"][:p.n_occ]))
+
+
+def run_batch(args):
+    """config3: every step is one gdm_solve_batch over the 64 resident problems."""
+    import numpy as np
+    import torch
+    import paper_1912_13403_gb300 as g
+    import workloads
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    probs = workloads.make_batch_config3(seed=3 + 100 * rank, device="cuda")
+    items = []
+    for p in probs:
+        items.append((torch.from_numpy(p.H).cuda(), torch.from_numpy(p.S).cuda(), p.n_occ,
+                      torch.empty((p.n, p.n), dtype=torch.float64, device="cuda")))
+    for _ in range(args.warmup):
+        st, res = g.solve_batch(items, concurrency=args.concurrency, device=local)
+    torch.cuda.synchronize()
+    launches0 = g.gdm_launch_count()
+    sampler = ClockSampler(local)
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st, res = g.solve_batch(items, concurrency=args.concurrency, device=local)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    clocks = sampler.stop()
+    launches = g.gdm_launch_count() - launches0
+    errs, tr = [], []
+    for p, it, r in zip(probs, items, res):
+        Pc, Ec = _closed_form_gpu(p, torch, np)
+        errs.append(float(torch.linalg.norm(it[3] - Pc) / torch.linalg.norm(Pc)))
+        tr.append(r["info"]["trace_err_raw"])
+    total = sum(times)
+    value = world * len(probs) * args.steps / total
+    flops = sum(4.0 * p.n ** 3 for p in probs)  # nominal FP64-equivalent work per problem
+    lat = sorted(r["latency_ms"] for r in res)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16-slices(f32-acc)+f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS["config3"]["desc"], "problems": len(probs),
+                       "n_range": [min(p.n for p in probs), max(p.n for p in probs)],
+                       "concurrency": args.concurrency, "status": st},
+            "latency_ms_per_problem": {"p50": lat[len(lat) // 2], "p99": lat[-1]},
+            "accuracy": {"max_rel_frobenius_err": max(errs), "max_trace_err_raw": max(tr)},
+            "gpu_launches": launches, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving(args):
+    """config4: Poisson arrivals at --rate req/s, then at 70% of the measured capacity."""
+    import numpy as np
+    import torch
+    import paper_1912_13403_gb300 as g
+    import workloads
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    reqs = workloads.make_request_stream(seed=4 + 100 * rank, count=args.requests,
+                                         rate=args.rate)
+    # a pool of distinct inputs from the request recipe (sizes spread over the range); each
+    # request uses the pool member closest to its own size class
+    sizes = sorted({int(round(256 * 32 ** (k / 11.0))) for k in range(12)})
+    pool = []
+    for k, n in enumerate(sizes):
+        q = workloads.make_request_problem(dict(seed=4000 + k, n=n, n_occ=int(round(0.25 * n)),
+                                                gap=0.2), device="cuda")
+        pool.append((torch.from_numpy(q.H).pin_memory(), torch.from_numpy(q.S).pin_memory(),
+                     q.n_occ, n))
+
+    def pick(n):
+        return min(pool, key=lambda it: abs(math.log(it[3]) - math.log(n)))
+
+    outs = {it[3]: torch.empty((it[3], it[3]), dtype=torch.float64).pin_memory() for it in pool}
+
+    def phase(arrivals):
+        srv = g.Server(slots=args.concurrency, device=local)
+        tickets, t0 = [], time.perf_counter()
+        for a, r in arrivals:
+            dt = a - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            it = pick(r["n"])
+            tickets.append((srv.submit(it[0], it[1], it[2], outs[it[3]]),
+                            time.perf_counter() - t0 - a))
+        res = [(srv.wait(t, -1.0), lag) for t, lag in tickets]
+        wall = time.perf_counter() - t0
+        srv.close()
+        lat = sorted(r["latency_ms"] + 1e3 * lag for r, lag in res)
+        ok = sum(1 for r, _ in res if r["status"] == g.GDM_OK)
+        return {"requests": len(res), "ok": ok, "wall_s": wall, "throughput": len(res) / wall,
+                "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1,
+                                                               int(0.99 * len(lat)))]}
+
+    warm = [(0.0, dict(n=n)) for n in sizes]
+    phase(warm)
+    stated = phase([(r["arrival_s"], r) for r in reqs])
+    cap = stated["throughput"]
+    rng = np.random.default_rng(44)
+    t, arr = 0.0, []
+    for r in reqs:
+        t += rng.exponential(1.0 / (0.7 * cap))
+        arr.append((t, r))
+    relaxed = phase(arr)
+    line = {"metric": METRIC, "value": stated["throughput"], "unit": UNIT, "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * stated["wall_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16-slices(f32-acc)+f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS["config4"]["desc"], "offered_rate": args.rate,
+                       "slots": args.concurrency, "input_pool": sizes},
+            "serving_stated_load": stated, "serving_70pct_capacity": relaxed}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "config3":
+        return run_batch(args)
+    if args.workload == "config4":
+        return run_serving(args)
     return run_ours(args)
 
 

@@ -165,6 +165,77 @@ const char* gdm_status_string(gdm_status s);
 const char* gdm_last_error(const gdm_handle* h);
 
 /* ---------------------------------------------------------------------------------------
+ * Batches and a request server.  Independent problems (the paper's spin / k-point "unit
+ * tasks", Sec. 2.4, solved fully in parallel) run as concurrent solves on one GPU: worker
+ * threads each own a handle and a stream, and their kernels overlap on the device.
+ * --------------------------------------------------------------------------------------- */
+
+/* One problem: H and S (n_basis x n_basis, leading dimensions ldh / lds) in `mem`; P (may be
+ * NULL) receives the density matrix in `p_mem` with leading dimension ldp. */
+typedef struct {
+  int64_t n_basis, n_occ;
+  const double* H;
+  int64_t ldh;
+  const double* S;
+  int64_t lds;
+  gdm_mem mem;
+  double* P;
+  int64_t ldp;
+  gdm_mem p_mem;
+} gdm_problem;
+
+typedef struct {
+  gdm_status status;  /* of this problem's solve */
+  double energy;      /* Tr(P H) */
+  gdm_info info;
+  double latency_ms;  /* batch: solve wall time; server: submission to completion */
+} gdm_result;
+
+typedef struct {
+  int device;               /* CUDA device */
+  int concurrency;          /* concurrent solves (worker threads / streams); <= 0: 4 */
+  gdm_precision precision;  /* GDM_PREC_MIXED (0-initialised structs give FP64: set it) */
+} gdm_batch_config;
+
+/* Solve `count` independent problems of any sizes; results[i] belongs to problems[i].  Larger
+ * problems start first.  cfg may be NULL (device 0, 4 concurrent, mixed precision).  Blocks
+ * until all are done.  Returns GDM_OK, or the first failing problem's status (every result
+ * is filled either way); GDM_ERR_ARG before any work for an invalid problem. */
+gdm_status gdm_solve_batch(const gdm_problem* problems, int count, gdm_result* results,
+                           const gdm_batch_config* cfg);
+
+typedef struct gdm_server gdm_server; /* opaque */
+
+typedef struct {
+  int device;
+  int slots;                  /* concurrent solves; <= 0: 4 */
+  uint64_t hbm_budget_bytes;  /* device memory for the workers' handles; 0: 120 GiB */
+  gdm_precision precision;
+} gdm_server_config;
+
+typedef gdm_problem gdm_request;
+
+/* Start a server (worker threads).  Errors: GDM_ERR_ARG (bad device). */
+gdm_status gdm_server_create(gdm_server** s, const gdm_server_config* cfg);
+
+/* Queue a request.  H and S are copied before the call returns (host or device memory per
+ * r->mem); P must stay valid until the request completes.  Requests are admitted in arrival
+ * order as workers and the memory budget allow.  Errors: GDM_ERR_ARG, GDM_ERR_BUDGET (the
+ * request alone exceeds the budget), GDM_ERR_STATE (server shutting down). */
+gdm_status gdm_submit(gdm_server* s, const gdm_request* r, uint64_t* ticket);
+
+/* Wait up to timeout_s seconds (< 0: no limit) for a request; on completion fills *out and
+ * forgets the ticket.  GDM_ERR_TIMEOUT leaves the request queued or running. */
+gdm_status gdm_wait(gdm_server* s, uint64_t ticket, double timeout_s, gdm_result* out);
+
+/* Non-blocking: *done = 1 and *out filled (ticket forgotten) when complete, else *done = 0. */
+gdm_status gdm_poll(gdm_server* s, uint64_t ticket, int* done, gdm_result* out);
+
+/* Finish running requests, cancel queued ones (status GDM_ERR_STATE), stop the workers and
+ * free everything.  NULL is accepted. */
+gdm_status gdm_server_destroy(gdm_server* s);
+
+/* ---------------------------------------------------------------------------------------
  * Stateless operations on device buffers (for building blocks and step-level checks).
  * All pointers are device pointers of the current CUDA device; `stream` is a cudaStream_t
  * (NULL = default stream); scratch is allocated stream-ordered and freed before return.

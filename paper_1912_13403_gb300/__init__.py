@@ -43,6 +43,32 @@ class gdm_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class gdm_problem(ctypes.Structure):
+    _fields_ = [("n_basis", ctypes.c_int64), ("n_occ", ctypes.c_int64),
+                ("H", ctypes.c_void_p), ("ldh", ctypes.c_int64),
+                ("S", ctypes.c_void_p), ("lds", ctypes.c_int64), ("mem", ctypes.c_int),
+                ("P", ctypes.c_void_p), ("ldp", ctypes.c_int64), ("p_mem", ctypes.c_int)]
+
+
+class gdm_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("energy", ctypes.c_double), ("info", gdm_info),
+                ("latency_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(status=self.status, energy=self.energy, info=self.info.as_dict(),
+                    latency_ms=self.latency_ms)
+
+
+class gdm_batch_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("concurrency", ctypes.c_int),
+                ("precision", ctypes.c_int)]
+
+
+class gdm_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("slots", ctypes.c_int),
+                ("hbm_budget_bytes", ctypes.c_uint64), ("precision", ctypes.c_int)]
+
+
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _int = ctypes.c_int
@@ -76,6 +102,13 @@ _decl("gdm_reinit", _int, [_vp])
 _decl("gdm_finalize", _int, [_vp])
 _decl("gdm_status_string", ctypes.c_char_p, [_int])
 _decl("gdm_last_error", ctypes.c_char_p, [_vp])
+_decl("gdm_solve_batch", _int, [ctypes.POINTER(gdm_problem), _int, ctypes.POINTER(gdm_result),
+                                ctypes.POINTER(gdm_batch_config)])
+_decl("gdm_server_create", _int, [ctypes.POINTER(_vp), ctypes.POINTER(gdm_server_config)])
+_decl("gdm_submit", _int, [_vp, ctypes.POINTER(gdm_problem), ctypes.POINTER(ctypes.c_uint64)])
+_decl("gdm_wait", _int, [_vp, ctypes.c_uint64, _dbl, ctypes.POINTER(gdm_result)])
+_decl("gdm_poll", _int, [_vp, ctypes.c_uint64, ctypes.POINTER(_int), ctypes.POINTER(gdm_result)])
+_decl("gdm_server_destroy", _int, [_vp])
 _decl("gdm_op_product", _int, [_vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _int, _int,
                                _int, _int, _vp])
 _decl("gdm_op_product_noalloc", _int, [_vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _int,
@@ -220,6 +253,86 @@ class Handle:
 
     def __exit__(self, *a):
         self.close()
+
+
+def _problem(H, S, n_occ, P=None):
+    ph, ldh, mem = _buf(H)
+    ps, lds, mem2 = _buf(S)
+    if mem != mem2:
+        raise ValueError("H and S must live in the same memory")
+    p = gdm_problem(H.shape[0], int(n_occ), ph, ldh, ps, lds, mem, None, 0, GDM_MEM_HOST)
+    if P is not None:
+        pp, ldp, pmem = _buf(P)
+        p.P, p.ldp, p.p_mem = pp, ldp, pmem
+    return p
+
+
+def solve_batch(items, concurrency=4, precision=GDM_PREC_MIXED, device=0):
+    """Solve a list of (H, S, n_occ, P) tuples concurrently (gdm_solve_batch).  P may be None.
+    Returns (status, list of result dicts)."""
+    arr = (gdm_problem * len(items))(*[_problem(*it) for it in items])
+    res = (gdm_result * len(items))()
+    cfg = gdm_batch_config(device, concurrency, precision)
+    st = gdm_solve_batch(arr, len(items), res, ctypes.byref(cfg))
+    return st, [r.as_dict() for r in res]
+
+
+class Server:
+    """Request server (gdm_server_*): submit() copies H and S, wait()/poll() return results."""
+
+    def __init__(self, slots=4, hbm_budget_bytes=0, precision=GDM_PREC_MIXED, device=0):
+        self._s = _vp()
+        cfg = gdm_server_config(device, slots, hbm_budget_bytes, precision)
+        st = gdm_server_create(ctypes.byref(self._s), ctypes.byref(cfg))
+        if st != GDM_OK:
+            raise GdmError(st, "gdm_server_create")
+        self._keep = {}
+
+    def submit(self, H, S, n_occ, P=None):
+        p = _problem(H, S, n_occ, P)
+        t = ctypes.c_uint64(0)
+        st = gdm_submit(self._s, ctypes.byref(p), ctypes.byref(t))
+        if st != GDM_OK:
+            raise GdmError(st, "gdm_submit")
+        self._keep[t.value] = P  # the output buffer must outlive the request
+        return t.value
+
+    def wait(self, ticket, timeout_s=-1.0):
+        r = gdm_result()
+        st = gdm_wait(self._s, ticket, timeout_s, ctypes.byref(r))
+        if st != GDM_OK:
+            raise GdmError(st, "gdm_wait")
+        self._keep.pop(ticket, None)
+        return r.as_dict()
+
+    def poll(self, ticket):
+        d = _int(0)
+        r = gdm_result()
+        st = gdm_poll(self._s, ticket, ctypes.byref(d), ctypes.byref(r))
+        if st != GDM_OK:
+            raise GdmError(st, "gdm_poll")
+        if d.value:
+            self._keep.pop(ticket, None)
+            return r.as_dict()
+        return None
+
+    def close(self):
+        if self._s:
+            gdm_server_destroy(self._s)
+            self._s = _vp()
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def op_product(A, Bt, C, nslice=3, max_order=3, symmetric=False, stream=None, slice_bits=0):

@@ -24,60 +24,9 @@
 
 #include "../../include/gdm.h"
 #include "gdm_internal.h"
+#include "handle.h"
 
 using namespace gdm;
-
-namespace {
-
-enum FBuf { F_H, F_S, F_Z, F_ZT, F_X, F_X2, F_XN, F_T, F_U, F_V, F_COUNT };
-enum SBuf { SL_S, SL_Z, SL_ZT, SL_A, SL_B, SL_X, SL_X2, SL_W, SL_COUNT };
-constexpr int kSmall = 4096;  // doubles of small device scratch beyond the partials
-
-}  // namespace
-
-struct gdm_handle {
-  int device = 0;
-  int64_t n = 0, n_occ = 0;
-  int64_t ld = 0;         // leading dimension of every internal n x n buffer
-  int rows_alloc = 0;     // rows of slice buffers (multiple of 128)
-  cudaStream_t own_stream = nullptr, stream = nullptr;
-  gdm_precision prec = GDM_PREC_MIXED;
-  Precision phase[4] = {{2, 1, 12}, {4, 3, 9}, {4, 3, 9}, {3, 3, 12}};
-  double idem_tol = 1e-13, trace_tol = 1e-6;
-  bool trace_correct = true;
-  int max_ns = 100, max_purif = 200, n_refine = 2;
-
-  void* pool = nullptr;
-  double* f[F_COUNT] = {};
-  SliceBuf sl[SL_COUNT];
-  double* partials = nullptr;  // >= 5 * ceil(n/8) doubles
-  double* small = nullptr;     // kSmall doubles: coefficients, bounds, reductions
-  Trs4State* st_dev = nullptr;
-  uint32_t* err_dev = nullptr;
-  double* host_buf = nullptr;  // pinned: kSmall doubles
-  Trs4State* st_host = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-
-  bool have_H = false, have_S = false, z_valid = false;
-  double z_err = 0.0;
-  struct HistRow {
-    double idem, trace, gamma;
-    int branch;
-  };
-  std::vector<HistRow> hist;  // purification history of the last solve
-  // optional timing of the sliced / FP64 product launches (CUDA events on the stream)
-  bool profiling = false;
-  struct Prof {
-    cudaEvent_t a, b;
-    double flops;
-    int kind;  // 0 sliced, 1 fp64
-  };
-  std::vector<Prof> prof_pending;
-  std::vector<cudaEvent_t> ev_pool;
-  int64_t prof_launches[2] = {0, 0};
-  double prof_ms[2] = {0, 0}, prof_flops[2] = {0, 0};
-  std::string last_error;
-};
 
 namespace {
 
@@ -596,6 +545,53 @@ void free_all(gdm_handle* h) {
 
 }  // namespace
 
+namespace {
+
+// Byte layout of a handle's single device allocation for capacity n.
+struct PoolLayout {
+  size_t fbytes, sdata, sscale, pbytes, small_bytes, st_bytes, total;
+  explicit PoolLayout(int64_t n) {
+    auto up = [](size_t x) { return (x + 1023) / 1024 * 1024; };
+    const size_t ld = static_cast<size_t>((n + 63) / 64 * 64);
+    const size_t rows_alloc = static_cast<size_t>((n + 127) / 128 * 128);
+    fbytes = up(sizeof(double) * ld * static_cast<size_t>(n));
+    sdata = up(sizeof(__half) * 4 * ld * rows_alloc);
+    sscale = up(sizeof(double) * rows_alloc);
+    pbytes = up(sizeof(double) * (kTraceTerms * static_cast<size_t>((n + 7) / 8) + 64));
+    small_bytes = up(sizeof(double) * kSmall);
+    st_bytes = up(sizeof(Trs4State));
+    total = F_COUNT * fbytes + SL_COUNT * (sdata + sscale) + pbytes + small_bytes + st_bytes +
+            up(sizeof(uint32_t));
+  }
+};
+
+}  // namespace
+
+namespace gdm {
+
+size_t handle_pool_bytes(int64_t n) { return PoolLayout(n).total; }
+
+gdm_status handle_reconfigure(gdm_handle* h, int64_t n, int64_t n_occ) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  if (n < 1 || n > h->n_cap || n_occ <= 0 || n_occ >= n)
+    return set_err(h, GDM_ERR_ARG, "problem n=%lld, n_occ=%lld does not fit capacity %lld",
+                   static_cast<long long>(n), static_cast<long long>(n_occ),
+                   static_cast<long long>(h->n_cap));
+  h->n = n;
+  h->n_occ = n_occ;
+  h->have_H = false;
+  h->have_S = false;
+  h->z_valid = false;
+  for (int i = 0; i < SL_COUNT; ++i) {
+    h->sl[i].rows = static_cast<int>(n);
+    h->sl[i].cols = static_cast<int>(n);
+    h->sl[i].nslice_valid = 0;
+  }
+  return GDM_OK;
+}
+
+}  // namespace gdm
+
 // ==========================================================================================
 // C ABI
 // ==========================================================================================
@@ -633,6 +629,7 @@ gdm_status gdm_init(gdm_handle** out, int64_t n_basis, int64_t n_occ, int device
   gdm_handle* h = new gdm_handle();
   h->device = device;
   h->n = n_basis;
+  h->n_cap = n_basis;
   h->n_occ = n_occ;
   h->ld = (n_basis + 63) / 64 * 64;
   h->rows_alloc = static_cast<int>((n_basis + 127) / 128 * 128);
@@ -640,16 +637,8 @@ gdm_status gdm_init(gdm_handle** out, int64_t n_basis, int64_t n_occ, int device
     delete h;
     return GDM_ERR_CUDA;
   }
-  const size_t fbytes = sizeof(double) * static_cast<size_t>(h->ld) * static_cast<size_t>(n_basis);
-  const size_t sdata = sizeof(__half) * 4 * static_cast<size_t>(h->ld) * h->rows_alloc;
-  const size_t sscale = sizeof(double) * h->rows_alloc;
-  const size_t nb = (n_basis + 7) / 8;
-  const size_t pbytes = sizeof(double) * (kTraceTerms * nb + 64);
-  const size_t small_bytes = sizeof(double) * kSmall;
-  auto up = [](size_t x) { return (x + 1023) / 1024 * 1024; };
-  size_t total = F_COUNT * up(fbytes) + SL_COUNT * (up(sdata) + up(sscale)) + up(pbytes) +
-                 up(small_bytes) + up(sizeof(Trs4State)) + up(sizeof(uint32_t));
-  if (cudaMalloc(&h->pool, total) != cudaSuccess) {
+  PoolLayout L(n_basis);
+  if (cudaMalloc(&h->pool, L.total) != cudaSuccess) {
     cudaGetLastError();
     delete h;
     return GDM_ERR_OOM;
@@ -657,24 +646,24 @@ gdm_status gdm_init(gdm_handle** out, int64_t n_basis, int64_t n_occ, int device
   uint8_t* p = static_cast<uint8_t*>(h->pool);
   for (int i = 0; i < F_COUNT; ++i) {
     h->f[i] = reinterpret_cast<double*>(p);
-    p += up(fbytes);
+    p += L.fbytes;
   }
   for (int i = 0; i < SL_COUNT; ++i) {
     h->sl[i].data = reinterpret_cast<__half*>(p);
-    p += up(sdata);
+    p += L.sdata;
     h->sl[i].row_scale = reinterpret_cast<double*>(p);
-    p += up(sscale);
+    p += L.sscale;
     h->sl[i].ld = static_cast<int>(h->ld);
     h->sl[i].rows_alloc = h->rows_alloc;
     h->sl[i].rows = static_cast<int>(n_basis);
     h->sl[i].cols = static_cast<int>(n_basis);
   }
   h->partials = reinterpret_cast<double*>(p);
-  p += up(pbytes);
+  p += L.pbytes;
   h->small = reinterpret_cast<double*>(p);
-  p += up(small_bytes);
+  p += L.small_bytes;
   h->st_dev = reinterpret_cast<Trs4State*>(p);
-  p += up(sizeof(Trs4State));
+  p += L.st_bytes;
   h->err_dev = reinterpret_cast<uint32_t*>(p);
   if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMallocHost(&h->host_buf, sizeof(double) * kSmall) != cudaSuccess ||
@@ -686,7 +675,7 @@ gdm_status gdm_init(gdm_handle** out, int64_t n_basis, int64_t n_occ, int device
     return GDM_ERR_CUDA;
   }
   h->stream = h->own_stream;
-  if (cudaMemsetAsync(h->pool, 0, total, h->stream) != cudaSuccess ||
+  if (cudaMemsetAsync(h->pool, 0, L.total, h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
     free_all(h);
     delete h;

@@ -1,0 +1,71 @@
+// Definition of the solver handle, shared by the handle API (engine.cu) and the batch /
+// server runtime (runtime.cu).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gdm.h"
+#include "gdm_internal.h"
+
+namespace gdm {
+
+enum FBuf { F_H, F_S, F_Z, F_ZT, F_X, F_X2, F_XN, F_T, F_U, F_V, F_COUNT };
+enum SBuf { SL_S, SL_Z, SL_ZT, SL_A, SL_B, SL_X, SL_X2, SL_W, SL_COUNT };
+constexpr int kSmall = 4096;  // doubles of small device scratch beyond the partials
+
+// Device bytes gdm_init allocates for capacity n (one cudaMalloc).
+size_t handle_pool_bytes(int64_t n);
+
+// Solve a handle whose capacity is at least n for a problem of size n with n_occ occupied
+// states: the buffers keep the capacity's leading dimension.  Drops S, H and Z.
+gdm_status handle_reconfigure(gdm_handle* h, int64_t n, int64_t n_occ);
+
+}  // namespace gdm
+
+struct gdm_handle {
+  int device = 0;
+  int64_t n = 0, n_occ = 0;
+  int64_t n_cap = 0;      // capacity the buffers were allocated for
+  int64_t ld = 0;         // leading dimension of every internal n x n buffer
+  int rows_alloc = 0;     // rows of slice buffers (multiple of 128)
+  cudaStream_t own_stream = nullptr, stream = nullptr;
+  gdm_precision prec = GDM_PREC_MIXED;
+  gdm::Precision phase[4] = {{2, 1, 12}, {4, 3, 9}, {4, 3, 9}, {3, 3, 12}};
+  double idem_tol = 1e-13, trace_tol = 1e-6;
+  bool trace_correct = true;
+  int max_ns = 100, max_purif = 200, n_refine = 2;
+
+  void* pool = nullptr;
+  double* f[gdm::F_COUNT] = {};
+  gdm::SliceBuf sl[gdm::SL_COUNT];
+  double* partials = nullptr;  // >= 5 * ceil(n/8) doubles
+  double* small = nullptr;     // kSmall doubles: coefficients, bounds, reductions
+  gdm::Trs4State* st_dev = nullptr;
+  uint32_t* err_dev = nullptr;
+  double* host_buf = nullptr;  // pinned: kSmall doubles
+  gdm::Trs4State* st_host = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  bool have_H = false, have_S = false, z_valid = false;
+  double z_err = 0.0;
+  struct HistRow {
+    double idem, trace, gamma;
+    int branch;
+  };
+  std::vector<HistRow> hist;  // purification history of the last solve
+  // optional timing of the sliced / FP64 product launches (CUDA events on the stream)
+  bool profiling = false;
+  struct Prof {
+    cudaEvent_t a, b;
+    double flops;
+    int kind;  // 0 sliced, 1 fp64
+  };
+  std::vector<Prof> prof_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  int64_t prof_launches[2] = {0, 0};
+  double prof_ms[2] = {0, 0}, prof_flops[2] = {0, 0};
+  std::string last_error;
+};
+

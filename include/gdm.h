@@ -147,6 +147,16 @@ gdm_status gdm_set_hamiltonian(gdm_handle* h, const double* H, int64_t ld, gdm_m
 gdm_status gdm_solve_dm(gdm_handle* h, double* P, int64_t ld, gdm_mem mem, double* energy,
                         gdm_info* info);
 
+/* Energy-weighted density matrix Q = P H P of the last successful (or GDM_ERR_NOT_CONVERGED)
+ * gdm_solve_dm, for the H and S of that solve (Sec. 2.6, Eq. energy_density_matrix: the
+ * eigenvalue-weighted sum over occupied orbitals, which equals P H P because C^T H C is the
+ * diagonal of eigenvalues).  As in the paper it is computed only when asked for, from H and P,
+ * with two products in the transform phase's format.  Q (n x n, leading dimension ld >= n) is
+ * host or device memory per `mem`; the caller owns it.  Blocks until Q has been written.
+ * Errors: GDM_ERR_STATE (no density matrix since the last gdm_set_hamiltonian/overlap,
+ * gdm_reinit, or a failed solve), GDM_ERR_ARG, GDM_ERR_CUDA, GDM_ERR_TIMEOUT. */
+gdm_status gdm_get_edm(gdm_handle* h, double* Q, int64_t ld, gdm_mem mem);
+
 /* Purification history of the last gdm_solve_dm: for iteration i < max_rows, idem[i] =
  * Tr(X_i - X_i^2), trace[i] = Tr X_i, gamma[i] and branch[i] (0: 2X - X^2, 1: X^2,
  * 2: F + gamma G, 3: McWeeny, -1: the stopping iteration, no step taken).  Any output pointer

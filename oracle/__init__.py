@@ -7,7 +7,8 @@ no code with it.
 Two parts:
   * `jacobi.c` (built into `_build/liboracle.so` with gcc + OpenMP): the plain definition of the
     result - Jacobi eigenpairs of S and of H~ = S^{-1/2} H S^{-1/2}, then P = C_occ C_occ^T
-    (Sec. 1 Eqs. evp, density_matrix; Sec. 2.2.2 Eq. ntpoly_lowdin).
+    (Sec. 1 Eqs. evp, density_matrix; Sec. 2.2.2 Eq. ntpoly_lowdin) and, on request, the
+    energy-weighted density matrix C_occ diag(eps) C_occ^T (Sec. 2.6, Eq. energy_density_matrix).
   * `steps.py` (numpy float64): the individual steps of the purification route written out in
     the paper's order (Eq. ntpoly_scale_hamiltonian initial guess, Eq. ntpoly_purification with
     the trace-resetting map the paper cites, Loewdin orthogonalisation), plus the closed forms
@@ -63,6 +64,9 @@ def _load():
             lib.oracle_density_matrix.argtypes = [ctypes.c_int64, ctypes.c_int64, dp, dp, dp,
                                                   dp, dp, dp, dp, dp]
             lib.oracle_density_matrix.restype = ctypes.c_int
+            lib.oracle_density_matrix_edm.argtypes = [ctypes.c_int64, ctypes.c_int64, dp, dp, dp,
+                                                      dp, dp, dp, dp, dp, dp]
+            lib.oracle_density_matrix_edm.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -106,18 +110,25 @@ def inv_sqrt(S):
     return Z, STATUS.get(st, str(st))
 
 
-def density_matrix(H, S, n_occ: int):
-    """Zero-temperature density matrix (Eq. density_matrix, f_l in {0,1}) of (H, S).
+def density_matrix(H, S, n_occ: int, edm: bool = False):
+    """Zero-temperature density matrix (Eq. density_matrix, f_l in {0,1}) of (H, S); with
+    edm=True also the energy-weighted density matrix q_ij = sum_l f_l eps_l c_il c_jl
+    (Eq. energy_density_matrix) as "Q".
 
-    Returns dict(P, energy, trace_ps, idem, gap, evals, status)."""
+    Returns dict(P, energy, trace_ps, idem, gap, evals, status[, Q])."""
     H = _f64(H)
     S = _f64(S)
     n = H.shape[0]
     P = np.empty((n, n))
+    Q = np.empty((n, n)) if edm else None
     w = np.empty(n)
     e, t, d, g = (ctypes.c_double(0) for _ in range(4))
-    st = _load().oracle_density_matrix(n, int(n_occ), _ptr(H), _ptr(S), _ptr(P),
-                                       ctypes.byref(e), ctypes.byref(t), ctypes.byref(d),
-                                       ctypes.byref(g), _ptr(w))
-    return dict(P=P, energy=e.value, trace_ps=t.value, idem=d.value, gap=g.value, evals=w,
-                status=STATUS.get(st, str(st)))
+    st = _load().oracle_density_matrix_edm(n, int(n_occ), _ptr(H), _ptr(S), _ptr(P),
+                                           ctypes.byref(e), ctypes.byref(t), ctypes.byref(d),
+                                           ctypes.byref(g), _ptr(w),
+                                           _ptr(Q) if edm else None)
+    out = dict(P=P, energy=e.value, trace_ps=t.value, idem=d.value, gap=g.value, evals=w,
+               status=STATUS.get(st, str(st)))
+    if edm:
+        out["Q"] = Q
+    return out

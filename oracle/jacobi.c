@@ -240,15 +240,43 @@ int oracle_inv_sqrt(int64_t n, const double *S, double *Z, double *s_min, double
 }
 
 /*
+ * Energy-weighted density matrix q_ij = sum_l f_l eps_l c_il c_jl (Sec. 2.6, Eq.
+ * energy_density_matrix) from C_occ (n x n_occ, leading dimension n_occ) and eps.
+ */
+static void energy_weighted(int64_t n, int64_t n_occ, const double *C, const double *eps,
+                            double *Q) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            double acc = 0.0;
+            for (int64_t l = 0; l < n_occ; ++l) acc += eps[l] * C[i * n_occ + l] * C[j * n_occ + l];
+            Q[i * n + j] = acc;
+        }
+    symmetrise(n, Q);
+}
+
+/*
  * Zero-temperature density matrix of (H, S) with n_occ occupied states (f_l in {0, 1}).
  * Outputs: P (n x n), *energy = sum of the n_occ lowest generalised eigenvalues = Tr(P H),
  * *trace_ps = Tr(P S), *idem = ||P S P - P||_F, *gap = lam[n_occ] - lam[n_occ-1] (0 if n_occ
  * is 0 or n), evals (optional, n ascending generalised eigenvalues).
  * Returns OR_OK, OR_NOT_SPD, OR_NO_GAP (outputs still written) or OR_NOT_CONVERGED.
  */
+int oracle_density_matrix_edm(int64_t n, int64_t n_occ, const double *H_in,
+                              const double *S_in, double *P, double *energy, double *trace_ps,
+                              double *idem, double *gap, double *evals, double *Q);
+
 int oracle_density_matrix(int64_t n, int64_t n_occ, const double *H_in, const double *S_in,
                           double *P, double *energy, double *trace_ps, double *idem,
                           double *gap, double *evals) {
+    return oracle_density_matrix_edm(n, n_occ, H_in, S_in, P, energy, trace_ps, idem, gap, evals,
+                                     NULL);
+}
+
+/* As oracle_density_matrix, plus the energy-weighted density matrix Q (n x n) when Q != NULL. */
+int oracle_density_matrix_edm(int64_t n, int64_t n_occ, const double *H_in,
+                              const double *S_in, double *P, double *energy, double *trace_ps,
+                              double *idem, double *gap, double *evals, double *Q) {
     if (n <= 0 || n_occ < 0 || n_occ > n || !H_in || !S_in || !P) return OR_ERR_ARG;
     const size_t nn = (size_t)n * (size_t)n;
     double *H = (double *)malloc(sizeof(double) * nn);
@@ -295,8 +323,10 @@ int oracle_density_matrix(int64_t n, int64_t n_occ, const double *H_in, const do
                 P[i * n + j] = acc;
             }
         symmetrise(n, P);
+        if (Q) energy_weighted(n, n_occ, T, lam, Q);
     } else {
         memset(P, 0, sizeof(double) * nn);
+        if (Q) memset(Q, 0, sizeof(double) * nn);
     }
 
     double e = 0.0;

@@ -174,6 +174,15 @@ def closed_form_dm(factors, n_occ):
     return sym(C @ C.T), float(np.sum(lam[:n_occ]))
 
 
+def closed_form_edm(factors, n_occ):
+    """Energy-weighted density matrix of the constructed input (Sec. 2.6, Eq.
+    energy_density_matrix): C = S^{-1/2} Q, Q_edm = C[:, :N] diag(lam[:N]) C[:, :N]^T."""
+    U, w, Q, lam = factors["S_U"], factors["S_w"], factors["Q"], factors["lam"]
+    Sm12 = (U * (1.0 / np.sqrt(w))[None, :]) @ U.T
+    C = Sm12 @ Q[:, :n_occ]
+    return sym((C * lam[:n_occ][None, :]) @ C.T)
+
+
 def closed_form_rows(factors, n_occ, rows):
     """Rows `rows` of the closed-form P (for spot checks at sizes where forming P on the CPU is
     slow): P[i, :] = (S^{-1/2} Q_occ)[i, :] (S^{-1/2} Q_occ)^T."""

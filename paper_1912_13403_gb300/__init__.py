@@ -97,6 +97,7 @@ _decl("gdm_set_stream", _int, [_vp, _vp])
 _decl("gdm_set_overlap", _int, [_vp, _vp, _i64, _int])
 _decl("gdm_set_hamiltonian", _int, [_vp, _vp, _i64, _int])
 _decl("gdm_solve_dm", _int, [_vp, _vp, _i64, _int, _dp, ctypes.POINTER(gdm_info)])
+_decl("gdm_get_edm", _int, [_vp, _vp, _i64, _int])
 _decl("gdm_get_history", _int, [_vp, _int, _dp, _dp, _dp, ctypes.POINTER(_int)])
 _decl("gdm_reinit", _int, [_vp])
 _decl("gdm_finalize", _int, [_vp])
@@ -224,6 +225,15 @@ class Handle:
         st = gdm_solve_dm(self._h, p, ld, mem, ctypes.byref(e), ctypes.byref(info))
         self._check(st, allow)
         return P, e.value, info.as_dict(), st
+
+    def edm(self, Q=None):
+        """Energy-weighted density matrix P H P of the last solve into Q (numpy or torch float64
+        n x n; allocated on the host when None).  Returns Q."""
+        if Q is None:
+            Q = np.empty((self.n, self.n))
+        q, ld, mem = _buf(Q)
+        self._check(gdm_get_edm(self._h, q, ld, mem))
+        return Q
 
     def history(self, max_rows=1000):
         """Purification history of the last solve: list of (idem, trace, gamma, branch)."""

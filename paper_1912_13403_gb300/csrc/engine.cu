@@ -581,6 +581,7 @@ gdm_status handle_reconfigure(gdm_handle* h, int64_t n, int64_t n_occ) {
   h->n_occ = n_occ;
   h->have_H = false;
   h->have_S = false;
+  h->have_P = false;
   h->z_valid = false;
   for (int i = 0; i < SL_COUNT; ++i) {
     h->sl[i].rows = static_cast<int>(n);
@@ -765,6 +766,7 @@ gdm_status gdm_set_stream(gdm_handle* h, void* stream) {
 gdm_status gdm_set_overlap(gdm_handle* h, const double* S, int64_t ld, gdm_mem mem) {
   if (h == nullptr) return GDM_ERR_ARG;
   h->have_S = false;
+  h->have_P = false;
   h->z_valid = false;
   gdm_status st = ingest(h, S, ld, mem, h->f[F_S]);
   if (st == GDM_OK) h->have_S = true;
@@ -774,6 +776,7 @@ gdm_status gdm_set_overlap(gdm_handle* h, const double* S, int64_t ld, gdm_mem m
 gdm_status gdm_set_hamiltonian(gdm_handle* h, const double* H, int64_t ld, gdm_mem mem) {
   if (h == nullptr) return GDM_ERR_ARG;
   h->have_H = false;
+  h->have_P = false;
   gdm_status st = ingest(h, H, ld, mem, h->f[F_H]);
   if (st == GDM_OK) h->have_H = true;
   return st;
@@ -790,8 +793,10 @@ gdm_status gdm_solve_dm(gdm_handle* h, double* P, int64_t ld, gdm_mem mem, doubl
   gdm_info local;
   memset(&local, 0, sizeof(local));
   CK(cudaEventRecord(h->ev0, h->stream));
+  h->have_P = false;
   gdm_status st = solve_core(h, &local, energy);
   CK(cudaEventRecord(h->ev1, h->stream));
+  h->have_P = (st == GDM_OK || st == GDM_ERR_NOT_CONVERGED);
   if (P != nullptr && (st == GDM_OK || st == GDM_ERR_NOT_CONVERGED)) {
     CK(cudaMemcpy2DAsync(P, sizeof(double) * ld, h->f[F_XN], sizeof(double) * h->ld,
                          sizeof(double) * h->n, static_cast<size_t>(h->n),
@@ -804,6 +809,37 @@ gdm_status gdm_solve_dm(gdm_handle* h, double* P, int64_t ld, gdm_mem mem, doubl
   if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) local.ms_total = ms;
   if (info) *info = local;
   return st;
+}
+
+gdm_status gdm_get_edm(gdm_handle* h, double* Q, int64_t ld, gdm_mem mem) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  if (!h->have_P || !h->have_H)
+    return set_err(h, GDM_ERR_STATE, "no density matrix: solve before asking for the EDM");
+  if (Q == nullptr) return set_err(h, GDM_ERR_ARG, "null output pointer");
+  if (ld < h->n) return set_err(h, GDM_ERR_ARG, "leading dimension < n");
+  if (mem != GDM_MEM_HOST && mem != GDM_MEM_DEVICE) return set_err(h, GDM_ERR_ARG, "bad mem kind");
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  CK(cudaMemsetAsync(h->err_dev, 0, sizeof(uint32_t), s));
+  // Q = P H P: T = P H (H symmetric, so it is its own transposed operand), then Q = T P^T with
+  // P symmetric; both products run in the transform phase's format.
+  double* P = h->f[F_XN];
+  double* H = h->f[F_H];
+  double* T = h->f[F_T];
+  double* Qd = h->f[F_V];
+  CK(slice(h, P, &h->sl[SL_A], GDM_PHASE_TRANSFORM));
+  CK(slice(h, H, &h->sl[SL_B], GDM_PHASE_TRANSFORM));
+  CK(product(h, {P, &h->sl[SL_A]}, {H, &h->sl[SL_B]}, T, nullptr, nullptr, 1.0, 0.0, 0.0, false,
+             GDM_PHASE_TRANSFORM));
+  CK(slice(h, T, &h->sl[SL_X], GDM_PHASE_TRANSFORM));
+  CK(product(h, {T, &h->sl[SL_X]}, {P, &h->sl[SL_A]}, Qd, nullptr, nullptr, 1.0, 0.0, 0.0, true,
+             GDM_PHASE_TRANSFORM));
+  CK(cudaMemcpy2DAsync(Q, sizeof(double) * ld, Qd, sizeof(double) * h->ld,
+                       sizeof(double) * h->n, static_cast<size_t>(h->n),
+                       mem == GDM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  collect_profile(h);
+  return check_device_error(h);
 }
 
 int gdm_get_history(const gdm_handle* h, int max_rows, double* idem, double* trace, double* gamma,
@@ -824,6 +860,7 @@ gdm_status gdm_reinit(gdm_handle* h) {
   if (h == nullptr) return GDM_ERR_ARG;
   h->have_H = false;
   h->have_S = false;
+  h->have_P = false;
   h->z_valid = false;
   return GDM_OK;
 }

@@ -49,6 +49,7 @@ struct gdm_handle {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
   bool have_H = false, have_S = false, z_valid = false;
+  bool have_P = false;  // F_XN holds the density matrix of the current H and S
   double z_err = 0.0;
   struct HistRow {
     double idem, trace, gamma;

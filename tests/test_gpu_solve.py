@@ -150,3 +150,66 @@ def test_error_paths(g):
         assert g.gdm_set_slices(h._h, 3, 5, 1, 0) == g.GDM_ERR_ARG
         assert g.gdm_set_slices(h._h, 3, 1, 2, 0) == g.GDM_ERR_ARG
         assert g.gdm_set_slices(h._h, 3, 3, 3, 13) == g.GDM_ERR_ARG
+
+
+# ------------------------------------------------------------------------------------------
+# Energy-weighted density matrix Q = P H P (Sec. 2.6, Eq. energy_density_matrix)
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_edm_matches_oracle(g, prec):
+    p = make_config0()
+    ref = oracle.density_matrix(p.H, p.S, p.n_occ, edm=True)
+    with g.Handle(p.n, p.n_occ) as h:
+        if prec == "fp64":
+            h.set_precision(g.GDM_PREC_FP64)
+        h.set_overlap(p.S)
+        h.set_hamiltonian(p.H)
+        P, e, info, st = h.solve()
+        Q = h.edm()
+    bar = 1e-9 if prec == "fp64" else REL_P
+    assert rel(Q, ref["Q"]) <= bar, info
+    assert rel(Q, steps.closed_form_edm(p.factors, p.n_occ)) <= bar
+    assert np.array_equal(Q, Q.T)
+    # Tr(Q S) is the band energy
+    assert abs(np.sum(Q * p.S) - ref["energy"]) <= bar * abs(ref["energy"])
+
+
+@pytest.mark.parametrize("n,n_occ", [(130, 33), (383, 96)])
+def test_edm_ragged_sizes_device_buffers(g, n, n_occ):
+    p = make_random_small(2000 + n, n, n_occ)
+    ref = oracle.density_matrix(p.H, p.S, n_occ, edm=True)
+    with g.Handle(n, n_occ) as h:
+        h.set_overlap(torch.from_numpy(p.S).cuda())
+        h.set_hamiltonian(torch.from_numpy(p.H).cuda())
+        h.solve()
+        Qd = torch.full((n, n + 3), float("nan"), dtype=torch.float64, device="cuda")
+        h.edm(Qd[:, :n])
+        Q = Qd[:, :n].cpu().numpy()
+        assert torch.isnan(Qd[:, n:]).all()        # nothing written beyond the n columns
+    assert rel(Q, ref["Q"]) <= REL_P
+
+
+def test_edm_state_errors(g):
+    p = make_config0(seed=5, n=128, n_occ=20)
+    with g.Handle(p.n, p.n_occ) as h:
+        with pytest.raises(g.GdmError) as ei:
+            h.edm()
+        assert ei.value.status == g.GDM_ERR_STATE
+        h.set_overlap(p.S)
+        h.set_hamiltonian(p.H)
+        h.solve()
+        Q1 = h.edm()
+        h.set_hamiltonian(1.5 * p.H)           # P no longer belongs to H
+        with pytest.raises(g.GdmError) as ei:
+            h.edm()
+        assert ei.value.status == g.GDM_ERR_STATE
+        h.solve()
+        Q2 = h.edm()
+        ref = oracle.density_matrix(1.5 * p.H, p.S, p.n_occ, edm=True)
+        assert rel(Q2, ref["Q"]) <= REL_P
+        assert rel(Q2, 1.5 * Q1) <= 10 * REL_P   # scaling H scales Q, P unchanged
+        h.reinit()
+        with pytest.raises(g.GdmError) as ei:
+            h.edm()
+        assert ei.value.status == g.GDM_ERR_STATE

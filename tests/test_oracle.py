@@ -121,6 +121,76 @@ def test_dm_golden_2x2():
         np.testing.assert_allclose(r["evals"], c["evals"], atol=1e-14, err_msg=c["name"])
 
 
+# ------------------------------------------------------------------------------------------
+# Energy-weighted density matrix (Sec. 2.6, Eq. energy_density_matrix)
+# ------------------------------------------------------------------------------------------
+
+def test_edm_golden_2x2():
+    with open(os.path.join(GOLDEN, "dm_2x2.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        r = oracle.density_matrix(np.array(c["H"]), np.array(c["S"]), c["n_occ"], edm=True)
+        np.testing.assert_allclose(r["Q"], np.array(c["Q"]), atol=1e-14, err_msg=c["name"])
+
+
+def test_edm_config0_closed_form():
+    p = make_config0()
+    r = oracle.density_matrix(p.H, p.S, p.n_occ, edm=True)
+    Qc = steps.closed_form_edm(p.factors, p.n_occ)
+    assert rel(r["Q"], Qc) <= 1e-11
+    # the P computed alongside is unchanged by asking for Q
+    assert np.array_equal(r["P"], oracle.density_matrix(p.H, p.S, p.n_occ)["P"])
+
+
+def test_edm_full_occupation_is_sinv_h_sinv():
+    # with every state occupied, C C^T = S^{-1} and Q = C diag(eps) C^T = S^{-1} H S^{-1}
+    p = make_random_small(77, 24, 5)
+    r = oracle.density_matrix(p.H, p.S, 24, edm=True)
+    Si = np.linalg.inv(p.S)
+    assert rel(r["Q"], Si @ p.H @ Si) <= 1e-11
+
+
+def test_edm_identities_on_unstructured_input():
+    # Q = P H P (C^T H C is diagonal), Tr(Q S) = sum of the occupied eigenvalues = Tr(P H),
+    # and Q S P = Q (the range of Q lies in the occupied subspace)
+    p = make_random_small(78, 40, 13)
+    r = oracle.density_matrix(p.H, p.S, 13, edm=True)
+    Q, P = r["Q"], r["P"]
+    assert rel(Q, P @ p.H @ P) <= 1e-11
+    assert abs(np.sum(Q * p.S) - np.sum(r["evals"][:13])) <= 1e-11 * np.abs(r["evals"]).sum()
+    assert abs(np.sum(Q * p.S) - r["energy"]) <= 1e-11 * abs(r["energy"])
+    assert rel(Q @ p.S @ P, Q) <= 1e-11
+    assert np.array_equal(Q, Q.T)
+
+
+def test_edm_zero_occupation_is_zero():
+    p = make_random_small(79, 10, 3)
+    r = oracle.density_matrix(p.H, p.S, 0, edm=True)
+    assert np.all(r["Q"] == 0.0)
+
+
+def test_edm_pins_catch_plausible_mistakes():
+    # each wrong formula below (a dropped factor, a missing occupation, the wrong eigenvalues)
+    # fails the closed-form pin that the oracle's Q passes
+    p = make_config0()
+    Qc = steps.closed_form_edm(p.factors, p.n_occ)
+    r = oracle.density_matrix(p.H, p.S, p.n_occ, edm=True)
+    P = r["P"]
+    Si = np.linalg.inv(p.S)
+    lam = p.factors["lam"]
+    U, w, Qf = p.factors["S_U"], p.factors["S_w"], p.factors["Q"]
+    C = ((U * (1.0 / np.sqrt(w))[None, :]) @ U.T) @ Qf[:, :p.n_occ]
+    wrong = {
+        "P H": P @ p.H,
+        "all states": Si @ p.H @ Si,
+        "unoccupied eigenvalues": (C * lam[p.n_occ:2 * p.n_occ][None, :]) @ C.T,
+        "S metric dropped": P @ p.S @ p.H @ p.S @ P,
+    }
+    assert rel(r["Q"], Qc) <= 1e-11
+    for name, Qw in wrong.items():
+        assert not rel(Qw, Qc) <= 1e-6, name
+
+
 def test_dm_full_occupation_is_inverse_overlap():
     p = make_random_small(12, 30, 30)
     r = oracle.density_matrix(p.H, p.S, 30)

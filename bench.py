@@ -127,6 +127,19 @@ def job_throughput(units_per_rank, total_ms_this_rank, device="cpu"):
     return world * units_per_rank / (t / 1e3), t
 
 
+PHASES = ("newton_schulz", "refine", "transform", "purify")
+
+# DRAM bytes (read + write) per purification product launch at n=4096 from one ncu capture of
+# the current sliced_gemm_kernel<3,32,4>; None until the kernel has been captured.
+PURIFY_TRAFFIC_N4096 = None
+
+
+def traffic_bytes(n):
+    if PURIFY_TRAFFIC_N4096 is None or n != 4096:
+        return None
+    return PURIFY_TRAFFIC_N4096
+
+
 def measured_peaks():
     """Roofline denominators: MEASURED_PEAKS.json when present, else the machine's fallback."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -313,7 +326,8 @@ def run_ours(args):
         for _ in range(args.warmup):
             _, e, info, st = step()
     torch.cuda.synchronize()
-    h.profile(0, reset=True)
+    for kind in range(6):
+        h.profile(kind, reset=True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -335,6 +349,7 @@ def run_ours(args):
     per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
     prof_launch, prof_ms, prof_flops = h.profile(0)
+    phase_prof = {name: h.profile(2 + ph) for ph, name in enumerate(PHASES)}
     value, total_ms = job_throughput(args.steps, total_ms, device="cuda")
 
     # accuracy of the last timed solve
@@ -383,6 +398,13 @@ def run_ours(args):
     peaks = measured_peaks()
     peak = peaks["bf16_tflops_sustained"]
     achieved = (prof_flops / (prof_ms / 1e3)) / 1e12 if prof_ms > 0 else 0.0
+    # the roofline's kernel: the purification products (sliced_gemm_kernel<3,32,4>), the
+    # largest share of the step's device time
+    pl, pms, pfl = phase_prof["purify"]
+    achieved_pu = (pfl / (pms / 1e3)) / 1e12 if pms > 0 else 0.0
+    per_phase = {name: {"launches_per_step": l / args.steps, "ms_per_step": ms / args.steps,
+                        "tflops": (fl / (ms / 1e3)) / 1e12 if ms > 0 else 0.0}
+                 for name, (l, ms, fl) in phase_prof.items()}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, cores, ns = cpu_baseline_sample(args.workload)
@@ -404,14 +426,21 @@ def run_ours(args):
                        "p99": per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)]},
         "accuracy": {"rel_frobenius_err": relerr, "abs_energy_err": abs(e - Ec),
                      "trace_err": info["trace_err"], "trace_err_raw": info["trace_err_raw"],
-                     "ns_iters": info["ns_iters"], "purif_iters": info["purif_iters"]},
+                     "ns_iters": info["ns_iters"], "refine_iters": info["refine_iters"],
+                     "z_err": info["z_err"], "idem_err": info["idem_err"],
+                     "purif_iters": info["purif_iters"]},
         "tflops_tensor_pipe": achieved,
         "gemm_ms_per_step": prof_ms / args.steps,
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if peak else None, "traffic": None,
-                     "kernel": "sliced_gemm_kernel (tcgen05 kind::f16, all launches of the step)",
+        "gemm_by_phase": per_phase,
+        "roofline": {"bound": "tensor", "achieved": achieved_pu, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved_pu / peak if peak else None,
+                     "traffic": traffic_bytes(n),
+                     "kernel": "sliced_gemm_kernel<3,32,4>: TRS4 products X X and X^2 W "
+                               "(tcgen05 kind::f16, 8 slice pairs, upper-triangle tiles)",
+                     "flops_per_launch": pfl / pl if pl else None,
+                     "ms_per_launch": pms / pl if pl else None,
                      "peak_source": "%s bf16 sustained (fp16 = bf16 rate)" % peaks["source"],
-                     "launches_per_step": prof_launch / args.steps},
+                     "launches_per_step": pl / args.steps},
         "fp64_gpu_path": fp64,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * n * n * 8,
                 "d2h_bytes_per_step": n * n * 8},

@@ -116,9 +116,10 @@ gdm_status gdm_set_trace_correction(gdm_handle* h, int enable);
  * product kernel on the handle's stream and folded into per-kind totals after each solve. */
 gdm_status gdm_set_profiling(gdm_handle* h, int enable);
 
-/* Totals since the last reset for kind 0 (sliced tensor-core products) or 1 (FP64 products):
- * launches, device milliseconds and tensor-pipe flops (slice pairs x computed tile area x 2K
- * for kind 0; computed tile area x 2K for kind 1).  reset != 0 zeroes the totals afterwards. */
+/* Totals since the last reset for kind 0 (sliced tensor-core products), 1 (FP64 products) or
+ * 2 + p (sliced products of gdm_phase p): launches, device milliseconds and tensor-pipe flops
+ * (slice pairs x computed tile area x 2K for sliced kinds; computed tile area x 2K for kind 1).
+ * reset != 0 zeroes the totals of that kind afterwards. */
 gdm_status gdm_get_profile(gdm_handle* h, int kind, int64_t* launches, double* ms, double* flops,
                            int reset);
 

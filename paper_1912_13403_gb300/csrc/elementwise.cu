@@ -292,14 +292,40 @@ __global__ void __launch_bounds__(kRowThreads)
   }
 }
 
+// x * (+-2^k) from the bit pattern (integer operations only): zero and subnormal x give 0,
+// Inf / NaN stay non-finite, results beyond the exponent range saturate to Inf.
+__device__ __forceinline__ double pow2_mul(double x, int k, bool neg) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int E = static_cast<int>((b >> 52) & 0x7FF);
+  const unsigned long long sign = (b & (1ULL << 63)) ^ (neg ? (1ULL << 63) : 0ULL);
+  if (E == 0) return 0.0;
+  if (E == 0x7FF) return __longlong_as_double(static_cast<long long>(b ^ (neg ? (1ULL << 63) : 0ULL)));
+  const int En = E + k;
+  if (En <= 0) return __longlong_as_double(static_cast<long long>(sign));
+  if (En >= 0x7FF) return __longlong_as_double(static_cast<long long>(sign | 0x7FF0000000000000ULL));
+  return __longlong_as_double(static_cast<long long>(
+      sign | (static_cast<unsigned long long>(En) << 52) | (b & ((1ULL << 52) - 1))));
+}
+
+// a = +-2^k exactly?
+__device__ __forceinline__ bool pow2_coef(double a, int& k, bool& neg) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(a));
+  const int E = static_cast<int>((b >> 52) & 0x7FF);
+  if (E == 0 || E == 0x7FF || (b & ((1ULL << 52) - 1)) != 0) return false;
+  k = E - 1023;
+  neg = (b >> 63) != 0;
+  return true;
+}
+
 // Row pass of the slicing, one warp per row: forms y = a X + b X2 + c I when (a, b, c) is not
 // (1, 0, 0) (FP64, written to Y), and writes the row scale 2^e > ||y|| from an FP32 norm of the
-// truncated values enlarged by 0.2% (NaN marks a row with NaN / Inf).
+// truncated values enlarged by 0.2% (NaN marks a row with NaN / Inf).  With dot != kDotNone it
+// also writes row_dot[row] = sum_j y_j^2 (kDotSelf) or sum_j y_j X2_j (kDotX2) in double-float.
 __global__ void __launch_bounds__(kRowsPerBlock * 32)
     form_norm_kernel(const double* __restrict__ X, int64_t ldx, const double* __restrict__ X2,
                      int64_t ldx2, int rows, int cols, const double* __restrict__ coef_dev,
                      double ha, double hb, double hc, double* Y, int64_t ldy, double* out_scale,
-                     const int* skip) {
+                     const int* skip, int dot, double* row_dot) {
   if (skip != nullptr && *skip != 0) return;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * kRowsPerBlock + w;
@@ -311,19 +337,46 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32)
     c = coef_dev[2];
   }
   const bool plain = (a == 1.0) && (X2 == nullptr || b == 0.0) && (c == 0.0);
+  // a power-of-two a without an X2 term scales by an exponent shift (no FP64 multiply)
+  int ak = 0;
+  bool aneg = false;
+  const bool a_pow2 = (X2 == nullptr || b == 0.0) && pow2_coef(a, ak, aneg);
   const double2* xr = reinterpret_cast<const double2*>(X + row * ldx);
   const double2* x2r = (X2 != nullptr) ? reinterpret_cast<const double2*>(X2 + row * ldx2)
                                         : nullptr;
   double2* yr = (Y != nullptr) ? reinterpret_cast<double2*>(Y + row * ldy) : nullptr;
   const int npairs = cols >> 1;
+  const bool need_x2 = x2r != nullptr && (!(plain || a_pow2) || dot == kDotX2);
   float ss = 0.0f;
-  for (int p = lane; p < npairs; p += 32) {
-    double2 y = xr[p];
-    if (!plain) {
+  DF acc{0.0f, 0.0f};
+  constexpr int U = 4;  // loads of U column pairs in flight per lane
+  for (int p0 = lane; p0 < npairs; p0 += 32 * U) {
+    double2 yv[U], x2v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = p0 + 32 * u;
+      yv[u] = make_double2(0.0, 0.0);
+      x2v[u] = make_double2(0.0, 0.0);
+      if (p < npairs) {
+        yv[u] = xr[p];
+        if (need_x2) x2v[u] = x2r[p];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+    const int p = p0 + 32 * u;
+    if (p >= npairs) break;
+    double2 y = yv[u];
+    const double2 x2 = x2v[u];
+    if (a_pow2) {
+      y.x = pow2_mul(y.x, ak, aneg);
+      y.y = pow2_mul(y.y, ak, aneg);
+      if (2 * p == row) y.x += c;
+      if (2 * p + 1 == row) y.y += c;
+    } else if (!plain) {
       y.x *= a;
       y.y *= a;
       if (x2r != nullptr) {
-        const double2 x2 = x2r[p];
         y.x = fma(b, x2.x, y.x);
         y.y = fma(b, x2.y, y.y);
       }
@@ -333,6 +386,20 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32)
     if (yr != nullptr) yr[p] = y;
     const float f0 = trunc_to_float(y.x), f1 = trunc_to_float(y.y);
     ss = fmaf(f0, f0, fmaf(f1, f1, ss));
+    if (dot != kDotNone) {
+      float yh, yl, ph, pl;
+      split_double(y.x, yh, yl);
+      if (dot == kDotX2) split_double(x2.x, ph, pl); else { ph = yh; pl = yl; }
+      acc = df_fma(acc, yh, yl, ph, pl);
+      split_double(y.y, yh, yl);
+      if (dot == kDotX2) split_double(x2.y, ph, pl); else { ph = yh; pl = yl; }
+      acc = df_fma(acc, yh, yl, ph, pl);
+    }
+    }
+  }
+  if (dot != kDotNone) {
+    acc = df_warp_sum(acc);
+    if (lane == 0) row_dot[row] = df_to_double(acc);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
@@ -347,33 +414,42 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32)
   }
 }
 
-// Element pass of the slicing, grid-stride over (row, column pair): the balanced base-2^bits
-// digits of round(y * 2^(11 - e + bits (nslice - 1))), e from the row scale; integer only.
-__global__ void __launch_bounds__(256)
+// Element pass of the slicing: block (row, chunk of 2 * 256 column pairs), two pairs per thread
+// with both loads issued first; the balanced base-2^bits digits of
+// round(y * 2^(11 - e + bits (nslice - 1))), e from the row scale; integer only.
+constexpr int kSliceThreads = 256;
+constexpr int kSlicePairsPerThread = 2;
+__global__ void __launch_bounds__(kSliceThreads)
     slice_pairs_kernel(const double* __restrict__ Yin, int64_t ldy, int rows, int cols,
                        const double* __restrict__ scale, __half* out, int64_t out_ld,
                        int64_t plane, int nslice, int bits, const int* skip) {
   if (skip != nullptr && *skip != 0) return;
+  const int row = blockIdx.x;
+  if (row >= rows) return;
   const int npairs = cols >> 1;
-  const int64_t total = static_cast<int64_t>(rows) * npairs;
   const long long H = 1LL << (bits - 1);
   const long long MASK = (1LL << bits) - 1;
   const int64_t plane2 = plane >> 1;
-  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
-       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int row = static_cast<int>(idx / npairs);
-    const int p = static_cast<int>(idx - static_cast<int64_t>(row) * npairs);
-    const double sc = scale[row];
-    long long n0 = 0, n1 = 0;
-    if (isfinite(sc)) {
-      const int e = static_cast<int>(
-          (static_cast<unsigned long long>(__double_as_longlong(sc)) >> 52) & 0x7FF) - 1023;
-      const int p2 = 11 - e + bits * (nslice - 1);
-      const double2 y = reinterpret_cast<const double2*>(Yin + row * ldy)[p];
-      n0 = fixed_point(y.x, p2);
-      n1 = fixed_point(y.y, p2);
-    }
-    __half2* orow = reinterpret_cast<__half2*>(out + row * out_ld);
+  const double sc = scale[row];
+  const bool ok = isfinite(sc);
+  const int e = static_cast<int>(
+      (static_cast<unsigned long long>(__double_as_longlong(sc)) >> 52) & 0x7FF) - 1023;
+  const int p2 = 11 - e + bits * (nslice - 1);
+  const double2* yrow = reinterpret_cast<const double2*>(Yin + row * ldy);
+  __half2* orow = reinterpret_cast<__half2*>(out + row * out_ld);
+  const int pbase = blockIdx.y * (kSliceThreads * kSlicePairsPerThread) + threadIdx.x;
+  double2 yv[kSlicePairsPerThread];
+#pragma unroll
+  for (int u = 0; u < kSlicePairsPerThread; ++u) {
+    const int p = pbase + u * kSliceThreads;
+    yv[u] = (ok && p < npairs) ? yrow[p] : make_double2(0.0, 0.0);
+  }
+#pragma unroll
+  for (int u = 0; u < kSlicePairsPerThread; ++u) {
+    const int p = pbase + u * kSliceThreads;
+    if (p >= npairs) break;
+    long long n0 = ok ? fixed_point(yv[u].x, p2) : 0;
+    long long n1 = ok ? fixed_point(yv[u].y, p2) : 0;
     for (int s = nslice - 1; s >= 1; --s) {
       const long long d0 = ((n0 + H) & MASK) - H, d1 = ((n1 + H) & MASK) - H;
       orow[s * plane2 + p] = __halves2half2(__int2half_rn(static_cast<int>(d0)),
@@ -617,7 +693,8 @@ __global__ void reduce_kernel(const double* partials, int nblocks, int nterms, d
 
 // TRS4 control: F(X) = X^2 (4X - 3X^2), G(X) = X^2 (I - X)^2, Tr F = 4 t3 - 3 t4,
 // Tr G = t2 - 2 t3 + t4, gamma = (N - Tr F) / Tr G; branches gamma > 6 -> 2X - X^2,
-// gamma < 0 -> X^2, else X^2 W + gamma X^2 with W = (4 - 2 gamma) X + (gamma - 3) X^2.
+// gamma < 0 -> X^2, else F + gamma G = X^2 W with W = gamma I + (4 - 2 gamma) X + (gamma - 3) X^2
+// (the gamma X^2 term folded into the right factor, so the product needs no addend).
 __global__ void trs4_control_kernel(const double* partials, int nblocks, Trs4State* st,
                                     double tol_idem) {
   __shared__ double red[32];
@@ -676,9 +753,9 @@ __global__ void trs4_control_kernel(const double* partials, int nblocks, Trs4Sta
     br = 2;
     st->coefW[0] = 4.0 - 2.0 * g;
     st->coefW[1] = g - 3.0;
-    st->coefW[2] = 0.0;
+    st->coefW[2] = g;
     st->gemm_coef[0] = 1.0;
-    st->gemm_coef[1] = g;
+    st->gemm_coef[1] = 0.0;
   }
   st->branch = br;
   const bool with_product = (br == 2 || br == 3);
@@ -826,9 +903,10 @@ __global__ void identity_kernel(double* A, int64_t lda, int n) {
 cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64_t ldx2,
                            int rows, int cols, const double* coef_dev, double ha, double hb,
                            double hc, double* Y, int64_t ldy, SliceBuf* out, int nslice,
-                           const int* skip, cudaStream_t stream, int bits) {
+                           const int* skip, cudaStream_t stream, int bits, int dot) {
   if (rows <= 0) return cudaSuccess;
   if (bits < 9 || bits > 12) return cudaErrorInvalidValue;
+  if (dot == kDotX2 && X2 == nullptr) return cudaErrorInvalidValue;
   __half* od = nullptr;
   double* osc = nullptr;
   int64_t old = 0, plane = 0;
@@ -842,6 +920,7 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
     out->cols = cols;
     out->nslice_valid = nslice;
     out->bits = bits;
+    out->dot_partner = nullptr;
   } else {
     nslice = 0;
   }
@@ -857,19 +936,21 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
   if (aligned && (host_plain || Y != nullptr || od == nullptr)) {
     // two passes: rows (form + norm) then elements (slices), both fully parallel
     const int nb = (rows + kRowsPerBlock - 1) / kRowsPerBlock;
+    const bool with_dot = dot != kDotNone && od != nullptr && out->row_dot != nullptr;
     count_launch();
-    form_norm_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(X, ldx, X2, ldx2, rows, cols,
-                                                            coef_dev, ha, hb, hc, Y, ldy,
-                                                            od != nullptr ? osc : nullptr, skip);
+    form_norm_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(
+        X, ldx, X2, ldx2, rows, cols, coef_dev, ha, hb, hc, Y, ldy,
+        od != nullptr ? osc : nullptr, skip, with_dot ? dot : kDotNone,
+        with_dot ? out->row_dot : nullptr);
+    if (with_dot) out->dot_partner = (dot == kDotX2) ? X2 : (Y != nullptr ? Y : X);
     if (od != nullptr) {
       const double* src = (Y != nullptr) ? Y : X;
       const int64_t lds = (Y != nullptr) ? ldy : ldx;
-      const int64_t total = static_cast<int64_t>(rows) * (cols / 2);
-      int blocks = static_cast<int>((total + 255) / 256);
-      if (blocks > 152 * 16) blocks = 152 * 16;
-      if (blocks < 1) blocks = 1;
+      const int per_block = kSliceThreads * kSlicePairsPerThread;
+      const dim3 grid(static_cast<unsigned>(rows),
+                      static_cast<unsigned>((cols / 2 + per_block - 1) / per_block));
       count_launch();
-      slice_pairs_kernel<<<blocks, 256, 0, stream>>>(src, lds, rows, cols, osc, od, old, plane,
+      slice_pairs_kernel<<<grid, kSliceThreads, 0, stream>>>(src, lds, rows, cols, osc, od, old, plane,
                                                      nslice, bits, skip);
     }
   } else if (aligned && cols <= 2 * kRowThreads * 16) {

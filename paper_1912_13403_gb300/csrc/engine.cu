@@ -96,6 +96,11 @@ void collect_profile(gdm_handle* h) {
       h->prof_ms[p.kind] += ms;
       h->prof_flops[p.kind] += p.flops;
       h->prof_launches[p.kind] += 1;
+      if (p.kind == 0) {
+        h->prof_ms[2 + p.phase] += ms;
+        h->prof_flops[2 + p.phase] += p.flops;
+        h->prof_launches[2 + p.phase] += 1;
+      }
     }
     h->ev_pool.push_back(p.a);
     h->ev_pool.push_back(p.b);
@@ -135,6 +140,10 @@ cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const dou
     a.diag = diag;
     a.coef = coef;
     a.err = h->err_dev;
+    // exact diagonal from the row dot products of the right operand's slicing pass, when that
+    // pass paired its rows with the left operand (X X, X^2 W, delta delta)
+    if (exact_diag && Bt.sl->row_dot != nullptr && Bt.sl->dot_partner == A.f)
+      a.diag_dot = Bt.sl->row_dot;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->profiling) {
       e0 = pool_event(h);
@@ -145,9 +154,9 @@ cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const dou
     if (e != cudaSuccess) return e;
     if (h->profiling) {
       cudaEventRecord(e1, h->stream);
-      h->prof_pending.push_back({e0, e1, sliced_flops(h, ph, sym), 0});
+      h->prof_pending.push_back({e0, e1, sliced_flops(h, ph, sym), 0, ph});
     }
-    if (!exact_diag) return cudaSuccess;
+    if (!exact_diag || a.diag_dot != nullptr) return cudaSuccess;
     e = diag_fix(A.f, h->ld, Bt.f, h->ld, C, h->ld, n, n, alpha, beta, D, h->ld, diag, coef,
                  h->stream);
     if (e != cudaSuccess || Ct == nullptr) return e;
@@ -184,17 +193,17 @@ cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const dou
     cudaEventRecord(e1, h->stream);
     const double nn = static_cast<double>(n);
     const double t = std::ceil(nn / 64.0);
-    h->prof_pending.push_back({e0, e1, (sym ? t * (t + 1) / 2 : t * t) * 64.0 * 64.0 * 2.0 * nn, 1});
+    h->prof_pending.push_back({e0, e1, (sym ? t * (t + 1) / 2 : t * t) * 64.0 * 64.0 * 2.0 * nn, 1, ph});
   }
   return e;
 }
 
 // Slice `src` (FP64) into `dst` in the format of phase `ph` (no-op when that phase is FP64).
-cudaError_t slice(gdm_handle* h, const double* src, SliceBuf* dst, int ph) {
+cudaError_t slice(gdm_handle* h, const double* src, SliceBuf* dst, int ph, int dot = kDotNone) {
   if (!sliced(h, ph)) return cudaSuccess;
   const int n = static_cast<int>(h->n);
   return form_and_slice(src, h->ld, nullptr, 0, n, n, nullptr, 1.0, 0.0, 0.0, nullptr, 0, dst,
-                        h->phase[ph].nslice, nullptr, h->stream, h->phase[ph].bits);
+                        h->phase[ph].nslice, nullptr, h->stream, h->phase[ph].bits, dot);
 }
 
 int bits_for(const gdm_handle* h, int ph) { return h->phase[ph].bits; }
@@ -280,11 +289,17 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
       break;
     }
     prev = res;
-    CK(slice(h, M, sM, GDM_PHASE_NEWTON_SCHULZ));
-    CK(slice(h, Mt, sMt, GDM_PHASE_NEWTON_SCHULZ));
-    CK(product(h, {M, sM}, {Y, sY}, Yn, nullptr, Y, -0.5, 1.5, 0.0, true,
+    // T = (3I - M)/2 and T^T, formed in place while slicing, so that Y <- T Y and Z <- T^T Z
+    // are plain products (no addend in the epilogue)
+    CK(form_and_slice(M, ld, nullptr, 0, n, n, nullptr, -0.5, 0.0, 1.5, M, ld,
+                      ns_sl > 0 ? sM : nullptr, ns_sl, nullptr, s,
+                      bits_for(h, GDM_PHASE_NEWTON_SCHULZ)));
+    CK(form_and_slice(Mt, ld, nullptr, 0, n, n, nullptr, -0.5, 0.0, 1.5, Mt, ld,
+                      ns_sl > 0 ? sMt : nullptr, ns_sl, nullptr, s,
+                      bits_for(h, GDM_PHASE_NEWTON_SCHULZ)));
+    CK(product(h, {M, sM}, {Y, sY}, Yn, nullptr, nullptr, 1.0, 0.0, 0.0, true,
                GDM_PHASE_NEWTON_SCHULZ));
-    CK(product(h, {Mt, sMt}, {Z, sZ}, Zn, nullptr, Z, -0.5, 1.5, 0.0, true,
+    CK(product(h, {Mt, sMt}, {Z, sZ}, Zn, nullptr, nullptr, 1.0, 0.0, 0.0, true,
                GDM_PHASE_NEWTON_SCHULZ));
     std::swap(Y, Yn);
     std::swap(Z, Zn);
@@ -319,7 +334,7 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
     derr = std::sqrt(d2);
     if (!std::isfinite(derr)) return set_err(h, GDM_ERR_NONFINITE, "non-finite Z^T S Z");
     if (r == nref || derr == 0.0) break;
-    CK(slice(h, Dl, &h->sl[SL_B], GDM_PHASE_REFINE));
+    CK(slice(h, Dl, &h->sl[SL_B], GDM_PHASE_REFINE, kDotSelf));
     CK(product(h, {Dl, &h->sl[SL_B]}, {Dl, &h->sl[SL_B]}, F, nullptr, Dl, 0.375, -0.5, 1.0, true,
                GDM_PHASE_REFINE, nullptr, true));                    // F = I - d/2 + 3d^2/8
     CK(slice(h, F, &h->sl[SL_A], GDM_PHASE_REFINE));
@@ -394,7 +409,7 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   double* Xn = h->f[F_XN];
   CK(form_and_slice(Ht, ld, nullptr, 0, n, n, h->small + SM_COEF_X0, 0, 0, 0, X, ld,
                     pu_sl > 0 ? &h->sl[SL_X] : nullptr, pu_sl, nullptr, s,
-                    bits_for(h, GDM_PHASE_PURIFY)));
+                    bits_for(h, GDM_PHASE_PURIFY), kDotSelf));
 
   // TRS4
   Trs4State init;
@@ -434,15 +449,16 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
     last_idem = t.idem;
     if (t.branch == 2 || t.branch == 3) {  // a product: F + gamma G, or McWeeny
       CK(slice(h, X2, &h->sl[SL_X2], GDM_PHASE_PURIFY));
-      CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefW)), 0, 0, 0, W, ld, pu_sl > 0 ? &h->sl[SL_W] : nullptr, pu_sl, nullptr, s,
-                        bits_for(h, GDM_PHASE_PURIFY)));
-      CK(product(h, {X2, &h->sl[SL_X2]}, {W, &h->sl[SL_W]}, Xn, nullptr, X2, 1.0, 0.0, 0.0, true,
-                 GDM_PHASE_PURIFY, st_field(h, offsetof(Trs4State, gemm_coef)), true));
-      CK(slice(h, Xn, &h->sl[SL_X], GDM_PHASE_PURIFY));
+      CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefW)), 0, 0, 0,
+                        W, ld, pu_sl > 0 ? &h->sl[SL_W] : nullptr, pu_sl, nullptr, s,
+                        bits_for(h, GDM_PHASE_PURIFY), kDotX2));
+      CK(product(h, {X2, &h->sl[SL_X2]}, {W, &h->sl[SL_W]}, Xn, nullptr, nullptr, 1.0, 0.0, 0.0,
+                 true, GDM_PHASE_PURIFY, nullptr, true));
+      CK(slice(h, Xn, &h->sl[SL_X], GDM_PHASE_PURIFY, kDotSelf));
     } else {
-      CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefX)), 0, 0, 0, Xn, ld,
-                        pu_sl > 0 ? &h->sl[SL_X] : nullptr, pu_sl, nullptr, s,
-                        bits_for(h, GDM_PHASE_PURIFY)));
+      CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefX)), 0, 0, 0,
+                        Xn, ld, pu_sl > 0 ? &h->sl[SL_X] : nullptr, pu_sl, nullptr, s,
+                        bits_for(h, GDM_PHASE_PURIFY), kDotSelf));
     }
     std::swap(X, Xn);
   }
@@ -556,7 +572,7 @@ struct PoolLayout {
     const size_t rows_alloc = static_cast<size_t>((n + 127) / 128 * 128);
     fbytes = up(sizeof(double) * ld * static_cast<size_t>(n));
     sdata = up(sizeof(__half) * 4 * ld * rows_alloc);
-    sscale = up(sizeof(double) * rows_alloc);
+    sscale = up(2 * sizeof(double) * rows_alloc);  // row scales, then row dot products
     pbytes = up(sizeof(double) * (kTraceTerms * static_cast<size_t>((n + 7) / 8) + 64));
     small_bytes = up(sizeof(double) * kSmall);
     st_bytes = up(sizeof(Trs4State));
@@ -587,6 +603,7 @@ gdm_status handle_reconfigure(gdm_handle* h, int64_t n, int64_t n_occ) {
     h->sl[i].rows = static_cast<int>(n);
     h->sl[i].cols = static_cast<int>(n);
     h->sl[i].nslice_valid = 0;
+    h->sl[i].dot_partner = nullptr;
   }
   return GDM_OK;
 }
@@ -653,6 +670,7 @@ gdm_status gdm_init(gdm_handle** out, int64_t n_basis, int64_t n_occ, int device
     h->sl[i].data = reinterpret_cast<__half*>(p);
     p += L.sdata;
     h->sl[i].row_scale = reinterpret_cast<double*>(p);
+    h->sl[i].row_dot = h->sl[i].row_scale + h->rows_alloc;
     p += L.sscale;
     h->sl[i].ld = static_cast<int>(h->ld);
     h->sl[i].rows_alloc = h->rows_alloc;
@@ -729,7 +747,7 @@ gdm_status gdm_set_profiling(gdm_handle* h, int enable) {
 
 gdm_status gdm_get_profile(gdm_handle* h, int kind, int64_t* launches, double* ms,
                            double* flops, int reset) {
-  if (h == nullptr || kind < 0 || kind > 1) return GDM_ERR_ARG;
+  if (h == nullptr || kind < 0 || kind >= gdm_handle::kProfKinds) return GDM_ERR_ARG;
   if (launches) *launches = h->prof_launches[kind];
   if (ms) *ms = h->prof_ms[kind];
   if (flops) *flops = h->prof_flops[kind];

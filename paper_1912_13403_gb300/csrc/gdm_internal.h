@@ -28,6 +28,11 @@ struct SliceBuf {
   int rows_alloc = 0;
   int nslice_valid = 0;          // slices written by the last slicing pass
   int bits = 12;                 // bits per slice after the first (9..12)
+  // Optional exact row dot products written by the slicing pass (double-float accurate):
+  // row_dot[i] = sum_k y_ik p_ik with p = dot_partner (y itself, or the X2 input of the pass).
+  // dot_partner == nullptr: row_dot holds nothing for the current slices.
+  double* row_dot = nullptr;     // [rows_alloc] or null (no storage)
+  const double* dot_partner = nullptr;
 };
 
 // Slice count and highest slice-pair order used by a product.
@@ -55,6 +60,7 @@ struct SlicedGemmArgs {
   double alpha = 1.0, beta = 0.0;
   double diag = 0.0;                  // added to the diagonal of C
   const double* coef = nullptr;       // optional device {alpha, beta}
+  const double* diag_dot = nullptr;   // optional: exact sum_k A_ik Bt_ik replaces C_ii's product
   const int* skip = nullptr;          // optional device flag: non-zero -> no-op launch
   uint32_t* err = nullptr;
   int tiles_n = 0, tiles_m = 0;
@@ -92,11 +98,15 @@ cudaError_t f64_gemm(const F64GemmArgs& a, cudaStream_t stream);
 // ---- elementwise / reduction kernels (elementwise.cu) --------------------------------------
 // Y = a*X + b*X2 + c*I with (a, b, c) from `coef_dev` (3 doubles) when non-null, else
 // (ha, hb, hc).  X2 may be null (then b is ignored).  Writes Y (FP64) when Y != null, and the
-// row slices of Y into `out` when out != null and nslice > 0.
+// row slices of Y into `out` when out != null and nslice > 0.  dot: 0 none, 1 the row dot
+// products sum_k y_ik^2, 2 sum_k y_ik X2_ik, written to out->row_dot when the buffer has one
+// (out->dot_partner then names the partner matrix; otherwise it is reset to null).
+enum { kDotNone = 0, kDotSelf = 1, kDotX2 = 2 };
 cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64_t ldx2,
                            int rows, int cols, const double* coef_dev, double ha, double hb,
                            double hc, double* Y, int64_t ldy, SliceBuf* out, int nslice,
-                           const int* skip, cudaStream_t stream, int bits = 12);
+                           const int* skip, cudaStream_t stream, int bits = 12,
+                           int dot = kDotNone);
 
 // Gershgorin bounds of a symmetric n x n matrix: writes {min_i(a_ii - r_i), max_i(a_ii + r_i)}
 // into out_dev[0..1].  `partials` holds >= 2 * ceil(n / 8) doubles.
@@ -125,9 +135,9 @@ struct Trs4State {
   double idem;            // Tr(X - X^2) = t1 - ||X||^2
   double idem_prev;
   double trG;
-  double coefW[3];        // W = a X + b X2 (+ c I)
+  double coefW[3];        // W = a X + b X2 + c I; X_next = X2 W
   double coefX[3];        // X_next = a X + b X2 for the branches without a product
-  double gemm_coef[2];    // X_next = alpha * X2 W + beta * X2
+  double gemm_coef[2];    // (1, 0): alpha and beta of the X2 W product (no addend)
   int branch;             // 0: 2X - X2, 1: X2, 2: F + gamma G, 3: McWeeny X2 (3I - 2X)
   int skip_gemm;          // 1 unless branch 2 or 3
   int skip_form_x;        // 1 when branch 2 or 3

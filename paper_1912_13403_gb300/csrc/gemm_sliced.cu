@@ -42,6 +42,7 @@ constexpr int kBN = 128;
 constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
 constexpr int kStageCols = 8;  // epilogue staging: 32 rows x 8 columns per warp
+constexpr int kPairsUsed = 10;  // most slice pairs of a format (4 slices, orders 0..3)
 
 template <int NSLICE, int BK, int STAGES>
 struct GemmCfg {
@@ -49,7 +50,6 @@ struct GemmCfg {
   static constexpr uint32_t kStageBytes = 2u * NSLICE * kTileBytes;   // A and B panels
   static constexpr uint32_t kStagingBytes = kEpiWarps * 32 * (kStageCols + 1) * 8;
   static constexpr uint32_t kSmemBytes = STAGES * kStageBytes + kStagingBytes + 1024;
-  static constexpr uint32_t kSwizzleBytes = BK * 2;                   // 128 or 64
   static_assert(BK == 64 || BK == 32, "BK must be 64 (128B swizzle) or 32 (64B swizzle)");
   static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 };
@@ -223,7 +223,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer (one thread) ----------------
+      // Everything but the stage base is fixed per launch: per-pair descriptor offsets (16-byte
+      // units), accumulator columns and whether the pair opens its order's accumulator; the
+      // unrolled issue loop is then two adds per MMA.
       constexpr uint32_t idesc = idesc_f16_f32(kBM, kBN);
+      const uint64_t desc_fixed = smem_desc(0u, BK);
+      uint32_t offa[kPairsUsed], offb[kPairsUsed], dcol[kPairsUsed], opens[kPairsUsed];
+      const int np = args.num_pairs;
+      uint32_t seen = 0;
+#pragma unroll
+      for (int p = 0; p < kPairsUsed; ++p) {
+        const int pp = p < np ? p : 0;
+        const int o = args.pair_o[pp];
+        offa[p] = (static_cast<uint32_t>(args.pair_s[pp]) * Cfg::kTileBytes) >> 4;
+        offb[p] = (static_cast<uint32_t>(args.pair_t[pp]) * Cfg::kTileBytes) >> 4;
+        dcol[p] = static_cast<uint32_t>(o * kBN);
+        opens[p] = ((seen >> o) & 1u) ? 0u : 1u;
+        if (p < np) seen |= 1u << o;
+      }
       int it = 0, tcount = 0;
       bool stop = false;
       for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x, ++tcount) {
@@ -233,7 +250,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        uint32_t started = 0;
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
@@ -243,16 +259,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t a0 = smem_u32(smem + s * Cfg::kStageBytes);
-          const uint32_t b0 = a0 + NSLICE * Cfg::kTileBytes;
-          for (int p = 0; p < args.num_pairs; ++p) {
-            const int sa = args.pair_s[p], sb = args.pair_t[p], o = args.pair_o[p];
-            const uint32_t d = tbase + static_cast<uint32_t>(o * kBN);
+          const uint64_t ad0 = desc_fixed | static_cast<uint64_t>((a0 >> 4) & 0x3FFFu);
+          const uint64_t bd0 =
+              desc_fixed | static_cast<uint64_t>(((a0 + NSLICE * Cfg::kTileBytes) >> 4) & 0x3FFFu);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              const uint64_t ad = smem_desc(a0 + sa * Cfg::kTileBytes + kk * 32, BK);
-              const uint64_t bd = smem_desc(b0 + sb * Cfg::kTileBytes + kk * 32, BK);
-              umma_f16(d, ad, bd, idesc, (started >> o) & 1u);
-              started |= 1u << o;
+          for (int p = 0; p < kPairsUsed; ++p) {
+            if (p < np) {
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint32_t acc = (kb > 0 || kk > 0 || opens[p] == 0u) ? 1u : 0u;
+                umma_f16(tbase + dcol[p], ad0 + offa[p] + 2u * kk, bd0 + offb[p] + 2u * kk, idesc,
+                         acc);
+              }
             }
           }
           umma_commit(&empty_bar[s]);  // stage reusable once these MMAs have read it
@@ -325,6 +343,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               } else {
                 val = sa * sb;  // a NaN / Inf row scale marks a non-finite input row
               }
+              // the diagonal from the exact row dot product of the slicing pass: the FP32
+              // accumulation truncates, and on the diagonal of a product of (nearly) parallel
+              // rows its residual-slice terms form a positive sum whose truncation biases C_ii
+              if (args.diag_dot != nullptr && grow == gcol) val = alpha * args.diag_dot[grow];
               if (args.D != nullptr)
                 val += beta * args.D[static_cast<int64_t>(gcol) * args.ldd + grow];
               if (grow == gcol) val += args.diag;
@@ -456,7 +478,7 @@ cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& B, const Precision& p
   if ((nslice > 1 && (A.bits != prec.bits || B.bits != prec.bits))) return cudaErrorInvalidValue;
   args.shift = prec.bits;
   if (A.cols != B.cols) return cudaErrorInvalidValue;  // contraction length
-  build_pairs(nslice, prec.max_order, &args);
+  if (build_pairs(nslice, prec.max_order, &args) > kPairsUsed) return cudaErrorInvalidValue;
   args.M = A.rows;
   args.N = B.rows;
   args.K = A.cols;

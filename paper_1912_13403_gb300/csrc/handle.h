@@ -62,11 +62,14 @@ struct gdm_handle {
     cudaEvent_t a, b;
     double flops;
     int kind;  // 0 sliced, 1 fp64
+    int phase;  // gdm_phase of the product
   };
+  // totals per kind: 0 sliced, 1 fp64, 2 + p sliced products of phase p
+  static constexpr int kProfKinds = 6;
   std::vector<Prof> prof_pending;
   std::vector<cudaEvent_t> ev_pool;
-  int64_t prof_launches[2] = {0, 0};
-  double prof_ms[2] = {0, 0}, prof_flops[2] = {0, 0};
+  int64_t prof_launches[kProfKinds] = {};
+  double prof_ms[kProfKinds] = {}, prof_flops[kProfKinds] = {};
   std::string last_error;
 };
 

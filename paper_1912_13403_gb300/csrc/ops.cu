@@ -195,12 +195,12 @@ gdm_status gdm_op_trs4_step(double* X, int64_t ld, int64_t n64, double n_occ, in
   if (!std::isfinite(host.gamma)) return GDM_ERR_NONFINITE;
   const char* base = reinterpret_cast<const char*>(st);
   if (host.branch == 2 || host.branch == 3) {
-    // W = (4 - 2g) X + (g - 3) X^2 ; X <- X^2 W + g X^2   (McWeeny: W = 3I - 2X, X <- X^2 W)
+    // W = g I + (4 - 2g) X + (g - 3) X^2 ; X <- X^2 W   (McWeeny: W = 3I - 2X)
     OPCK(form_and_slice(X, ld, X2, ld, n, n,
                         reinterpret_cast<const double*>(base + offsetof(Trs4State, coefW)), 0, 0,
                         0, W, ld, nullptr, 0, nullptr, s));
-    OPCK(run_product(sc, X2, ld, W, ld, X, ld, n, n, n, nslice, max_order, true, X2, ld, 1.0, 0.0,
-                     reinterpret_cast<const double*>(base + offsetof(Trs4State, gemm_coef)), err));
+    OPCK(run_product(sc, X2, ld, W, ld, X, ld, n, n, n, nslice, max_order, true, nullptr, 0, 1.0,
+                     0.0, nullptr, err));
   } else {
     OPCK(form_and_slice(X, ld, X2, ld, n, n,
                         reinterpret_cast<const double*>(base + offsetof(Trs4State, coefX)), 0, 0,

@@ -8,7 +8,8 @@ Two parts:
   * `jacobi.c` (built into `_build/liboracle.so` with gcc + OpenMP): the plain definition of the
     result - Jacobi eigenpairs of S and of H~ = S^{-1/2} H S^{-1/2}, then P = C_occ C_occ^T
     (Sec. 1 Eqs. evp, density_matrix; Sec. 2.2.2 Eq. ntpoly_lowdin) and, on request, the
-    energy-weighted density matrix C_occ diag(eps) C_occ^T (Sec. 2.6, Eq. energy_density_matrix).
+    energy-weighted density matrix C_occ diag(eps) C_occ^T (Sec. 2.6, Eq. energy_density_matrix);
+    `extrapolate_dm` takes a density matrix to a new overlap in Loewdin form (Sec. 2.7).
   * `steps.py` (numpy float64): the individual steps of the purification route written out in
     the paper's order (Eq. ntpoly_scale_hamiltonian initial guess, Eq. ntpoly_purification with
     the trace-resetting map the paper cites, Loewdin orthogonalisation), plus the closed forms
@@ -132,3 +133,25 @@ def density_matrix(H, S, n_occ: int, edm: bool = False):
     if edm:
         out["Q"] = Q
     return out
+
+
+def extrapolate_dm(P0, S0, S1):
+    """Density-matrix extrapolation to a new geometry in Loewdin form (Sec. 2.7, the Loewdin
+    counterpart of Eq. cholesky_extrapolation): P0 is taken to the orthogonal basis of S0 and
+    from there to the basis of S1,  P1 = S1^{-1/2} S0^{1/2} P0 S0^{1/2} S1^{-1/2},
+    with both square roots from Jacobi eigenpairs.  Returns (P1, status)."""
+    S0 = _f64(S0)
+    S1 = _f64(S1)
+    P0 = _f64(P0)
+    w0, U0, _, st0 = jacobi_eigh(S0)
+    w1, U1, _, st1 = jacobi_eigh(S1)
+    if st0 != "OK" or st1 != "OK":
+        return None, st0 if st0 != "OK" else st1
+    if w0.min() <= 0.0 or w1.min() <= 0.0:
+        return None, "NOT_SPD"
+    s0_half = (U0 * np.sqrt(w0)[None, :]) @ U0.T
+    s1_mhalf = (U1 * (1.0 / np.sqrt(w1))[None, :]) @ U1.T
+    T = s1_mhalf @ s0_half
+    P1 = T @ P0 @ T.T
+    return 0.5 * (P1 + P1.T), "OK"
+

@@ -15,6 +15,10 @@ Each function is the plain numpy statement of one step, in the paper's order:
      gamma > 6, X <- X^2 for gamma < 0                               (Eq. ntpoly_purification)
   5. back-transform P = S^{-1/2} P~ S^{-1/2}, and the outputs Tr(P S), Tr(P H)
                                                       (Sec. 4 "back-transforming the density matrix")
+The paper's Sec. 2.2.2 also names 2nd-order trace resetting, canonical purification and the
+generalised hole-particle canonical purification, without formulas; `trs2_step` and
+`canonical_step` state the maps of the cited methods that are built, `hole_particle_step` the
+hole-particle form that turns out to coincide with the canonical step.
 Closed forms for the synthetic inputs are at the end.  Matrix products are numpy matmul
 (a library primitive); there is no blocking, fusion or reordering beyond the formulas.
 """
@@ -103,6 +107,91 @@ def mcweeny(X):
     """McWeeny purification 3X^2 - 2X^3 (an idempotency fixer used for the final sweeps)."""
     X2 = X @ X
     return sym(3.0 * X2 - 2.0 * X2 @ X)
+
+
+# ------------------------------------------------------------------------------------------
+# the other purification maps the paper names (Sec. 2.2.2): 2nd-order trace resetting,
+# canonical purification, generalised (hole-particle) canonical purification
+# ------------------------------------------------------------------------------------------
+
+def trs2_step(X, n_occ):
+    """2nd-order trace-resetting step: of X^2 (lowers the trace) and 2X - X^2 (raises it) take the
+    one whose trace lands nearer N.  Returns (X_next, branch)."""
+    X2 = X @ X
+    t1 = float(np.trace(X))
+    t2 = float(np.trace(X2))
+    if abs(t2 - n_occ) <= abs(2.0 * t1 - t2 - n_occ):
+        return sym(X2), "X2"
+    return sym(2.0 * X - X2), "2X-X2"
+
+
+def canonical_initial_guess(Ht, n_occ, eps_min, eps_max):
+    """Initial guess of canonical purification: X0 = (lam/n)(mu I - H~) + (N/n) I with
+    mu = Tr H~ / n and lam = min(N / (eps_max - mu), (n - N) / (mu - eps_min)), so that
+    Tr X0 = N and the spectrum of X0 lies in [0, 1]."""
+    n = Ht.shape[0]
+    mu = float(np.trace(Ht)) / n
+    lam = min(n_occ / (eps_max - mu), (n - n_occ) / (mu - eps_min))
+    return (lam / n) * (mu * np.eye(n) - Ht) + (n_occ / n) * np.eye(n)
+
+
+def canonical_c(X):
+    """c = Tr(X^2 - X^3) / Tr(X - X^2), the weight both canonical maps take from X."""
+    X2 = X @ X
+    X3 = X2 @ X
+    return float(np.trace(X2 - X3)) / float(np.trace(X - X2))
+
+
+def canonical_step(X):
+    """Canonical purification step (keeps Tr X): with c = canonical_c(X),
+    c >= 1/2: X <- ((1 + c) X^2 - X^3) / c;  c < 1/2: X <- ((1 - 2c) X + (1 + c) X^2 - X^3) / (1 - c).
+    Returns (X_next, c)."""
+    c = canonical_c(X)
+    X2 = X @ X
+    X3 = X2 @ X
+    if c >= 0.5:
+        return sym(((1.0 + c) * X2 - X3) / c), c
+    return sym(((1.0 - 2.0 * c) * X + (1.0 + c) * X2 - X3) / (1.0 - c)), c
+
+
+def hole_particle_step(X):
+    """Hole-particle form of a trace-keeping cubic step, with the hole matrix I - X:
+    X <- X + beta (X^2 (I - X) - c X (I - X)),  c = Tr(X^2 (I - X)) / Tr(X (I - X)),
+    beta = 1 / max(c, 1 - c), the longest step for which the eigenvalue map stays monotone on
+    [0, 1].  With this beta it is the canonical step term by term (a pin checks that), which is
+    why no separate hole-particle method is built.  Returns (X_next, c, beta)."""
+    n = X.shape[0]
+    Xh = np.eye(n) - X
+    X2 = X @ X
+    c = float(np.trace(X2 @ Xh)) / float(np.trace(X @ Xh))
+    beta = 1.0 / max(c, 1.0 - c)
+    return sym(X + beta * (X2 @ Xh - c * (X @ Xh))), c, beta
+
+
+def purify(Ht, n_occ, method, max_iter=400, idem_tol=1e-13, bounds=None):
+    """Purification of an orthogonal-basis Hamiltonian with `method` in
+    {"trs4", "trs2", "canonical"}, from the method's own initial guess, until
+    ||X^2 - X||_F <= idem_tol * sqrt(n).  Returns (P~, iterations, traces of the iterates)."""
+    n = Ht.shape[0]
+    lo, hi = gershgorin_bounds(Ht) if bounds is None else bounds
+    if method in ("trs4", "trs2"):
+        X = initial_guess(Ht, lo, hi)
+    else:
+        X = canonical_initial_guess(Ht, n_occ, lo, hi)
+    traces = [float(np.trace(X))]
+    for it in range(max_iter):
+        if np.linalg.norm(X @ X - X) <= idem_tol * np.sqrt(n):
+            return X, it, traces
+        if method == "trs4":
+            X, _, _ = trs4_step(X, n_occ)
+        elif method == "trs2":
+            X, _ = trs2_step(X, n_occ)
+        elif method == "canonical":
+            X, _ = canonical_step(X)
+        else:
+            raise ValueError("unknown purification method %r" % (method,))
+        traces.append(float(np.trace(X)))
+    return X, max_iter, traces
 
 
 # ------------------------------------------------------------------------------------------

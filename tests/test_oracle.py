@@ -17,7 +17,7 @@ import scipy.linalg
 import oracle
 from oracle import steps
 from workloads import (make_config0, make_random_small, make_small_diag, make_spectrum_problem,
-                       haar_orthogonal)
+                       haar_orthogonal, make_geometry_step)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -191,6 +191,56 @@ def test_edm_pins_catch_plausible_mistakes():
         assert not rel(Qw, Qc) <= 1e-6, name
 
 
+# ------------------------------------------------------------------------------------------
+# Density-matrix extrapolation (Sec. 2.7, Loewdin form)
+# ------------------------------------------------------------------------------------------
+
+def test_extrapolation_closed_form_geometry_step():
+    # the step keeps the orthogonal-basis eigenvectors, so the extrapolated P0 is exactly the
+    # new geometry's density matrix S1^{-1/2} Q_occ Q_occ^T S1^{-1/2}
+    p0 = make_spectrum_problem(31, 48, 12, cond_S=50.0, gap=0.3)
+    p1 = make_geometry_step(p0, seed=5, eps=0.05)
+    P0 = steps.closed_form_dm(p0.factors, p0.n_occ)[0]
+    P1, st = oracle.extrapolate_dm(P0, p0.S, p1.S)
+    assert st == "OK"
+    assert rel(P1, steps.closed_form_dm(p1.factors, p1.n_occ)[0]) <= 1e-11
+    assert rel(P1, oracle.density_matrix(p1.H, p1.S, p1.n_occ)["P"]) <= 1e-10
+
+
+def test_extrapolation_same_overlap_is_identity_and_keeps_invariants():
+    p = make_random_small(81, 30, 9)
+    P0 = oracle.density_matrix(p.H, p.S, 9)["P"]
+    P1, st = oracle.extrapolate_dm(P0, p.S, p.S)
+    assert st == "OK" and rel(P1, P0) <= 1e-12
+    # a different overlap: P1 is again a projector in the new metric with the same count
+    q = make_random_small(82, 30, 9)
+    P1, st = oracle.extrapolate_dm(P0, p.S, q.S)
+    assert rel(P1 @ q.S @ P1, P1) <= 1e-11
+    assert abs(np.sum(P1 * q.S) - 9) <= 1e-11
+
+
+def test_extrapolation_diagonal_overlaps_by_hand():
+    # S0 = I, S1 = diag(s): P1_ij = P0_ij / sqrt(s_i s_j)
+    rng = np.random.default_rng(83)
+    n = 9
+    Q = haar_orthogonal(rng, n)
+    P0 = Q[:, :4] @ Q[:, :4].T
+    s1 = rng.uniform(0.5, 2.0, n)
+    P1, st = oracle.extrapolate_dm(P0, np.eye(n), np.diag(s1))
+    assert st == "OK"
+    np.testing.assert_allclose(P1, P0 / np.sqrt(np.outer(s1, s1)), atol=1e-13)
+    # a plausible mistake (S1^{-1} instead of S1^{-1/2}) breaks idempotency in the S1 metric
+    Pw = P0 / np.outer(s1, s1)
+    assert not rel(Pw @ np.diag(s1) @ Pw, Pw) <= 1e-6
+
+
+def test_extrapolation_rejects_indefinite_overlap():
+    S1 = np.eye(6)
+    S1[2, 2] = -0.5
+    P1, st = oracle.extrapolate_dm(np.eye(6) * 0.5, np.eye(6), S1)
+    assert P1 is None and st == "NOT_SPD"
+
+
 def test_dm_full_occupation_is_inverse_overlap():
     p = make_random_small(12, 30, 30)
     r = oracle.density_matrix(p.H, p.S, 30)
@@ -297,6 +347,75 @@ def test_trs4_purify_reaches_eigh_projector():
     Vo = V[:, :30]
     assert rel(Pt, Vo @ Vo.T) <= 1e-10
     assert it < 100 and all(0.0 <= g <= 6.0 or br != "F+gG" for g, br in hist)
+
+
+@pytest.mark.parametrize("method", ["trs4", "trs2", "canonical"])
+def test_purification_variants_reach_the_projector(method):
+    rng = np.random.default_rng(91)
+    n, N = 60, 17
+    Q = haar_orthogonal(rng, n)
+    lam = np.sort(rng.uniform(-3.0, 3.0, n))
+    lam[N:] += 0.5
+    Ht = (Q * lam) @ Q.T
+    X, it, traces = steps.purify(Ht, N, method)
+    assert it < 400
+    assert np.linalg.norm(X - Q[:, :N] @ Q[:, :N].T) <= 1e-11
+    if method == "canonical":
+        # canonical purification keeps the electron count at every iteration
+        assert max(abs(t - N) for t in traces) <= 1e-11
+
+
+def test_canonical_initial_guess_has_trace_n_and_unit_interval_spectrum():
+    rng = np.random.default_rng(92)
+    n, N = 40, 11
+    Q = haar_orthogonal(rng, n)
+    lam = rng.uniform(-5.0, 2.0, n)
+    Ht = (Q * lam) @ Q.T
+    lo, hi = steps.gershgorin_bounds(Ht)
+    X0 = steps.canonical_initial_guess(Ht, N, lo, hi)
+    w = np.linalg.eigvalsh(X0)
+    assert abs(np.trace(X0) - N) <= 1e-12
+    assert w.min() >= -1e-12 and w.max() <= 1.0 + 1e-12
+    # the map is decreasing in the energy: the lowest level gets the largest occupation
+    order = np.argsort(lam)
+    occ = np.array([Q[:, k] @ X0 @ Q[:, k] for k in order])
+    assert np.all(np.diff(occ) <= 1e-12)
+
+
+def test_canonical_and_trs2_steps_by_hand():
+    # X = diag(0.2, 0.9): Tr(X - X^2) = 0.25, Tr(X^2 - X^3) = 0.113, c = 0.452 < 1/2, so
+    # x <- ((1 - 2c) x + (1 + c) x^2 - x^3) / (1 - c):  0.2 -> 0.06928 / 0.548, 0.9 -> 0.53352 / 0.548
+    X = np.diag([0.2, 0.9])
+    Xn, c = steps.canonical_step(X)
+    assert abs(c - 0.452) <= 1e-15
+    np.testing.assert_allclose(np.diag(Xn), [0.06928 / 0.548, 0.53352 / 0.548], rtol=1e-14)
+    # X = diag(0.3, 0.95): c = (0.063 + 0.045125) / (0.21 + 0.0475) = 0.108125 / 0.2575 < 1/2 too;
+    # X = diag(0.6, 0.95): Tr(X-X^2) = 0.24 + 0.0475, Tr(X^2-X^3) = 0.144 + 0.045125, c > 1/2:
+    # x <- ((1 + c) x^2 - x^3) / c
+    X = np.diag([0.6, 0.95])
+    c = (0.144 + 0.045125) / (0.24 + 0.0475)
+    Xn, c2 = steps.canonical_step(X)
+    assert abs(c2 - c) <= 1e-15 and c > 0.5
+    np.testing.assert_allclose(np.diag(Xn), [((1 + c) * 0.36 - 0.216) / c,
+                                             ((1 + c) * 0.9025 - 0.857375) / c], rtol=1e-14)
+    # TRS2 with N = 1 on diag(0.2, 0.9): Tr X^2 = 0.85, Tr(2X - X^2) = 1.35 -> X^2 (|0.15| < |0.35|)
+    Xn, br = steps.trs2_step(np.diag([0.2, 0.9]), 1)
+    assert br == "X2"
+    np.testing.assert_allclose(np.diag(Xn), [0.04, 0.81], rtol=1e-15)
+    Xn, br = steps.trs2_step(np.diag([0.2, 0.5]), 1)   # 0.29 vs 1.11: 2X - X^2
+    assert br == "2X-X2"
+    np.testing.assert_allclose(np.diag(Xn), [0.36, 0.75], rtol=1e-15)
+
+
+def test_hole_particle_form_coincides_with_canonical():
+    rng = np.random.default_rng(93)
+    Q = haar_orthogonal(rng, 12)
+    for x in (rng.uniform(0.0, 1.0, 12), np.r_[rng.uniform(0.6, 1.0, 9), rng.uniform(0, 0.2, 3)]):
+        X = (Q * x) @ Q.T
+        Xc, c = steps.canonical_step(X)
+        Xh, c2, beta = steps.hole_particle_step(X)
+        assert abs(c - c2) <= 1e-14
+        assert np.linalg.norm(Xc - Xh) <= 1e-13
 
 
 def test_newton_schulz_and_refinement():

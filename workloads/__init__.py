@@ -16,4 +16,5 @@ from .synthetic import (  # noqa: F401
     make_request_problem,
     make_small_diag,
     make_random_small,
+    make_geometry_step,
 )

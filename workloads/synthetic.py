@@ -323,3 +323,32 @@ def _finish(be, H, S, n_occ, Q, lam, S_U, S_w, meta) -> Problem:
                    dict(Q=be.to_numpy(Q), lam=np.asarray(lam, dtype=np.float64),
                         S_U=be.to_numpy(S_U), S_w=np.asarray(S_w, dtype=np.float64)),
                    meta)
+
+
+def make_geometry_step(p: Problem, seed: int, eps: float = 0.02) -> Problem:
+    """The next geometry of a constructed problem: S rotated and rescaled a little,
+    S' = U' diag(w') U'^T with U' = U_s R (R the orthogonal factor of I + eps G) and
+    w' = w_s exp(eps xi), G and xi Gaussian; H' = S'^{1/2} Q diag(lam) Q^T S'^{1/2} keeps the
+    orthogonal-basis eigenvectors Q and the spectrum lam of `p`.  (Then the Loewdin-form
+    extrapolation of p's density matrix is exactly the density matrix of the new geometry.)"""
+    f = p.factors
+    if f is None:
+        raise ValueError("make_geometry_step needs a problem built from factors")
+    rng = np.random.default_rng(seed)
+    n = p.n
+    G = rng.standard_normal((n, n))
+    R, r = np.linalg.qr(np.eye(n) + eps * G)
+    d = np.sign(np.diag(r))
+    d[d == 0] = 1.0
+    R = R * d[None, :]
+    S_U = np.asarray(f["S_U"]) @ R
+    S_w = np.asarray(f["S_w"]) * np.exp(eps * rng.standard_normal(n))
+    Q = np.asarray(f["Q"])
+    lam = np.asarray(f["lam"])
+    be = _Np()
+    H, S = _assemble(be, Q, lam, S_U, S_w)
+    meta = dict(p.meta)
+    meta.update(config=str(p.meta.get("config", "")) + "+step", step_seed=seed, step_eps=eps,
+                cond_S=float(S_w.max() / S_w.min()))
+    return _finish(be, H, S, p.n_occ, Q, lam, S_U, S_w, meta)
+

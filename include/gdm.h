@@ -158,6 +158,20 @@ gdm_status gdm_solve_dm(gdm_handle* h, double* P, int64_t ld, gdm_mem mem, doubl
  * gdm_reinit, or a failed solve), GDM_ERR_ARG, GDM_ERR_CUDA, GDM_ERR_TIMEOUT. */
 gdm_status gdm_get_edm(gdm_handle* h, double* Q, int64_t ld, gdm_mem mem);
 
+/* Density-matrix extrapolation to a new geometry (Sec. 2.7; the Loewdin counterpart of Eq.
+ * cholesky_extrapolation): takes the last solve's P0 to the orthogonal basis and from there to
+ * the basis of the new overlap, P1 = Z1 (Z0^{-1} P0 Z0^{-T}) Z1^T with Z^T S Z = I from the
+ * Newton-Schulz route (Z ~ S^{-1/2}, so P1 ~ S1^{-1/2} S0^{1/2} P0 S0^{1/2} S1^{-1/2}).  P1 is
+ * again a projector in the S1 metric with Tr(P1 S1) = n_occ: an initial guess for the density
+ * of the next SCF cycle, not a solution.  S_new (n x n, leading dimension lds >= n, host or
+ * device per mem_s) becomes the handle's overlap as with gdm_set_overlap, and its Z is computed
+ * and cached for the next solve; the Hamiltonian is dropped (set the new one before solving).
+ * P (leading dimension ldp >= n, per mem_p) is owned by the caller.  Blocks until P is written.
+ * Errors: GDM_ERR_STATE (no solve since the last overlap change), GDM_ERR_ARG,
+ * GDM_ERR_NONFINITE, GDM_ERR_NOT_SPD, GDM_ERR_CUDA, GDM_ERR_TIMEOUT. */
+gdm_status gdm_extrapolate_dm(gdm_handle* h, const double* S_new, int64_t lds, gdm_mem mem_s,
+                              double* P, int64_t ldp, gdm_mem mem_p);
+
 /* Purification history of the last gdm_solve_dm: for iteration i < max_rows, idem[i] =
  * Tr(X_i - X_i^2), trace[i] = Tr X_i, gamma[i] and branch[i] (0: 2X - X^2, 1: X^2,
  * 2: F + gamma G, 3: McWeeny, -1: the stopping iteration, no step taken).  Any output pointer

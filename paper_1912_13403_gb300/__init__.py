@@ -98,6 +98,7 @@ _decl("gdm_set_overlap", _int, [_vp, _vp, _i64, _int])
 _decl("gdm_set_hamiltonian", _int, [_vp, _vp, _i64, _int])
 _decl("gdm_solve_dm", _int, [_vp, _vp, _i64, _int, _dp, ctypes.POINTER(gdm_info)])
 _decl("gdm_get_edm", _int, [_vp, _vp, _i64, _int])
+_decl("gdm_extrapolate_dm", _int, [_vp, _vp, _i64, _int, _vp, _i64, _int])
 _decl("gdm_get_history", _int, [_vp, _int, _dp, _dp, _dp, ctypes.POINTER(_int)])
 _decl("gdm_reinit", _int, [_vp])
 _decl("gdm_finalize", _int, [_vp])
@@ -234,6 +235,17 @@ class Handle:
         q, ld, mem = _buf(Q)
         self._check(gdm_get_edm(self._h, q, ld, mem))
         return Q
+
+    def extrapolate(self, S_new, P=None):
+        """New geometry: S_new becomes the overlap (its Z is computed and cached) and the last
+        solve's density matrix is extrapolated to it in Loewdin form.  Returns P (numpy or torch
+        float64 n x n; allocated on the host when None)."""
+        if P is None:
+            P = np.empty((self.n, self.n))
+        s, lds, ms = _buf(S_new)
+        p, ldp, mp = _buf(P)
+        self._check(gdm_extrapolate_dm(self._h, s, lds, ms, p, ldp, mp))
+        return P
 
     def history(self, max_rows=1000):
         """Purification history of the last solve: list of (idem, trace, gamma, branch)."""

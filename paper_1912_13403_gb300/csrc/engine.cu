@@ -860,6 +860,50 @@ gdm_status gdm_get_edm(gdm_handle* h, double* Q, int64_t ld, gdm_mem mem) {
   return check_device_error(h);
 }
 
+gdm_status gdm_extrapolate_dm(gdm_handle* h, const double* S_new, int64_t lds, gdm_mem mem_s,
+                              double* P, int64_t ldp, gdm_mem mem_p) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  if (!h->have_P) return set_err(h, GDM_ERR_STATE, "no density matrix to extrapolate: solve first");
+  if (P == nullptr) return set_err(h, GDM_ERR_ARG, "null output pointer");
+  if (ldp < h->n) return set_err(h, GDM_ERR_ARG, "leading dimension < n");
+  if (mem_p != GDM_MEM_HOST && mem_p != GDM_MEM_DEVICE)
+    return set_err(h, GDM_ERR_ARG, "bad mem kind");
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  const int64_t ld = h->ld;
+  CK(cudaMemsetAsync(h->err_dev, 0, sizeof(uint32_t), s));
+  // X0 = Z0^{-1} P0 Z0^{-T}, the last solve's projector in the orthogonal basis, is still in
+  // F_X; keep it in F_H (the Hamiltonian belongs to the old geometry and is dropped)
+  CK(cudaMemcpyAsync(h->f[F_H], h->f[F_X], sizeof(double) * ld * h->n, cudaMemcpyDeviceToDevice,
+                     s));
+  h->have_H = false;
+  h->have_P = false;
+  h->have_S = false;
+  h->z_valid = false;
+  gdm_status st = ingest(h, S_new, lds, mem_s, h->f[F_S]);
+  if (st != GDM_OK) return st;
+  h->have_S = true;
+  st = compute_z(h, nullptr);  // Z1 for the new overlap, cached for the next solve
+  if (st != GDM_OK) return st;
+  // P1 = Z1 X0 Z1^T (the back-transform of the solve, applied to X0)
+  double* X0 = h->f[F_H];
+  Op Z = {h->f[F_Z], &h->sl[SL_Z]};
+  CK(slice(h, X0, &h->sl[SL_X], GDM_PHASE_TRANSFORM));
+  CK(product(h, Z, {X0, &h->sl[SL_X]}, h->f[F_T], nullptr, nullptr, 1.0, 0.0, 0.0, false,
+             GDM_PHASE_TRANSFORM));
+  CK(slice(h, h->f[F_T], &h->sl[SL_A], GDM_PHASE_TRANSFORM));
+  double* P1 = h->f[F_XN];
+  CK(product(h, {h->f[F_T], &h->sl[SL_A]}, Z, P1, nullptr, nullptr, 1.0, 0.0, 0.0, true,
+             GDM_PHASE_TRANSFORM));
+  CK(cudaMemcpy2DAsync(P, sizeof(double) * ldp, P1, sizeof(double) * ld, sizeof(double) * h->n,
+                       static_cast<size_t>(h->n),
+                       mem_p == GDM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                       s));
+  CK(cudaStreamSynchronize(s));
+  collect_profile(h);
+  return check_device_error(h);
+}
+
 int gdm_get_history(const gdm_handle* h, int max_rows, double* idem, double* trace, double* gamma,
                     int* branch) {
   if (h == nullptr) return 0;

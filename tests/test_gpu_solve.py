@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 import oracle
 from oracle import steps
 from workloads import (make_config0, make_random_small, make_spectrum_problem, make_config2,
-                       make_request_problem)
+                       make_request_problem, make_geometry_step)
 
 pytestmark = pytest.mark.gpu
 
@@ -213,3 +213,53 @@ def test_edm_state_errors(g):
         with pytest.raises(g.GdmError) as ei:
             h.edm()
         assert ei.value.status == g.GDM_ERR_STATE
+
+
+# ------------------------------------------------------------------------------------------
+# Density-matrix extrapolation to a new geometry (Sec. 2.7, Loewdin form)
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_extrapolation_matches_closed_form_and_warm_z(g, prec):
+    p0 = make_spectrum_problem(41, 384, 96, cond_S=100.0, gap=0.3)
+    p1 = make_geometry_step(p0, seed=7, eps=0.03)
+    bar = 1e-9 if prec == "fp64" else REL_P
+    with g.Handle(p0.n, p0.n_occ) as h:
+        if prec == "fp64":
+            h.set_precision(g.GDM_PREC_FP64)
+        h.set_overlap(p0.S)
+        h.set_hamiltonian(p0.H)
+        P0, _, _, _ = h.solve()
+        P1 = h.extrapolate(p1.S)
+        # the step keeps the orthogonal-basis projector: P1 is the new geometry's answer
+        assert rel(P1, steps.closed_form_dm(p1.factors, p1.n_occ)[0]) <= bar
+        ref, st = oracle.extrapolate_dm(P0, p0.S, p1.S)
+        assert st == "OK" and rel(P1, ref) <= bar
+        assert abs(np.sum(P1 * p1.S) - p1.n_occ) <= 1e-7
+        # the overlap and its Z carry over; the Hamiltonian does not
+        with pytest.raises(g.GdmError) as ei:
+            h.solve()
+        assert ei.value.status == g.GDM_ERR_STATE
+        h.set_hamiltonian(p1.H)
+        P, e, info, st = h.solve()
+        assert info["ns_iters"] == 0
+        assert rel(P, steps.closed_form_dm(p1.factors, p1.n_occ)[0]) <= bar
+
+
+def test_extrapolation_general_overlaps_device_buffers(g):
+    p = make_random_small(3001, 200, 50)
+    q = make_random_small(3002, 200, 50)
+    ref0 = oracle.density_matrix(p.H, p.S, 50)
+    with g.Handle(200, 50) as h:
+        with pytest.raises(g.GdmError) as ei:
+            h.extrapolate(q.S)
+        assert ei.value.status == g.GDM_ERR_STATE
+        h.set_overlap(torch.from_numpy(p.S).cuda())
+        h.set_hamiltonian(torch.from_numpy(p.H).cuda())
+        h.solve()
+        Pd = torch.empty((200, 200), dtype=torch.float64, device="cuda")
+        h.extrapolate(torch.from_numpy(q.S).cuda(), Pd)
+        P1 = Pd.cpu().numpy()
+    ref, st = oracle.extrapolate_dm(ref0["P"], p.S, q.S)
+    assert rel(P1, ref) <= REL_P
+    assert rel(P1 @ q.S @ P1, P1) <= 10 * REL_P

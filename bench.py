@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-fp64-ref", action="store_true", help="skip the all-FP64 GPU solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the TRS2 / canonical purification solves")
     ap.add_argument("--concurrency", type=int, default=4, help="batch / server worker count")
     ap.add_argument("--requests", type=int, default=200, help="config4: requests per phase")
     ap.add_argument("--rate", type=float, default=200.0, help="config4: offered req/s")
@@ -395,6 +397,37 @@ def run_ours(args):
         h3.close()
         del P3
 
+    # the other purification maps of the paper (Sec. 2.2.2) on the same input and harness
+    variants = None
+    if not args.no_variants and rank == 0:
+        variants = {}
+        for name, code in (("trs2", g.GDM_PURIFY_TRS2), ("canonical", g.GDM_PURIFY_CANONICAL)):
+            hv = g.Handle(n, n_occ, device=local)
+            hv.set_stream(stream)
+            hv.set_purification(code)
+            times = []
+            with torch.cuda.stream(stream):
+                for k in range(3):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    hv.reinit()
+                    hv.set_overlap(S)
+                    hv.set_hamiltonian(H)
+                    _, ev, infov, stv = hv.solve(P)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    if k > 0:
+                        times.append(e0.elapsed_time(e1))
+            variants[name] = {
+                "ms_per_solve": sum(times) / len(times), "purif_iters": infov["purif_iters"],
+                "rel_frobenius_err": float(torch.linalg.norm(P - Pc) / torch.linalg.norm(Pc)),
+                "trace_err": infov["trace_err"], "status": stv}
+            hv.close()
+        variants["trs4"] = {"ms_per_solve": total_ms / args.steps,
+                            "purif_iters": info["purif_iters"], "rel_frobenius_err": relerr,
+                            "trace_err": info["trace_err"], "status": st}
+
     peaks = measured_peaks()
     peak = peaks["bf16_tflops_sustained"]
     achieved = (prof_flops / (prof_ms / 1e3)) / 1e12 if prof_ms > 0 else 0.0
@@ -442,6 +475,7 @@ def run_ours(args):
                      "peak_source": "%s bf16 sustained (fp16 = bf16 rate)" % peaks["source"],
                      "launches_per_step": pl / args.steps},
         "fp64_gpu_path": fp64,
+        "purification_variants": variants,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * n * n * 8,
                 "d2h_bytes_per_step": n * n * 8},
         "gpu_launches": launches,

@@ -61,6 +61,20 @@ typedef enum { GDM_MEM_HOST = 0, GDM_MEM_DEVICE = 1 } gdm_mem;
  * GDM_PREC_FP64: every product in plain FP64 on the CUDA cores (the reference path). */
 typedef enum { GDM_PREC_FP64 = 0, GDM_PREC_MIXED = 1 } gdm_precision;
 
+/* Purification map (Sec. 2.2.2 names all three; Sec. 4, Table 1 uses TRS4):
+ *   GDM_PURIFY_TRS4      4th-order trace resetting from X0 = (eps_max I - H~)/(eps_max - eps_min)
+ *   GDM_PURIFY_TRS2      2nd-order trace resetting (X^2 or 2X - X^2, whichever trace is nearer
+ *                        n_occ) from the same X0
+ *   GDM_PURIFY_CANONICAL canonical purification (keeps Tr X = n_occ) from
+ *                        X0 = (lam/n)(mu I - H~) + (n_occ/n) I, mu = Tr H~ / n,
+ *                        lam = min(n_occ/(eps_max - mu), (n - n_occ)/(mu - eps_min)).
+ * All three finish with McWeeny steps once every eigenvalue is within 0.113 of 0 or 1. */
+typedef enum {
+  GDM_PURIFY_TRS4 = 0,
+  GDM_PURIFY_TRS2 = 1,
+  GDM_PURIFY_CANONICAL = 2
+} gdm_purification;
+
 /* Phases whose slice format can be tuned with gdm_set_slices. */
 typedef enum {
   GDM_PHASE_NEWTON_SCHULZ = 0, /* coupled Newton-Schulz iterations for S^{-1/2} */
@@ -92,6 +106,9 @@ gdm_status gdm_init(gdm_handle** h, int64_t n_basis, int64_t n_occ, int device);
 
 /* Choose the product arithmetic (default GDM_PREC_MIXED).  Invalidates a cached Z. */
 gdm_status gdm_set_precision(gdm_handle* h, gdm_precision prec);
+
+/* Select the purification map for later solves (default GDM_PURIFY_TRS4).  Errors: GDM_ERR_ARG. */
+gdm_status gdm_set_purification(gdm_handle* h, gdm_purification method);
 
 /* Slice format of one phase in GDM_PREC_MIXED: nslice in 1..4 FP16 slices per operand, slice
  * pairs up to order max_order (0..3, <= 2*(nslice-1)), and slice_bits in 9..12 bits for every
@@ -166,6 +183,10 @@ gdm_status gdm_get_edm(gdm_handle* h, double* Q, int64_t ld, gdm_mem mem);
  * of the next SCF cycle, not a solution.  S_new (n x n, leading dimension lds >= n, host or
  * device per mem_s) becomes the handle's overlap as with gdm_set_overlap, and its Z is computed
  * and cached for the next solve; the Hamiltonian is dropped (set the new one before solving).
+ * Z equals S^{-1/2} up to a rotation left by the Newton-Schulz rounding, so P1 deviates from the
+ * symmetric-root formula by that rotation (~1e-4 relative with the default 2-slice Newton-Schulz
+ * format at cond(S) ~ 100; select a 3-slice format with gdm_set_slices for ~1e-8); it is a
+ * projector in the S1 metric with the right count either way.
  * P (leading dimension ldp >= n, per mem_p) is owned by the caller.  Blocks until P is written.
  * Errors: GDM_ERR_STATE (no solve since the last overlap change), GDM_ERR_ARG,
  * GDM_ERR_NONFINITE, GDM_ERR_NOT_SPD, GDM_ERR_CUDA, GDM_ERR_TIMEOUT. */

@@ -27,6 +27,7 @@ GDM_OK, GDM_ERR_ARG, GDM_ERR_STATE, GDM_ERR_NOT_SPD, GDM_ERR_NONFINITE, GDM_ERR_
     GDM_ERR_NOT_CONVERGED, GDM_ERR_OOM, GDM_ERR_BUDGET, GDM_ERR_TIMEOUT, GDM_ERR_CUDA = range(11)
 GDM_MEM_HOST, GDM_MEM_DEVICE = 0, 1
 GDM_PREC_FP64, GDM_PREC_MIXED = 0, 1
+GDM_PURIFY_TRS4, GDM_PURIFY_TRS2, GDM_PURIFY_CANONICAL = 0, 1, 2
 GDM_PHASE_NEWTON_SCHULZ, GDM_PHASE_REFINE, GDM_PHASE_TRANSFORM, GDM_PHASE_PURIFY = range(4)
 
 
@@ -86,6 +87,7 @@ def _decl(name, res, args):
 
 _decl("gdm_init", _int, [ctypes.POINTER(_vp), _i64, _i64, _int])
 _decl("gdm_set_precision", _int, [_vp, _int])
+_decl("gdm_set_purification", _int, [_vp, _int])
 _decl("gdm_set_slices", _int, [_vp, _int, _int, _int, _int])
 _decl("gdm_set_tolerance", _int, [_vp, _dbl, _dbl])
 _decl("gdm_set_max_iter", _int, [_vp, _int, _int])
@@ -178,6 +180,10 @@ class Handle:
 
     def set_precision(self, prec):
         return self._check(gdm_set_precision(self._h, prec))
+
+    def set_purification(self, method):
+        """GDM_PURIFY_TRS4 (default), GDM_PURIFY_TRS2 or GDM_PURIFY_CANONICAL."""
+        return self._check(gdm_set_purification(self._h, method))
 
     def set_slices(self, phase, nslice, max_order, slice_bits=0):
         return self._check(gdm_set_slices(self._h, phase, nslice, max_order, slice_bits))

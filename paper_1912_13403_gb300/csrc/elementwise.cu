@@ -105,12 +105,76 @@ __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
   }
   hi = __uint_as_float(sign | (static_cast<unsigned>(ef) << 23) |
                        static_cast<unsigned>((b >> 29) & 0x7FFFFF));
+  // lo = rem * 2^(E-1075) for the 29 mantissa bits below hi, truncated to 24 bits and built
+  // from its bits (no conversion instruction)
   const unsigned rem = static_cast<unsigned>(b & ((1ULL << 29) - 1));
-  const int el = E - 1075 + 127;  // 2^(E-1075) as a float
-  lo = (el > 0 && rem != 0) ? __int2float_rn(static_cast<int>(rem)) *
-                                  __uint_as_float(static_cast<unsigned>(el) << 23)
-                            : 0.0f;
-  if (sign) lo = -lo;
+  lo = 0.0f;
+  if (rem != 0) {
+    const int msb = 31 - __clz(rem);          // 0..28
+    const int el = E - 1075 + msb + 127;      // biased exponent of lo
+    if (el > 0) {
+      const unsigned mant = (msb >= 23) ? (rem >> (msb - 23)) : (rem << (23 - msb));
+      lo = __uint_as_float(sign | (static_cast<unsigned>(el) << 23) | (mant & 0x7FFFFFu));
+    }
+  }
+}
+
+// Balanced base-2^bits digits of N = round(|y| 2^p) (nearest, ties to even), top digit first,
+// with the sign of y applied: |y| 2^p = sum_s d[s] 2^(bits (nslice - 1 - s)), |d[s]| <= 2^(bits-1)
+// for s >= 1 and |d[0]| <= 2^11 when |y| < 2^(11 + bits (nslice - 1) - p).  From the bit
+// pattern yb with integer operations: the rounding is one 64-bit add and shift, each digit a
+// bit field plus a carry.
+__device__ __forceinline__ void slice_digits(long long yb, int p, int nslice, int bits, int* d) {
+  const unsigned long long ub = static_cast<unsigned long long>(yb);
+  const int E = static_cast<int>((ub >> 52) & 0x7FF);
+  unsigned long long mant = ub & ((1ULL << 52) - 1);
+  int Ee = E;
+  if (E != 0) mant |= (1ULL << 52); else Ee = 1;
+  int r = 1075 - Ee - p;  // >= 6 when |y| is below the row scale (at most 36 digit bits)
+  if (r < 1) r = 1;        // not reached for a valid scale; keeps the shifts defined
+  unsigned long long N = 0;
+  if (r < 64) N = (mant + ((1ULL << (r - 1)) - 1) + ((mant >> r) & 1ULL)) >> r;
+  const int H = 1 << (bits - 1);
+  const unsigned MASK = (1u << bits) - 1u;
+  int carry = 0;
+#pragma unroll
+  for (int s = 3; s >= 1; --s) {
+    if (s < nslice) {
+      const int u = static_cast<int>(static_cast<unsigned>(N >> (bits * (nslice - 1 - s))) & MASK) +
+                    carry;
+      carry = (u >= H) ? 1 : 0;
+      d[s] = u - (carry << bits);
+    }
+  }
+  d[0] = static_cast<int>(N >> (bits * (nslice - 1))) + carry;
+  if (yb < 0) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) d[s] = -d[s];
+  }
+}
+
+// Two integers |m| <= 2048 as an FP16 pair (low half = m0): the integers become floats by the
+// 1.5 * 2^23 bias trick (an integer add and an FP32 subtract) and are packed by one conversion.
+__device__ __forceinline__ uint32_t half_pair(int m0, int m1) {
+  const float f0 = __int_as_float(0x4B400000 + m0) - 12582912.0f;
+  const float f1 = __int_as_float(0x4B400000 + m1) - 12582912.0f;
+  const __half2 h = __floats2half2_rn(f0, f1);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// FP16 bit pattern of an integer |m| <= 2048 (exact), from integer operations only.
+__device__ __forceinline__ uint32_t int_to_half_bits(int m) {
+  if (m == 0) return 0u;
+  const uint32_t sgn = (m < 0) ? 0x8000u : 0u;
+  const uint32_t a = static_cast<uint32_t>(m < 0 ? -m : m);
+  const int e = 31 - __clz(a);  // 0..11
+  const uint32_t mant = (e <= 10) ? (a << (10 - e)) : (a >> (e - 10));
+  return sgn | (static_cast<uint32_t>(e + 15) << 10) | (mant & 0x3FFu);
+}
+
+// two FP16 integers packed as a half2 word (low half = first)
+__device__ __forceinline__ uint32_t pack_half_ints(long long m0, long long m1) {
+  return int_to_half_bits(static_cast<int>(m0)) | (int_to_half_bits(static_cast<int>(m1)) << 16);
 }
 
 struct DF {
@@ -165,9 +229,8 @@ __device__ __forceinline__ float trunc_to_float(double y) {
 }
 
 // round(y * 2^p) as a signed 64-bit integer (nearest, ties to even), p chosen by the caller so
-// that |y * 2^p| < 2^62; exact from the bit pattern.
-__device__ __forceinline__ long long fixed_point(double y, int p) {
-  const long long b = __double_as_longlong(y);
+// that |y * 2^p| < 2^62; exact from the bit pattern b of y.
+__device__ __forceinline__ long long fixed_point_bits(long long b, int p) {
   const int E = static_cast<int>((b >> 52) & 0x7FF);
   long long mant = b & ((1LL << 52) - 1);
   int Ee = E;
@@ -271,23 +334,21 @@ __global__ void __launch_bounds__(kRowThreads)
   const int p2 = shift_sh;
   const long long H = 1LL << (bits - 1);
   const long long MASK = (1LL << bits) - 1;
-  __half2* orow = reinterpret_cast<__half2*>(out + row * out_ld);
+  uint32_t* orow = reinterpret_cast<uint32_t*>(out + row * out_ld);
   const int64_t plane2 = plane >> 1;
 #pragma unroll
   for (int i = 0; i < MAXV; ++i) {
     const int p = threadIdx.x + i * kRowThreads;
     if (p < npairs) {
-      long long n0 = (p2 > -1000) ? fixed_point(v[i].x, p2) : 0;
-      long long n1 = (p2 > -1000) ? fixed_point(v[i].y, p2) : 0;
+      long long n0 = (p2 > -1000) ? fixed_point_bits(__double_as_longlong(v[i].x), p2) : 0;
+      long long n1 = (p2 > -1000) ? fixed_point_bits(__double_as_longlong(v[i].y), p2) : 0;
       for (int s = nslice - 1; s >= 1; --s) {
         const long long d0 = ((n0 + H) & MASK) - H, d1 = ((n1 + H) & MASK) - H;
-        orow[s * plane2 + p] = __halves2half2(__int2half_rn(static_cast<int>(d0)),
-                                              __int2half_rn(static_cast<int>(d1)));
+        orow[s * plane2 + p] = pack_half_ints(d0, d1);
         n0 = (n0 - d0) >> bits;
         n1 = (n1 - d1) >> bits;
       }
-      orow[p] = __halves2half2(__int2half_rn(static_cast<int>(n0)),
-                               __int2half_rn(static_cast<int>(n1)));
+      orow[p] = pack_half_ints(n0, n1);
     }
   }
 }
@@ -320,8 +381,83 @@ __device__ __forceinline__ bool pow2_coef(double a, int& k, bool& neg) {
 // Row pass of the slicing, one warp per row: forms y = a X + b X2 + c I when (a, b, c) is not
 // (1, 0, 0) (FP64, written to Y), and writes the row scale 2^e > ||y|| from an FP32 norm of the
 // truncated values enlarged by 0.2% (NaN marks a row with NaN / Inf).  With dot != kDotNone it
-// also writes row_dot[row] = sum_j y_j^2 (kDotSelf) or sum_j y_j X2_j (kDotX2) in double-float.
-__global__ void __launch_bounds__(kRowsPerBlock * 32)
+// also writes row_dot[row] = sum_j y_j^2 (kDotSelf), sum_j y_j X2_j (kDotX2) or sum_j y_j X_j
+// (kDotX) in double-float.
+// y_ii + c for the pair p that holds the diagonal element of `row`.  Kept out of line so that the
+// FP64 add is a real branch taken once per row, not an if-converted instruction on every element
+// (GB300 issues FP64 at about 1/64 of the FP32 rate).
+__device__ __noinline__ double2 add_on_diagonal(double2 y, int p, int row, double c) {
+  if (2 * p == row) y.x += c;
+  else y.y += c;
+  return y;
+}
+
+// v - 1, out of line for the same reason (the identity's diagonal in a residual)
+__device__ __noinline__ double minus_one(double v) { return v - 1.0; }
+
+enum { kFormPlain = 0, kFormPow2 = 1, kFormGeneral = 2 };
+
+// One warp's pass over a row: form y, write it, accumulate the FP32 norm and the optional
+// double-float row dot product.  MODE picks the forming arithmetic: kFormPlain y = x, kFormPow2
+// y = +-2^k x (exponent shift), kFormGeneral y = a x + b x2 (FP64); c I is added in a branch.
+template <int MODE>
+__device__ __forceinline__ void form_norm_row(const double2* __restrict__ xr,
+                                              const double2* __restrict__ x2r, double2* yr,
+                                              int npairs, int row, int lane, double a, double b,
+                                              int ak, bool aneg, bool has_c, double c, int dot,
+                                              float& ss, DF& acc) {
+  const bool need_x2 = x2r != nullptr && (MODE == kFormGeneral || dot == kDotX2);
+  constexpr int U = 4;  // loads of U column pairs in flight per lane
+  for (int p0 = lane; p0 < npairs; p0 += 32 * U) {
+    double2 xv[U], x2v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = p0 + 32 * u;
+      xv[u] = make_double2(0.0, 0.0);
+      x2v[u] = make_double2(0.0, 0.0);
+      if (p < npairs) {
+        xv[u] = xr[p];
+        if (need_x2) x2v[u] = x2r[p];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = p0 + 32 * u;
+      if (p >= npairs) break;
+      double2 y = xv[u];
+      if (MODE == kFormPow2) {
+        y.x = pow2_mul(y.x, ak, aneg);
+        y.y = pow2_mul(y.y, ak, aneg);
+      } else if (MODE == kFormGeneral) {
+        y.x *= a;
+        y.y *= a;
+        if (x2r != nullptr) {
+          y.x = fma(b, x2v[u].x, y.x);
+          y.y = fma(b, x2v[u].y, y.y);
+        }
+      }
+      if (has_c && (2 * p == row || 2 * p + 1 == row)) y = add_on_diagonal(y, p, row, c);
+      if (yr != nullptr) yr[p] = y;
+      const float f0 = trunc_to_float(y.x), f1 = trunc_to_float(y.y);
+      ss = fmaf(f0, f0, fmaf(f1, f1, ss));
+      if (dot != kDotNone) {
+        float yh, yl, ph, pl;
+        split_double(y.x, yh, yl);
+        if (dot == kDotX2) split_double(x2v[u].x, ph, pl);
+        else if (dot == kDotX) split_double(xv[u].x, ph, pl);
+        else { ph = yh; pl = yl; }
+        acc = df_fma(acc, yh, yl, ph, pl);
+        split_double(y.y, yh, yl);
+        if (dot == kDotX2) split_double(x2v[u].y, ph, pl);
+        else if (dot == kDotX) split_double(xv[u].y, ph, pl);
+        else { ph = yh; pl = yl; }
+        acc = df_fma(acc, yh, yl, ph, pl);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kRowsPerBlock * 32, 4)
     form_norm_kernel(const double* __restrict__ X, int64_t ldx, const double* __restrict__ X2,
                      int64_t ldx2, int rows, int cols, const double* __restrict__ coef_dev,
                      double ha, double hb, double hc, double* Y, int64_t ldy, double* out_scale,
@@ -336,67 +472,30 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32)
     b = coef_dev[1];
     c = coef_dev[2];
   }
-  const bool plain = (a == 1.0) && (X2 == nullptr || b == 0.0) && (c == 0.0);
-  // a power-of-two a without an X2 term scales by an exponent shift (no FP64 multiply)
+  // the forming arithmetic, decided once per warp (uniform)
   int ak = 0;
   bool aneg = false;
-  const bool a_pow2 = (X2 == nullptr || b == 0.0) && pow2_coef(a, ak, aneg);
+  const bool no_x2 = (X2 == nullptr || b == 0.0);
+  const bool has_c = (c != 0.0);
+  int mode = kFormGeneral;
+  if (no_x2 && a == 1.0) mode = kFormPlain;
+  else if (no_x2 && pow2_coef(a, ak, aneg)) mode = kFormPow2;
   const double2* xr = reinterpret_cast<const double2*>(X + row * ldx);
   const double2* x2r = (X2 != nullptr) ? reinterpret_cast<const double2*>(X2 + row * ldx2)
                                         : nullptr;
   double2* yr = (Y != nullptr) ? reinterpret_cast<double2*>(Y + row * ldy) : nullptr;
   const int npairs = cols >> 1;
-  const bool need_x2 = x2r != nullptr && (!(plain || a_pow2) || dot == kDotX2);
   float ss = 0.0f;
   DF acc{0.0f, 0.0f};
-  constexpr int U = 4;  // loads of U column pairs in flight per lane
-  for (int p0 = lane; p0 < npairs; p0 += 32 * U) {
-    double2 yv[U], x2v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int p = p0 + 32 * u;
-      yv[u] = make_double2(0.0, 0.0);
-      x2v[u] = make_double2(0.0, 0.0);
-      if (p < npairs) {
-        yv[u] = xr[p];
-        if (need_x2) x2v[u] = x2r[p];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-    const int p = p0 + 32 * u;
-    if (p >= npairs) break;
-    double2 y = yv[u];
-    const double2 x2 = x2v[u];
-    if (a_pow2) {
-      y.x = pow2_mul(y.x, ak, aneg);
-      y.y = pow2_mul(y.y, ak, aneg);
-      if (2 * p == row) y.x += c;
-      if (2 * p + 1 == row) y.y += c;
-    } else if (!plain) {
-      y.x *= a;
-      y.y *= a;
-      if (x2r != nullptr) {
-        y.x = fma(b, x2.x, y.x);
-        y.y = fma(b, x2.y, y.y);
-      }
-      if (2 * p == row) y.x += c;
-      if (2 * p + 1 == row) y.y += c;
-    }
-    if (yr != nullptr) yr[p] = y;
-    const float f0 = trunc_to_float(y.x), f1 = trunc_to_float(y.y);
-    ss = fmaf(f0, f0, fmaf(f1, f1, ss));
-    if (dot != kDotNone) {
-      float yh, yl, ph, pl;
-      split_double(y.x, yh, yl);
-      if (dot == kDotX2) split_double(x2.x, ph, pl); else { ph = yh; pl = yl; }
-      acc = df_fma(acc, yh, yl, ph, pl);
-      split_double(y.y, yh, yl);
-      if (dot == kDotX2) split_double(x2.y, ph, pl); else { ph = yh; pl = yl; }
-      acc = df_fma(acc, yh, yl, ph, pl);
-    }
-    }
-  }
+  if (mode == kFormPlain)
+    form_norm_row<kFormPlain>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, dot, ss,
+                              acc);
+  else if (mode == kFormPow2)
+    form_norm_row<kFormPow2>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, dot, ss,
+                             acc);
+  else
+    form_norm_row<kFormGeneral>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, dot,
+                                ss, acc);
   if (dot != kDotNone) {
     acc = df_warp_sum(acc);
     if (lane == 0) row_dot[row] = df_to_double(acc);
@@ -407,7 +506,7 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32)
     if (ss > 0.0f && isfinite(ss)) {
       int e = 0;
       frexpf(sqrtf(ss * 1.002f) * 1.0001f, &e);  // 2^e > ||y|| with margin
-      out_scale[row] = ldexp(1.0, e);
+      out_scale[row] = __longlong_as_double(static_cast<long long>(e + 1023) << 52);  // 2^e
     } else {
       out_scale[row] = isfinite(ss) ? 1.0 : __longlong_as_double(0x7FF8000000000000LL);
     }
@@ -427,38 +526,36 @@ __global__ void __launch_bounds__(kSliceThreads)
   const int row = blockIdx.x;
   if (row >= rows) return;
   const int npairs = cols >> 1;
-  const long long H = 1LL << (bits - 1);
-  const long long MASK = (1LL << bits) - 1;
   const int64_t plane2 = plane >> 1;
-  const double sc = scale[row];
-  const bool ok = isfinite(sc);
-  const int e = static_cast<int>(
-      (static_cast<unsigned long long>(__double_as_longlong(sc)) >> 52) & 0x7FF) - 1023;
+  // the row scale and the values are handled as bit patterns: no FP64 instruction here
+  const unsigned long long scb =
+      static_cast<unsigned long long>(reinterpret_cast<const long long*>(scale)[row]);
+  const int Es = static_cast<int>((scb >> 52) & 0x7FF);
+  const bool ok = Es != 0x7FF;
+  const int e = Es - 1023;
   const int p2 = 11 - e + bits * (nslice - 1);
-  const double2* yrow = reinterpret_cast<const double2*>(Yin + row * ldy);
-  __half2* orow = reinterpret_cast<__half2*>(out + row * out_ld);
+  const longlong2* yrow = reinterpret_cast<const longlong2*>(Yin + row * ldy);
+  uint32_t* orow = reinterpret_cast<uint32_t*>(out + row * out_ld);
   const int pbase = blockIdx.y * (kSliceThreads * kSlicePairsPerThread) + threadIdx.x;
-  double2 yv[kSlicePairsPerThread];
+  longlong2 yv[kSlicePairsPerThread];
 #pragma unroll
   for (int u = 0; u < kSlicePairsPerThread; ++u) {
     const int p = pbase + u * kSliceThreads;
-    yv[u] = (ok && p < npairs) ? yrow[p] : make_double2(0.0, 0.0);
+    yv[u] = make_longlong2(0, 0);
+    if (ok && p < npairs) yv[u] = yrow[p];
   }
 #pragma unroll
   for (int u = 0; u < kSlicePairsPerThread; ++u) {
     const int p = pbase + u * kSliceThreads;
     if (p >= npairs) break;
-    long long n0 = ok ? fixed_point(yv[u].x, p2) : 0;
-    long long n1 = ok ? fixed_point(yv[u].y, p2) : 0;
-    for (int s = nslice - 1; s >= 1; --s) {
-      const long long d0 = ((n0 + H) & MASK) - H, d1 = ((n1 + H) & MASK) - H;
-      orow[s * plane2 + p] = __halves2half2(__int2half_rn(static_cast<int>(d0)),
-                                            __int2half_rn(static_cast<int>(d1)));
-      n0 = (n0 - d0) >> bits;
-      n1 = (n1 - d1) >> bits;
+    int d0[4] = {0, 0, 0, 0}, d1[4] = {0, 0, 0, 0};
+    if (ok) {
+      slice_digits(yv[u].x, p2, nslice, bits, d0);
+      slice_digits(yv[u].y, p2, nslice, bits, d1);
     }
-    orow[p] = __halves2half2(__int2half_rn(static_cast<int>(n0)),
-                             __int2half_rn(static_cast<int>(n1)));
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      if (s < nslice) orow[s * plane2 + p] = half_pair(d0[s], d1[s]);
   }
 }
 
@@ -633,8 +730,10 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32)
         for (int u = 0; u < 4; ++u) {
           const int j = 2 * (p + 32 * u);
           double x0 = av[u].x, x1 = av[u].y;
-          if (minus_identity && j == row) x0 -= 1.0;
-          if (minus_identity && j + 1 == row) x1 -= 1.0;
+          if (minus_identity && (j == row || j + 1 == row)) {
+            if (j == row) x0 = minus_one(x0);
+            else x1 = minus_one(x1);
+          }
           double y0 = (b2 != nullptr) ? bv[u].x : x0, y1 = (b2 != nullptr) ? bv[u].y : x1;
           float ah, al, bh, bl;
           split_double(x0, ah, al);
@@ -652,7 +751,7 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32)
       for (int j = j0; j < j0 + (vec ? 2 : 1) && j < cols; ++j) {
         float ah, al;
         double av = ar[j];
-        if (minus_identity && j == row) av -= 1.0;
+        if (minus_identity && j == row) av = minus_one(av);
         split_double(av, ah, al);
         if (br != nullptr) {
           float bh, bl;
@@ -728,10 +827,51 @@ __global__ void trs4_control_kernel(const double* partials, int nblocks, Trs4Sta
   // needs no gamma: gamma = (N - Tr F)/Tr G is a ratio of two differences that both vanish at
   // convergence, so its digits go first and a wrong branch would move the trace by Tr(X - X^2).
   const bool endgame = fabs(idem) < 0.1 && fabs(t[0] - N) < 0.25;
-  const bool gamma_ok = !endgame && trG > 1e-12 * Nf;
+  int br;
+  if (st->method == kPurifyTrs2 && !endgame) {
+    // 2nd-order trace resetting: of X^2 and 2X - X^2, the one whose trace is nearer N
+    st->gamma = 0.0;
+    if (fabs(t[1] - N) <= fabs(2.0 * t[0] - t[1] - N)) {
+      br = 1;
+      st->coefX[0] = 0.0;
+      st->coefX[1] = 1.0;
+    } else {
+      br = 0;
+      st->coefX[0] = 2.0;
+      st->coefX[1] = -1.0;
+    }
+    st->coefX[2] = 0.0;
+    st->branch = br;
+    st->skip_gemm = 1;
+    st->skip_form_x = (stop != 0) ? 1 : 0;
+    st->iter += 1;
+    return;
+  }
+  if (st->method == kPurifyCanonical && !endgame && idem > 1e-12 * Nf) {
+    // canonical purification, X <- X W with c = Tr(X^2 - X^3) / Tr(X - X^2) (Tr X is kept):
+    // c >= 1/2: W = ((1 + c) X - X^2) / c;  c < 1/2: W = ((1 - 2c) I + (1 + c) X - X^2) / (1 - c)
+    const double cc = (t[1] - t[2]) / idem;
+    st->gamma = cc;
+    if (cc >= 0.5) {
+      st->coefW[0] = (1.0 + cc) / cc;
+      st->coefW[1] = -1.0 / cc;
+      st->coefW[2] = 0.0;
+    } else {
+      st->coefW[0] = (1.0 + cc) / (1.0 - cc);
+      st->coefW[1] = -1.0 / (1.0 - cc);
+      st->coefW[2] = (1.0 - 2.0 * cc) / (1.0 - cc);
+    }
+    st->gemm_coef[0] = 1.0;
+    st->gemm_coef[1] = 0.0;
+    st->branch = 4;
+    st->skip_gemm = (stop != 0) ? 1 : 0;
+    st->skip_form_x = 1;
+    st->iter += 1;
+    return;
+  }
+  const bool gamma_ok = st->method == kPurifyTrs4 && !endgame && trG > 1e-12 * Nf;
   const double g = gamma_ok ? (N - trF) / trG : 0.0;
   st->gamma = g;
-  int br;
   if (!gamma_ok) {
     br = 3;
     st->coefW[0] = -2.0;
@@ -762,6 +902,25 @@ __global__ void trs4_control_kernel(const double* partials, int nblocks, Trs4Sta
   st->skip_gemm = (stop != 0 || !with_product) ? 1 : 0;
   st->skip_form_x = (stop != 0 || with_product) ? 1 : 0;
   st->iter += 1;
+}
+
+// Canonical initial guess X0 = (lam/n)(mu I - H~) + (N/n) I: coef = {-lam/n, 0, lam mu/n + N/n}
+// with mu = Tr H~ / n (diagonal summed in a fixed order) and
+// lam = min(N / (eps_max - mu), (n - N) / (mu - eps_min)).
+__global__ void canonical_x0_coef_kernel(const double* bounds, const double* Ht, int64_t ld, int n,
+                                         double n_occ, double* coef) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += Ht[static_cast<int64_t>(i) * (ld + 1)];
+  acc = block_sum(acc, red);
+  if (threadIdx.x != 0) return;
+  const double lo = bounds[0], hi = bounds[1];
+  const double nn = static_cast<double>(n);
+  const double mu = acc / nn;
+  const double lam = fmin(n_occ / (hi - mu), (nn - n_occ) / (mu - lo));
+  coef[0] = -lam / nn;
+  coef[1] = 0.0;
+  coef[2] = lam * mu / nn + n_occ / nn;
 }
 
 __global__ void x0_coef_kernel(const double* bounds, double* coef) {
@@ -942,7 +1101,8 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
         X, ldx, X2, ldx2, rows, cols, coef_dev, ha, hb, hc, Y, ldy,
         od != nullptr ? osc : nullptr, skip, with_dot ? dot : kDotNone,
         with_dot ? out->row_dot : nullptr);
-    if (with_dot) out->dot_partner = (dot == kDotX2) ? X2 : (Y != nullptr ? Y : X);
+    if (with_dot)
+      out->dot_partner = (dot == kDotX2) ? X2 : (dot == kDotX ? X : (Y != nullptr ? Y : X));
     if (od != nullptr) {
       const double* src = (Y != nullptr) ? Y : X;
       const int64_t lds = (Y != nullptr) ? ldy : ldx;
@@ -1014,6 +1174,13 @@ cudaError_t trs4_control(const double* partials, int nblocks, Trs4State* st, dou
 cudaError_t x0_coefficients(const double* bounds_dev, double* coef_dev, cudaStream_t stream) {
   count_launch();
   x0_coef_kernel<<<1, 1, 0, stream>>>(bounds_dev, coef_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t canonical_x0_coefficients(const double* bounds_dev, const double* Ht, int64_t ld, int n,
+                                      double n_occ, double* coef_dev, cudaStream_t stream) {
+  count_launch();
+  canonical_x0_coef_kernel<<<1, 256, 0, stream>>>(bounds_dev, Ht, ld, n, n_occ, coef_dev);
   return cudaGetLastError();
 }
 

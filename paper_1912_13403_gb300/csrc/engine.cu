@@ -393,7 +393,11 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
 
   // bounds and X_0
   CK(gershgorin(Ht, ld, n, h->partials, h->small + SM_BOUNDS_H, s));
-  CK(x0_coefficients(h->small + SM_BOUNDS_H, h->small + SM_COEF_X0, s));
+  if (h->purify == kPurifyCanonical)
+    CK(canonical_x0_coefficients(h->small + SM_BOUNDS_H, Ht, ld, n,
+                                 static_cast<double>(h->n_occ), h->small + SM_COEF_X0, s));
+  else
+    CK(x0_coefficients(h->small + SM_BOUNDS_H, h->small + SM_COEF_X0, s));
   double bh[2];
   st = read_small(h, SM_BOUNDS_H, 2, bh);
   if (st != GDM_OK) return st;
@@ -415,6 +419,7 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   Trs4State init;
   memset(&init, 0, sizeof(init));
   init.n_occ = static_cast<double>(h->n_occ);
+  init.method = h->purify;
   init.idem = INFINITY;
   CK(cudaMemcpyAsync(h->st_dev, &init, sizeof(init), cudaMemcpyHostToDevice, s));
   const double tol_abs = h->idem_tol * static_cast<double>(h->n_occ);
@@ -447,7 +452,14 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
       break;
     }
     last_idem = t.idem;
-    if (t.branch == 2 || t.branch == 3) {  // a product: F + gamma G, or McWeeny
+    if (t.branch == 4) {  // canonical: X <- X W, W = a X + b X^2 + c I (X's slices are current)
+      CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefW)), 0, 0, 0,
+                        W, ld, pu_sl > 0 ? &h->sl[SL_W] : nullptr, pu_sl, nullptr, s,
+                        bits_for(h, GDM_PHASE_PURIFY), kDotX));
+      CK(product(h, {X, &h->sl[SL_X]}, {W, &h->sl[SL_W]}, Xn, nullptr, nullptr, 1.0, 0.0, 0.0,
+                 true, GDM_PHASE_PURIFY, nullptr, true));
+      CK(slice(h, Xn, &h->sl[SL_X], GDM_PHASE_PURIFY, kDotSelf));
+    } else if (t.branch == 2 || t.branch == 3) {  // a product: F + gamma G, or McWeeny
       CK(slice(h, X2, &h->sl[SL_X2], GDM_PHASE_PURIFY));
       CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefW)), 0, 0, 0,
                         W, ld, pu_sl > 0 ? &h->sl[SL_W] : nullptr, pu_sl, nullptr, s,
@@ -701,6 +713,18 @@ gdm_status gdm_init(gdm_handle** out, int64_t n_basis, int64_t n_occ, int device
     return GDM_ERR_CUDA;
   }
   *out = h;
+  return GDM_OK;
+}
+
+static_assert(GDM_PURIFY_TRS4 == kPurifyTrs4 && GDM_PURIFY_TRS2 == kPurifyTrs2 &&
+                  GDM_PURIFY_CANONICAL == kPurifyCanonical,
+              "purification codes");
+
+gdm_status gdm_set_purification(gdm_handle* h, gdm_purification method) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  if (method != GDM_PURIFY_TRS4 && method != GDM_PURIFY_TRS2 && method != GDM_PURIFY_CANONICAL)
+    return set_err(h, GDM_ERR_ARG, "unknown purification method %d", static_cast<int>(method));
+  h->purify = static_cast<int>(method);
   return GDM_OK;
 }
 

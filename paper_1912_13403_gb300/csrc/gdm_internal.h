@@ -99,9 +99,12 @@ cudaError_t f64_gemm(const F64GemmArgs& a, cudaStream_t stream);
 // Y = a*X + b*X2 + c*I with (a, b, c) from `coef_dev` (3 doubles) when non-null, else
 // (ha, hb, hc).  X2 may be null (then b is ignored).  Writes Y (FP64) when Y != null, and the
 // row slices of Y into `out` when out != null and nslice > 0.  dot: 0 none, 1 the row dot
-// products sum_k y_ik^2, 2 sum_k y_ik X2_ik, written to out->row_dot when the buffer has one
+// products sum_k y_ik^2, 2 sum_k y_ik X2_ik, 3 sum_k y_ik X_ik, written to out->row_dot when the buffer has one
 // (out->dot_partner then names the partner matrix; otherwise it is reset to null).
-enum { kDotNone = 0, kDotSelf = 1, kDotX2 = 2 };
+enum { kDotNone = 0, kDotSelf = 1, kDotX2 = 2, kDotX = 3 };
+
+// purification maps (the values of gdm_purification)
+enum { kPurifyTrs4 = 0, kPurifyTrs2 = 1, kPurifyCanonical = 2 };
 cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64_t ldx2,
                            int rows, int cols, const double* coef_dev, double ha, double hb,
                            double hc, double* Y, int64_t ldy, SliceBuf* out, int nslice,
@@ -138,7 +141,9 @@ struct Trs4State {
   double coefW[3];        // W = a X + b X2 + c I; X_next = X2 W
   double coefX[3];        // X_next = a X + b X2 for the branches without a product
   double gemm_coef[2];    // (1, 0): alpha and beta of the X2 W product (no addend)
-  int branch;             // 0: 2X - X2, 1: X2, 2: F + gamma G, 3: McWeeny X2 (3I - 2X)
+  int method;             // kPurify*
+  int branch;             // 0: 2X - X2, 1: X2, 2: X2 W (TRS4 F + gamma G), 3: McWeeny X2 (3I - 2X),
+                          // 4: X W (canonical)
   int skip_gemm;          // 1 unless branch 2 or 3
   int skip_form_x;        // 1 when branch 2 or 3
   int stop;               // 1: converged (X is final), 2: stalled, 3: non-finite
@@ -147,6 +152,11 @@ struct Trs4State {
 };
 cudaError_t trs4_control(const double* partials, int nblocks, Trs4State* st, double tol_idem,
                          cudaStream_t stream);
+
+// Coefficients {a, 0, c} of the canonical initial guess X0 = a H~ + c I from the bounds and
+// the trace of H~ (read from its diagonal).
+cudaError_t canonical_x0_coefficients(const double* bounds_dev, const double* Ht, int64_t ld, int n,
+                                      double n_occ, double* coef_dev, cudaStream_t stream);
 
 // Set the bounds-dependent coefficients of the initial guess
 // X0 = (eps_max I - H~)/(eps_max - eps_min): coef = {-1/(hi-lo), 0, hi/(hi-lo)}.

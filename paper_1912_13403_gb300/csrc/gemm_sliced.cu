@@ -143,6 +143,18 @@ __device__ __forceinline__ double scaled_int_to_double(long long T, int ex) {
       sign | (static_cast<unsigned long long>(e + 1023) << 52) | (mant & ((1ULL << 52) - 1))));
 }
 
+// Out-of-line FP64 steps of the epilogue (see the call sites).
+__device__ __noinline__ double fp64_scale(double v, double a) { return v * a; }
+__device__ __noinline__ double fp64_axpy(double a, double x, double y) { return fma(a, x, y); }
+// C_ii from the exact row dot product of the slicing pass when there is one: the FP32
+// accumulation truncates, and on the diagonal of a product of (nearly) parallel rows its
+// residual-slice terms form a positive sum whose truncation biases C_ii; plus the diagonal shift.
+__device__ __noinline__ double diagonal_value(double v, const double* diag_dot, double shift,
+                                              int i, double alpha) {
+  if (diag_dot != nullptr) v = alpha * diag_dot[i];
+  return v + shift;
+}
+
 template <int NSLICE, int BK, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     sliced_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
@@ -299,6 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool ok = mbar_wait_bounded(&acc_full_bar, tcount & 1u, args.err, &abort_flag);
       tc_fence_after();
       if (!ok || abort_flag) break;
+      const bool diag_tile = (ti == tj);
       const int r0 = ti * kBM + q * 32;
       const int grow = r0 + lane;
       const double sa = (grow < args.M) ? args.row_scale_a[grow] : 0.0;
@@ -339,17 +352,18 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (sa_ok && finite_bits(sb)) {
                 const long long tv = (pow2_alpha && alpha_neg) ? -T[j] : T[j];
                 val = scaled_int_to_double(tv, ex_base + pow2_exponent(sb));
-                if (!pow2_alpha) val *= alpha;
+                if (!pow2_alpha) val = fp64_scale(val, alpha);
               } else {
-                val = sa * sb;  // a NaN / Inf row scale marks a non-finite input row
+                // a NaN / Inf row scale marks a non-finite input row; bit-level propagation
+                val = finite_bits(sa) ? sb : sa;
               }
-              // the diagonal from the exact row dot product of the slicing pass: the FP32
-              // accumulation truncates, and on the diagonal of a product of (nearly) parallel
-              // rows its residual-slice terms form a positive sum whose truncation biases C_ii
-              if (args.diag_dot != nullptr && grow == gcol) val = alpha * args.diag_dot[grow];
+              // FP64 arithmetic only where it is needed, in out-of-line calls behind uniform or
+              // per-element tests (GB300 issues FP64 at about 1/64 of the FP32 rate, and an
+              // if-converted FP64 instruction would run for every element)
+              if (diag_tile && grow == gcol)
+                val = diagonal_value(val, args.diag_dot, args.diag, grow, alpha);
               if (args.D != nullptr)
-                val += beta * args.D[static_cast<int64_t>(gcol) * args.ldd + grow];
-              if (grow == gcol) val += args.diag;
+                val = fp64_axpy(beta, args.D[static_cast<int64_t>(gcol) * args.ldd + grow], val);
               if (sym && grow < gcol) args.C[static_cast<int64_t>(gcol) * args.ldc + grow] = val;
               if (args.Ct != nullptr) args.Ct[static_cast<int64_t>(gcol) * args.ldct + grow] = val;
             }

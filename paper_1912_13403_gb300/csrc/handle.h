@@ -32,6 +32,7 @@ struct gdm_handle {
   int rows_alloc = 0;     // rows of slice buffers (multiple of 128)
   cudaStream_t own_stream = nullptr, stream = nullptr;
   gdm_precision prec = GDM_PREC_MIXED;
+  int purify = 0;  // gdm_purification
   gdm::Precision phase[4] = {{2, 1, 12}, {4, 3, 9}, {4, 3, 9}, {3, 3, 12}};
   double idem_tol = 1e-13, trace_tol = 1e-6;
   bool trace_correct = true;

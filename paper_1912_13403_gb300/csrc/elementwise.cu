@@ -119,6 +119,48 @@ __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
   }
 }
 
+// The same split from the two 32-bit words of the double (lo word first in memory), for data
+// that is loaded and kept in integer registers.
+__device__ __forceinline__ void split_words(unsigned whi, unsigned wlo, float& hi, float& lo) {
+  const int E = static_cast<int>((whi >> 20) & 0x7FF);
+  const unsigned sign = whi & 0x80000000u;
+  const int ef = E - 1023 + 127;
+  // hi: the top 24 significant bits, truncated
+  const unsigned hbits = sign | (static_cast<unsigned>(ef) << 23) | ((whi & 0xFFFFFu) << 3) |
+                         (wlo >> 29);
+  // lo: the remaining 29 bits, normalised
+  const unsigned rem = wlo & ((1u << 29) - 1u);
+  const int msb = 31 - __clz(rem | 1u);
+  const int el = E - 1075 + msb + 127;
+  const unsigned mant = (msb >= 23) ? (rem >> (msb - 23)) : (rem << (23 - msb));
+  const unsigned lbits = sign | (static_cast<unsigned>(el) << 23) | (mant & 0x7FFFFFu);
+  const bool normal = (E != 0) && (E != 0x7FF) && (ef > 0) && (ef < 255);
+  const unsigned nan_bit = (E == 0x7FF && ((whi & 0xFFFFFu) | wlo) != 0u) ? 1u : 0u;
+  hi = __uint_as_float(normal ? hbits
+                              : (E == 0x7FF || ef >= 255 ? (sign | 0x7F800000u | nan_bit) : 0u));
+  lo = __uint_as_float((normal && rem != 0u && el > 0) ? lbits : 0u);
+}
+
+// +-2^k x on the two words of x: only the high word changes (exponent and sign); zero and
+// subnormal x give 0, results below the normal range 0 (signed), above it Inf, Inf/NaN stay.
+__device__ __forceinline__ void pow2_words(unsigned& whi, unsigned& wlo, int k, bool neg) {
+  const int E = static_cast<int>((whi >> 20) & 0x7FF);
+  const unsigned flip = neg ? 0x80000000u : 0u;
+  const unsigned sgn = (whi & 0x80000000u) ^ flip;
+  const int En = E + k;
+  unsigned h = sgn | (static_cast<unsigned>(En & 0x7FF) << 20) | (whi & 0xFFFFFu);
+  unsigned l = wlo;
+  const bool under = (E == 0) || (En <= 0);
+  h = (En >= 0x7FF) ? (sgn | 0x7FF00000u) : h;
+  l = (En >= 0x7FF) ? 0u : l;
+  h = under ? ((E == 0) ? 0u : sgn) : h;
+  l = under ? 0u : l;
+  h = (E == 0x7FF) ? (whi ^ flip) : h;
+  l = (E == 0x7FF) ? wlo : l;
+  whi = h;
+  wlo = l;
+}
+
 // Balanced base-2^bits digits of N = round(|y| 2^p) (nearest, ties to even), top digit first,
 // with the sign of y applied: |y| 2^p = sum_s d[s] 2^(bits (nslice - 1 - s)), |d[s]| <= 2^(bits-1)
 // for s >= 1 and |d[0]| <= 2^11 when |y| < 2^(11 + bits (nslice - 1) - p).  From the bit
@@ -353,21 +395,6 @@ __global__ void __launch_bounds__(kRowThreads)
   }
 }
 
-// x * (+-2^k) from the bit pattern (integer operations only): zero and subnormal x give 0,
-// Inf / NaN stay non-finite, results beyond the exponent range saturate to Inf.
-__device__ __forceinline__ double pow2_mul(double x, int k, bool neg) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-  const int E = static_cast<int>((b >> 52) & 0x7FF);
-  const unsigned long long sign = (b & (1ULL << 63)) ^ (neg ? (1ULL << 63) : 0ULL);
-  if (E == 0) return 0.0;
-  if (E == 0x7FF) return __longlong_as_double(static_cast<long long>(b ^ (neg ? (1ULL << 63) : 0ULL)));
-  const int En = E + k;
-  if (En <= 0) return __longlong_as_double(static_cast<long long>(sign));
-  if (En >= 0x7FF) return __longlong_as_double(static_cast<long long>(sign | 0x7FF0000000000000ULL));
-  return __longlong_as_double(static_cast<long long>(
-      sign | (static_cast<unsigned long long>(En) << 52) | (b & ((1ULL << 52) - 1))));
-}
-
 // a = +-2^k exactly?
 __device__ __forceinline__ bool pow2_coef(double a, int& k, bool& neg) {
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(a));
@@ -383,77 +410,123 @@ __device__ __forceinline__ bool pow2_coef(double a, int& k, bool& neg) {
 // truncated values enlarged by 0.2% (NaN marks a row with NaN / Inf).  With dot != kDotNone it
 // also writes row_dot[row] = sum_j y_j^2 (kDotSelf), sum_j y_j X2_j (kDotX2) or sum_j y_j X_j
 // (kDotX) in double-float.
-// y_ii + c for the pair p that holds the diagonal element of `row`.  Kept out of line so that the
-// FP64 add is a real branch taken once per row, not an if-converted instruction on every element
+// Diagonal additions are kept out of line (add_on_diagonal_words, minus_one) so that the FP64
+// add is a real branch taken once per row, not an if-converted instruction on every element
 // (GB300 issues FP64 at about 1/64 of the FP32 rate).
-__device__ __noinline__ double2 add_on_diagonal(double2 y, int p, int row, double c) {
-  if (2 * p == row) y.x += c;
-  else y.y += c;
-  return y;
-}
 
 // v - 1, out of line for the same reason (the identity's diagonal in a residual)
 __device__ __noinline__ double minus_one(double v) { return v - 1.0; }
 
 enum { kFormPlain = 0, kFormPow2 = 1, kFormGeneral = 2 };
 
-// One warp's pass over a row: form y, write it, accumulate the FP32 norm and the optional
-// double-float row dot product.  MODE picks the forming arithmetic: kFormPlain y = x, kFormPow2
-// y = +-2^k x (exponent shift), kFormGeneral y = a x + b x2 (FP64); c I is added in a branch.
-template <int MODE>
-__device__ __forceinline__ void form_norm_row(const double2* __restrict__ xr,
-                                              const double2* __restrict__ x2r, double2* yr,
+// y_jj + c on the word pair of a diagonal element, out of line (once per row).
+__device__ __noinline__ uint2 add_on_diagonal_words(uint2 w, double c) {
+  const double v = __hiloint2double(static_cast<int>(w.y), static_cast<int>(w.x)) + c;
+  return make_uint2(static_cast<unsigned>(__double2loint(v)), static_cast<unsigned>(__double2hiint(v)));
+}
+
+// a x + b x2 on word pairs (FP64: the general forming step).
+__device__ __forceinline__ uint2 axpby_words(double a, uint2 x, double b, uint2 x2, bool with_x2) {
+  double v = a * __hiloint2double(static_cast<int>(x.y), static_cast<int>(x.x));
+  if (with_x2) v = fma(b, __hiloint2double(static_cast<int>(x2.y), static_cast<int>(x2.x)), v);
+  return make_uint2(static_cast<unsigned>(__double2loint(v)), static_cast<unsigned>(__double2hiint(v)));
+}
+
+// One warp's pass over a row, on integer registers throughout (16-byte loads of two doubles as
+// uint4 = {lo0, hi0, lo1, hi1}): form y, write it, accumulate the FP32 norm from the truncated
+// values and, for DOT != kDotNone, the double-float row dot product.  MODE picks the forming
+// arithmetic: kFormPlain y = x, kFormPow2 y = +-2^k x (exponent shift), kFormGeneral
+// y = a x + b x2 (FP64); c I is added out of line on the diagonal element.  Everything that
+// is not FP64 arithmetic stays in integer types: on GB300 a double that takes part in integer
+// selects can cost FP64-pipe instructions.
+template <int MODE, int DOT>
+__device__ __forceinline__ void form_norm_row(const uint4* __restrict__ xr,
+                                              const uint4* __restrict__ x2r, uint4* yr,
                                               int npairs, int row, int lane, double a, double b,
-                                              int ak, bool aneg, bool has_c, double c, int dot,
+                                              int ak, bool aneg, bool has_c, double c,
                                               float& ss, DF& acc) {
-  const bool need_x2 = x2r != nullptr && (MODE == kFormGeneral || dot == kDotX2);
+  constexpr bool kNeedX2 = (MODE == kFormGeneral) || (DOT == kDotX2);
+  const bool with_x2 = x2r != nullptr;
+  auto one = [&](int p, uint4 x, uint4 x2) {
+    uint4 y = x;
+    if (MODE == kFormPow2) {
+      pow2_words(y.y, y.x, ak, aneg);
+      pow2_words(y.w, y.z, ak, aneg);
+    } else if (MODE == kFormGeneral) {
+      const uint2 y0 = axpby_words(a, make_uint2(x.x, x.y), b, make_uint2(x2.x, x2.y), with_x2);
+      const uint2 y1 = axpby_words(a, make_uint2(x.z, x.w), b, make_uint2(x2.z, x2.w), with_x2);
+      y = make_uint4(y0.x, y0.y, y1.x, y1.y);
+    }
+    if (has_c && (2 * p == row || 2 * p + 1 == row)) {
+      if (2 * p == row) {
+        const uint2 d = add_on_diagonal_words(make_uint2(y.x, y.y), c);
+        y.x = d.x;
+        y.y = d.y;
+      } else {
+        const uint2 d = add_on_diagonal_words(make_uint2(y.z, y.w), c);
+        y.z = d.x;
+        y.w = d.y;
+      }
+    }
+    if (yr != nullptr) yr[p] = y;
+    float h0, l0, h1, l1;
+    split_words(y.y, y.x, h0, l0);
+    split_words(y.w, y.z, h1, l1);
+    ss = fmaf(h0, h0, fmaf(h1, h1, ss));  // the truncated value bounds |y| from below by 2^-23
+    if (DOT != kDotNone) {
+      float ph0 = h0, pl0 = l0, ph1 = h1, pl1 = l1;
+      if (DOT == kDotX2) {
+        split_words(x2.y, x2.x, ph0, pl0);
+        split_words(x2.w, x2.z, ph1, pl1);
+      } else if (DOT == kDotX) {
+        split_words(x.y, x.x, ph0, pl0);
+        split_words(x.w, x.z, ph1, pl1);
+      }
+      acc = df_fma(acc, h0, l0, ph0, pl0);
+      acc = df_fma(acc, h1, l1, ph1, pl1);
+    }
+  };
   constexpr int U = 4;  // loads of U column pairs in flight per lane
-  for (int p0 = lane; p0 < npairs; p0 += 32 * U) {
-    double2 xv[U], x2v[U];
+  int p0 = lane;
+  for (; p0 + 32 * (U - 1) < npairs; p0 += 32 * U) {
+    uint4 xv[U], x2v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int p = p0 + 32 * u;
-      xv[u] = make_double2(0.0, 0.0);
-      x2v[u] = make_double2(0.0, 0.0);
-      if (p < npairs) {
-        xv[u] = xr[p];
-        if (need_x2) x2v[u] = x2r[p];
-      }
+      xv[u] = xr[p0 + 32 * u];
+      if (kNeedX2 && with_x2) x2v[u] = x2r[p0 + 32 * u];
+      else x2v[u] = make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int p = p0 + 32 * u;
-      if (p >= npairs) break;
-      double2 y = xv[u];
-      if (MODE == kFormPow2) {
-        y.x = pow2_mul(y.x, ak, aneg);
-        y.y = pow2_mul(y.y, ak, aneg);
-      } else if (MODE == kFormGeneral) {
-        y.x *= a;
-        y.y *= a;
-        if (x2r != nullptr) {
-          y.x = fma(b, x2v[u].x, y.x);
-          y.y = fma(b, x2v[u].y, y.y);
-        }
-      }
-      if (has_c && (2 * p == row || 2 * p + 1 == row)) y = add_on_diagonal(y, p, row, c);
-      if (yr != nullptr) yr[p] = y;
-      const float f0 = trunc_to_float(y.x), f1 = trunc_to_float(y.y);
-      ss = fmaf(f0, f0, fmaf(f1, f1, ss));
-      if (dot != kDotNone) {
-        float yh, yl, ph, pl;
-        split_double(y.x, yh, yl);
-        if (dot == kDotX2) split_double(x2v[u].x, ph, pl);
-        else if (dot == kDotX) split_double(xv[u].x, ph, pl);
-        else { ph = yh; pl = yl; }
-        acc = df_fma(acc, yh, yl, ph, pl);
-        split_double(y.y, yh, yl);
-        if (dot == kDotX2) split_double(x2v[u].y, ph, pl);
-        else if (dot == kDotX) split_double(xv[u].y, ph, pl);
-        else { ph = yh; pl = yl; }
-        acc = df_fma(acc, yh, yl, ph, pl);
-      }
-    }
+    for (int u = 0; u < U; ++u) one(p0 + 32 * u, xv[u], x2v[u]);
+  }
+  for (; p0 < npairs; p0 += 32) {
+    const uint4 x = xr[p0];
+    const uint4 x2 = (kNeedX2 && with_x2) ? x2r[p0] : make_uint4(0u, 0u, 0u, 0u);
+    one(p0, x, x2);
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void form_norm_dispatch(int dot, const uint4* xr, const uint4* x2r,
+                                                   uint4* yr, int npairs, int row, int lane,
+                                                   double a, double b, int ak, bool aneg,
+                                                   bool has_c, double c, float& ss, DF& acc) {
+  switch (dot) {
+    case kDotSelf:
+      form_norm_row<MODE, kDotSelf>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, ss,
+                                    acc);
+      break;
+    case kDotX2:
+      form_norm_row<MODE, kDotX2>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, ss,
+                                  acc);
+      break;
+    case kDotX:
+      form_norm_row<MODE, kDotX>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, ss,
+                                 acc);
+      break;
+    default:
+      form_norm_row<MODE, kDotNone>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, ss,
+                                    acc);
   }
 }
 
@@ -480,22 +553,21 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32, 4)
   int mode = kFormGeneral;
   if (no_x2 && a == 1.0) mode = kFormPlain;
   else if (no_x2 && pow2_coef(a, ak, aneg)) mode = kFormPow2;
-  const double2* xr = reinterpret_cast<const double2*>(X + row * ldx);
-  const double2* x2r = (X2 != nullptr) ? reinterpret_cast<const double2*>(X2 + row * ldx2)
-                                        : nullptr;
-  double2* yr = (Y != nullptr) ? reinterpret_cast<double2*>(Y + row * ldy) : nullptr;
+  const uint4* xr = reinterpret_cast<const uint4*>(X + row * ldx);
+  const uint4* x2r = (X2 != nullptr) ? reinterpret_cast<const uint4*>(X2 + row * ldx2) : nullptr;
+  uint4* yr = (Y != nullptr) ? reinterpret_cast<uint4*>(Y + row * ldy) : nullptr;
   const int npairs = cols >> 1;
   float ss = 0.0f;
   DF acc{0.0f, 0.0f};
   if (mode == kFormPlain)
-    form_norm_row<kFormPlain>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, dot, ss,
-                              acc);
+    form_norm_dispatch<kFormPlain>(dot, xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c,
+                                   ss, acc);
   else if (mode == kFormPow2)
-    form_norm_row<kFormPow2>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, dot, ss,
-                             acc);
+    form_norm_dispatch<kFormPow2>(dot, xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c,
+                                  ss, acc);
   else
-    form_norm_row<kFormGeneral>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, dot,
-                                ss, acc);
+    form_norm_dispatch<kFormGeneral>(dot, xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c,
+                                     c, ss, acc);
   if (dot != kDotNone) {
     acc = df_warp_sum(acc);
     if (lane == 0) row_dot[row] = df_to_double(acc);
@@ -505,7 +577,9 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32, 4)
   if (lane == 0 && out_scale != nullptr) {
     if (ss > 0.0f && isfinite(ss)) {
       int e = 0;
-      frexpf(sqrtf(ss * 1.002f) * 1.0001f, &e);  // 2^e > ||y|| with margin
+      // the norm from truncated values is low by at most 2^-23 relative: the 0.2% margin covers
+      // it and the FP32 accumulation, so 2^e > ||y||
+      frexpf(sqrtf(ss * 1.002f) * 1.0001f, &e);
       out_scale[row] = __longlong_as_double(static_cast<long long>(e + 1023) << 52);  // 2^e
     } else {
       out_scale[row] = isfinite(ss) ? 1.0 : __longlong_as_double(0x7FF8000000000000LL);

@@ -131,9 +131,9 @@ def job_throughput(units_per_rank, total_ms_this_rank, device="cpu"):
 
 PHASES = ("newton_schulz", "refine", "transform", "purify")
 
-# DRAM bytes (read + write) per purification product launch at n=4096 from one ncu capture of
-# the current sliced_gemm_kernel<3,32,4>; None until the kernel has been captured.
-PURIFY_TRAFFIC_N4096 = None
+# DRAM bytes (read + write) per purification product launch at n=4096: the mean of the X X and
+# X^2 W launches of one ncu capture of sliced_gemm_kernel<3,32,4> (379 MB and 503 MB).
+PURIFY_TRAFFIC_N4096 = 0.5 * ((280.993024 + 97.957632) + (388.463872 + 114.712064)) * 1e6
 
 
 def traffic_bytes(n):

@@ -131,9 +131,9 @@ def job_throughput(units_per_rank, total_ms_this_rank, device="cpu"):
 
 PHASES = ("newton_schulz", "refine", "transform", "purify")
 
-# DRAM bytes (read + write) per purification product launch at n=4096: the mean of the X X and
-# X^2 W launches of one ncu capture of sliced_gemm_kernel<3,32,4> (379 MB and 503 MB).
-PURIFY_TRAFFIC_N4096 = 0.5 * ((280.993024 + 97.957632) + (388.463872 + 114.712064)) * 1e6
+# DRAM bytes (read + write) per purification product launch at n=4096 from one ncu capture of
+# the current sliced_gemm_kernel<3,64,2>; None until that kernel has been captured.
+PURIFY_TRAFFIC_N4096 = None
 
 
 def traffic_bytes(n):
@@ -468,7 +468,7 @@ def run_ours(args):
         "roofline": {"bound": "tensor", "achieved": achieved_pu, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved_pu / peak if peak else None,
                      "traffic": traffic_bytes(n),
-                     "kernel": "sliced_gemm_kernel<3,32,4>: TRS4 products X X and X^2 W "
+                     "kernel": "sliced_gemm_kernel<3,64,2>: TRS4 products X X and X^2 W "
                                "(tcgen05 kind::f16, 8 slice pairs, upper-triangle tiles)",
                      "flops_per_launch": pfl / pl if pl else None,
                      "ms_per_launch": pms / pl if pl else None,

@@ -20,8 +20,8 @@
 //
 // Kernel shape: persistent, one CTA per SM, each CTA walks the 128x128 output tiles
 // blockIdx.x, blockIdx.x + gridDim.x, ...  10 warps.  Warp 0: TMA producer (a 3-D box loads all
-// slices of a 128 x BK panel at once); its stage ring runs on across tiles, so the next tile's
-// operands stream in while the current tile's epilogue runs.  Warp 1: TMEM allocator and the
+// slices of a 128 x BK panel at once, BK = 64 for up to 3 slices); its stage ring runs on
+// across tiles, so the next tile's operands stream in while the current tile's epilogue runs.  Warp 1: TMEM allocator and the
 // single MMA-issuing thread; it waits for the epilogue to release the accumulators before the
 // next tile.  Warps 2-9: epilogue, two warps per TMEM lane quarter (32*(warp%4) ...), each
 // covering 64 of the 128 columns.  Symmetric mode computes only tiles on or above the diagonal
@@ -506,14 +506,18 @@ cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& B, const Precision& p
   const int grid = (args.mode & kGemmSym) ? tn * (tn + 1) / 2 : tm * tn;
   if (grid == 0) return cudaSuccess;
 
-  const int bk = (nslice >= 3) ? 32 : 64;
+  // 128-byte TMA lines (BK = 64) wherever two stages fit: the TMA's cost per stage grows with
+  // its line count (~1.5 cycles per line) as much as with its bytes, so longer lines beat a
+  // deeper ring (measured: 3 slices with BK = 64 and 2 stages run 13-17% faster than with
+  // BK = 32 and 4 stages).  Four slices need BK = 32 to fit two or more stages.
+  const int bk = (nslice >= 4) ? 32 : 64;
   CUtensorMap ta, tb;
   if (!make_slice_map(&ta, A, bk, nslice) || !make_slice_map(&tb, B, bk, nslice))
     return cudaErrorInvalidValue;
   switch (nslice) {
     case 1: return launch_cfg<1, 64, 6>(ta, tb, args, grid, stream);
     case 2: return launch_cfg<2, 64, 3>(ta, tb, args, grid, stream);
-    case 3: return launch_cfg<3, 32, 4>(ta, tb, args, grid, stream);
+    case 3: return launch_cfg<3, 64, 2>(ta, tb, args, grid, stream);
     default: return launch_cfg<4, 32, 3>(ta, tb, args, grid, stream);
   }
 }

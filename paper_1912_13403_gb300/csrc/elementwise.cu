@@ -1005,6 +1005,84 @@ __global__ void x0_coef_kernel(const double* bounds, double* coef) {
   coef[2] = hi / w;
 }
 
+// ---- power iteration for lambda_max of a symmetric positive matrix --------------------------
+// x is kept as a double-float pair (xh, xl) so that y = A x needs no FP64 instruction.
+
+// Start vector: a fixed pseudo-random positive vector (integer hash), as a double-float pair.
+__global__ void power_init_kernel(int n, float* xh, float* xl) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    unsigned h = static_cast<unsigned>(i) * 2654435761u + 0x9E3779B9u;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    xh[i] = 0.5f + __uint_as_float(0x3F800000u | (h >> 9)) - 1.0f;  // in [0.5, 1.5)
+    xl[i] = 0.0f;
+  }
+}
+
+// y_i = sum_j A_ij x_j (double-float), one warp per row; per-block partial sums of y_i^2.
+__global__ void __launch_bounds__(kRowsPerBlock * 32)
+    matvec_kernel(const double* __restrict__ A, int64_t lda, int n, const float* __restrict__ xh,
+                  const float* __restrict__ xl, double* y, double* partials) {
+  __shared__ double sq[kRowsPerBlock];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * kRowsPerBlock + w;
+  double yi = 0.0;
+  if (row < n) {
+    const uint2* ar = reinterpret_cast<const uint2*>(A + row * lda);
+    DF acc{0.0f, 0.0f};
+    for (int j = lane; j < n; j += 32) {
+      const uint2 a = ar[j];
+      float ah, al;
+      split_words(a.y, a.x, ah, al);
+      acc = df_fma(acc, ah, al, xh[j], xl[j]);
+    }
+    acc = df_warp_sum(acc);
+    yi = df_to_double(acc);
+    if (lane == 0) y[row] = yi;
+  }
+  if (lane == 0) sq[w] = yi * yi;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kRowsPerBlock; ++i) t += sq[i];
+    partials[blockIdx.x] = t;
+  }
+}
+
+// ||y|| from the partials (fixed order), x = y / ||y|| as a double-float pair; *est = ||y||.
+// With `init`, y is the start vector (xh, xl) itself.
+__global__ void power_scale_kernel(const double* y, int n, const double* partials, int nb,
+                                   float* xh, float* xl, double* est, int init) {
+  __shared__ double red[32];
+  __shared__ double norm_sh;
+  double acc = 0.0;
+  if (init) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += static_cast<double>(xh[i]) * xh[i];
+  } else {
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partials[i];
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    norm_sh = sqrt(acc);
+    if (!init) *est = norm_sh;
+  }
+  __syncthreads();
+  const double inv = (norm_sh > 0.0) ? 1.0 / norm_sh : 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = (init ? static_cast<double>(xh[i]) : y[i]) * inv;
+    const float hi = static_cast<float>(v);
+    xh[i] = hi;
+    xl[i] = static_cast<float>(v - static_cast<double>(hi));
+  }
+}
+
+// bounds[1] <- min(bounds[1], factor * est): a tighter scale for the Newton-Schulz start.
+__global__ void tighten_bound_kernel(double* bounds, const double* est, double factor) {
+  const double c = factor * (*est);
+  if (isfinite(c) && c > 0.0 && c < bounds[1]) bounds[1] = c;
+}
+
 __global__ void scale_coef_kernel(const double* bounds, int inv_sqrt, double* coef) {
   const double c = bounds[1];
   coef[0] = inv_sqrt ? 1.0 / sqrt(c) : 1.0 / c;
@@ -1198,6 +1276,29 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
                                                         ha, hb, hc, Y, ldy, od, osc, old, plane,
                                                         nslice, skip, step);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t power_bound(const double* A, int64_t lda, int n, int iters, double factor,
+                        double* work, double* partials, double* bounds_dev, double* est_dev,
+                        cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  float* xh = reinterpret_cast<float*>(work);
+  float* xl = xh + n;
+  double* y = work + n;  // n doubles after the two float vectors (n doubles of room)
+  const int nb = (n + kRowsPerBlock - 1) / kRowsPerBlock;
+  count_launch();
+  power_init_kernel<<<(n + 255) / 256, 256, 0, stream>>>(n, xh, xl);
+  count_launch();
+  power_scale_kernel<<<1, 1024, 0, stream>>>(y, n, partials, 0, xh, xl, est_dev, 1);
+  for (int k = 0; k < iters; ++k) {
+    count_launch();
+    matvec_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, n, xh, xl, y, partials);
+    count_launch();
+    power_scale_kernel<<<1, 1024, 0, stream>>>(y, n, partials, nb, xh, xl, est_dev, 0);
+  }
+  count_launch();
+  tighten_bound_kernel<<<1, 1, 0, stream>>>(bounds_dev, est_dev, factor);
   return cudaGetLastError();
 }
 

@@ -252,8 +252,6 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
   double* coef_isqrt = h->small + SM_COEF_B;
 
   CK(gershgorin(S, ld, n, h->partials, bounds, s));
-  CK(scale_coefficients(bounds, 0, coef_inv, s));
-  CK(scale_coefficients(bounds, 1, coef_isqrt, s));
   double bnd[2];
   gdm_status st = read_small(h, SM_BOUNDS_S, 2, bnd);
   if (st != GDM_OK) return st;
@@ -264,47 +262,73 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
   double *Y = h->f[F_X], *Z = h->f[F_XN], *M = h->f[F_T], *Mt = h->f[F_U];
   double *Yn = h->f[F_X2], *Zn = h->f[F_V];
   SliceBuf *sY = &h->sl[SL_X], *sZ = &h->sl[SL_Z], *sM = &h->sl[SL_A], *sMt = &h->sl[SL_B];
-  CK(form_and_slice(S, ld, nullptr, 0, n, n, coef_inv, 0, 0, 0, Y, ld, ns_sl > 0 ? sY : nullptr,
-                    ns_sl, nullptr, s, bits_for(h, GDM_PHASE_NEWTON_SCHULZ)));
-  CK(set_identity(Z, ld, n, s));
-  CK(slice(h, Z, sZ, GDM_PHASE_NEWTON_SCHULZ));
-
   const double rn = std::sqrt(static_cast<double>(n));
   double prev = INFINITY, res = INFINITY;
   int it = 0;
   bool converged = false;
-  for (it = 0; it < h->max_ns; ++it) {
-    CK(product(h, {Y, sY}, {Z, sZ}, M, Mt, nullptr, 1.0, 0.0, 0.0, false,
-               GDM_PHASE_NEWTON_SCHULZ));
-    double r2 = 0.0;
-    st = dot(h, M, nullptr, 1, &r2);
-    if (st != GDM_OK) return st;
-    res = std::sqrt(r2);
-    if (!std::isfinite(res) || res > 1e6 * rn)
-      return set_err(h, GDM_ERR_NOT_SPD,
-                     "Newton-Schulz for S^-1/2 diverged (residual %g): S not positive definite",
-                     res);
-    if (res <= 1e-13 * rn || (res < 1e-2 * rn && res > 0.5 * prev)) {
-      converged = true;
-      break;
+  // The iteration converges for every scale c with lambda_max(S)/c < 3, and the number of
+  // steps grows with c/lambda_min(S).  Gershgorin's bound can exceed lambda_max many times over
+  // for a dense S, so the first attempt uses 1.25 x a power-iteration estimate of lambda_max
+  // (never above Gershgorin); if that attempt diverges, the second uses Gershgorin's guaranteed
+  // bound.
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (attempt == 0) {
+      CK(power_bound(S, ld, n, 12, 1.25, h->f[F_T], h->partials, bounds, h->small + SM_RED + 7,
+                     s));
+    } else {
+      h->host_buf[0] = bnd[0];
+      h->host_buf[1] = bnd[1];
+      CK(cudaMemcpyAsync(bounds, h->host_buf, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
     }
-    prev = res;
-    // T = (3I - M)/2 and T^T, formed in place while slicing, so that Y <- T Y and Z <- T^T Z
-    // are plain products (no addend in the epilogue)
-    CK(form_and_slice(M, ld, nullptr, 0, n, n, nullptr, -0.5, 0.0, 1.5, M, ld,
-                      ns_sl > 0 ? sM : nullptr, ns_sl, nullptr, s,
-                      bits_for(h, GDM_PHASE_NEWTON_SCHULZ)));
-    CK(form_and_slice(Mt, ld, nullptr, 0, n, n, nullptr, -0.5, 0.0, 1.5, Mt, ld,
-                      ns_sl > 0 ? sMt : nullptr, ns_sl, nullptr, s,
-                      bits_for(h, GDM_PHASE_NEWTON_SCHULZ)));
-    CK(product(h, {M, sM}, {Y, sY}, Yn, nullptr, nullptr, 1.0, 0.0, 0.0, true,
-               GDM_PHASE_NEWTON_SCHULZ));
-    CK(product(h, {Mt, sMt}, {Z, sZ}, Zn, nullptr, nullptr, 1.0, 0.0, 0.0, true,
-               GDM_PHASE_NEWTON_SCHULZ));
-    std::swap(Y, Yn);
-    std::swap(Z, Zn);
-    CK(slice(h, Y, sY, GDM_PHASE_NEWTON_SCHULZ));
+    CK(scale_coefficients(bounds, 0, coef_inv, s));
+    CK(scale_coefficients(bounds, 1, coef_isqrt, s));
+    CK(form_and_slice(S, ld, nullptr, 0, n, n, coef_inv, 0, 0, 0, Y, ld, ns_sl > 0 ? sY : nullptr,
+                      ns_sl, nullptr, s, bits_for(h, GDM_PHASE_NEWTON_SCHULZ)));
+    CK(set_identity(Z, ld, n, s));
     CK(slice(h, Z, sZ, GDM_PHASE_NEWTON_SCHULZ));
+    prev = INFINITY;
+    res = INFINITY;
+    converged = false;
+    bool diverged = false;
+    for (it = 0; it < h->max_ns; ++it) {
+      CK(product(h, {Y, sY}, {Z, sZ}, M, Mt, nullptr, 1.0, 0.0, 0.0, false,
+                 GDM_PHASE_NEWTON_SCHULZ));
+      double r2 = 0.0;
+      st = dot(h, M, nullptr, 1, &r2);
+      if (st != GDM_OK) return st;
+      res = std::sqrt(r2);
+      if (!std::isfinite(res) || res > 1e6 * rn) {
+        if (attempt == 0) {
+          diverged = true;
+          break;
+        }
+        return set_err(h, GDM_ERR_NOT_SPD,
+                       "Newton-Schulz for S^-1/2 diverged (residual %g): S not positive definite",
+                       res);
+      }
+      if (res <= 1e-13 * rn || (res < 1e-2 * rn && res > 0.5 * prev)) {
+        converged = true;
+        break;
+      }
+      prev = res;
+      // T = (3I - M)/2 and T^T, formed in place while slicing, so that Y <- T Y and Z <- T^T Z
+      // are plain products (no addend in the epilogue)
+      CK(form_and_slice(M, ld, nullptr, 0, n, n, nullptr, -0.5, 0.0, 1.5, M, ld,
+                        ns_sl > 0 ? sM : nullptr, ns_sl, nullptr, s,
+                        bits_for(h, GDM_PHASE_NEWTON_SCHULZ)));
+      CK(form_and_slice(Mt, ld, nullptr, 0, n, n, nullptr, -0.5, 0.0, 1.5, Mt, ld,
+                        ns_sl > 0 ? sMt : nullptr, ns_sl, nullptr, s,
+                        bits_for(h, GDM_PHASE_NEWTON_SCHULZ)));
+      CK(product(h, {M, sM}, {Y, sY}, Yn, nullptr, nullptr, 1.0, 0.0, 0.0, true,
+                 GDM_PHASE_NEWTON_SCHULZ));
+      CK(product(h, {Mt, sMt}, {Z, sZ}, Zn, nullptr, nullptr, 1.0, 0.0, 0.0, true,
+                 GDM_PHASE_NEWTON_SCHULZ));
+      std::swap(Y, Yn);
+      std::swap(Z, Zn);
+      CK(slice(h, Y, sY, GDM_PHASE_NEWTON_SCHULZ));
+      CK(slice(h, Z, sZ, GDM_PHASE_NEWTON_SCHULZ));
+    }
+    if (!diverged) break;
   }
   if (info) info->ns_iters = it;
   (void)converged;  // a capped run is still refined below; z_err reports the outcome

@@ -111,6 +111,14 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
                            const int* skip, cudaStream_t stream, int bits = 12,
                            int dot = kDotNone);
 
+// Power iteration for lambda_max of a symmetric positive matrix (iters matrix-vector products
+// in double-float from a fixed start vector), then bounds_dev[1] <- min(bounds_dev[1],
+// factor * estimate); the estimate is also written to *est_dev.  `work` holds >= 2 n doubles,
+// `partials` >= ceil(n / 8).
+cudaError_t power_bound(const double* A, int64_t lda, int n, int iters, double factor,
+                        double* work, double* partials, double* bounds_dev, double* est_dev,
+                        cudaStream_t stream);
+
 // Gershgorin bounds of a symmetric n x n matrix: writes {min_i(a_ii - r_i), max_i(a_ii + r_i)}
 // into out_dev[0..1].  `partials` holds >= 2 * ceil(n / 8) doubles.
 cudaError_t gershgorin(const double* A, int64_t lda, int n, double* partials, double* out_dev,

@@ -17,7 +17,7 @@ import scipy.linalg
 import oracle
 from oracle import steps
 from workloads import (make_config0, make_random_small, make_small_diag, make_spectrum_problem,
-                       haar_orthogonal, make_geometry_step)
+                       haar_orthogonal, make_geometry_step, make_banded)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -416,6 +416,43 @@ def test_hole_particle_form_coincides_with_canonical():
         Xh, c2, beta = steps.hole_particle_step(X)
         assert abs(c - c2) <= 1e-14
         assert np.linalg.norm(Xc - Xh) <= 1e-13
+
+
+# ------------------------------------------------------------------------------------------
+# Truncated purification (threshold filtering, Sec. 2.2.2)
+# ------------------------------------------------------------------------------------------
+
+def test_filter_small_by_hand():
+    A = np.array([[1e-3, -2e-6, 5e-6], [-2e-6, -4e-5, 0.0], [5e-6, 0.0, 1.0]])
+    np.testing.assert_array_equal(steps.filter_small(A, 5e-6),
+                                  [[1e-3, 0.0, 5e-6], [0.0, -4e-5, 0.0], [5e-6, 0.0, 1.0]])
+
+
+def test_truncated_trs4_without_threshold_is_the_projector():
+    p = make_banded(7, 256, 64, s_amp=0.0)
+    X, it = steps.trs4_purify_truncated(p.H, 64, 0.0)
+    Q = p.factors["Q"]
+    assert rel(X, Q[:, :64] @ Q[:, :64].T) <= 1e-12
+    assert it < 60
+
+
+def test_truncated_trs4_error_grows_with_threshold_and_keeps_count():
+    p = make_banded(8, 512, 128, s_amp=0.0)
+    Q = p.factors["Q"]
+    Pex = Q[:, :128] @ Q[:, :128].T
+    errs = []
+    for tau in (1e-9, 1e-7, 1e-5):
+        X, _ = steps.trs4_purify_truncated(p.H, 128, tau)
+        assert abs(np.trace(X) - 128) <= 1e-10
+        assert np.array_equal(X, X.T)
+        errs.append(rel(X, Pex))
+    assert errs[0] < errs[1] < errs[2]
+    assert errs[0] <= 1e-6 and errs[2] <= 1e-1
+    # the filtered iterate is sparse: most entries far from the diagonal are exactly zero
+    X, _ = steps.trs4_purify_truncated(p.H, 128, 1e-5)
+    idx = np.arange(512)
+    far = np.abs(idx[:, None] - idx[None, :]) > 256
+    assert np.mean(X[far] == 0.0) > 0.5
 
 
 def test_newton_schulz_and_refinement():

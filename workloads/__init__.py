@@ -17,4 +17,5 @@ from .synthetic import (  # noqa: F401
     make_small_diag,
     make_random_small,
     make_geometry_step,
+    make_banded,
 )

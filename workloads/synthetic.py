@@ -239,6 +239,40 @@ def make_config2(seed: int = 2, n: int = 8192, n_occ: int = 2048, s_amp: float =
                         s_amp=s_amp, cond_S=float(w.max() / w.min())))
 
 
+def make_banded(seed: int, n: int, n_occ: int, decay: float = 8.0, gap: float = 0.5,
+                s_amp: float = 0.3, s_decay: float = 8.0, device=None) -> Problem:
+    """Local (sparse-regime) variant of config 2: H_base_ij = g_ij exp(-|i-j|/decay) with the
+    gap at n_occ opened to `gap` by shifting the occupied / virtual eigenvalues apart, and
+    S = I + s_amp exp(-|i-j|/s_decay) off the diagonal (s_amp = 0 gives S = I, an orthogonal
+    basis).  With decay 8 and gap 0.5 the density matrix decays fast enough that most of its
+    128 x 128 tiles fall below 1e-5 at n = 2048 and above."""
+    rng = np.random.default_rng(seed)
+    be = _backend(device)
+    g = rng.standard_normal((n, n))
+    g = (g + g.T) / math.sqrt(2.0)
+    idx = np.arange(n)
+    dist = np.abs(idx[:, None] - idx[None, :]).astype(np.float64)
+    Hb = g * np.exp(-dist / decay)
+    del g
+    L, V = be.eigh(be.asarray(Hb))
+    L = be.to_numpy(L).copy()
+    shift = 0.5 * (gap - (L[n_occ] - L[n_occ - 1]))
+    L[:n_occ] -= shift
+    L[n_occ:] += shift
+    L[n_occ] = L[n_occ - 1] + gap
+    S0 = np.eye(n) + s_amp * np.exp(-dist / s_decay) * (1.0 - np.eye(n))
+    del dist
+    S_w, S_U = be.eigh(be.asarray(S0))
+    w = be.to_numpy(S_w)
+    if s_amp == 0.0:
+        S_U = be.asarray(np.eye(n))
+        w = np.ones(n)
+    H, S = _assemble(be, V, L, S_U, w)
+    return _finish(be, H, S, n_occ, V, L, S_U, w,
+                   dict(config="banded", seed=seed, n=n, n_occ=n_occ, decay=decay, gap=gap,
+                        s_amp=s_amp, cond_S=float(w.max() / w.min())))
+
+
 def make_batch_config3(seed: int = 3, count: int = 64, n_lo: int = 512, n_hi: int = 3072,
                        device=None):
     """Batched spin / multi-molecule set: `count` independent problems, n log-uniform in

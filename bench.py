@@ -45,6 +45,10 @@ WORKLOADS = {
     "config4": dict(desc="config4: serving stream, Poisson arrivals, n log-uniform [256, 8192], "
                          "n_occ = n/4, gap log-uniform [0.05, 0.5], S as config0",
                     n=8192, n_occ=2048),
+    "banded8192": dict(desc="banded8192: local sparse-regime system, n=8192, n_occ=2048, "
+                            "H_ij = g_ij exp(-|i-j|/8) with a 0.5 gap at n_occ, "
+                            "S = I + 0.3 exp(-|i-j|/8) (for --truncation)",
+                       n=8192, n_occ=2048),
 }
 
 
@@ -58,6 +62,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-fp64-ref", action="store_true", help="skip the all-FP64 GPU solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--truncation", type=float, default=0.0,
+                    help="threshold filtering of the purification (0: off)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the TRS2 / canonical purification solves")
     ap.add_argument("--concurrency", type=int, default=4, help="batch / server worker count")
@@ -106,6 +112,9 @@ def _generate(name, seed, device):
         return workloads.make_config1(seed=seed, device=device)
     if name == "config2":
         return workloads.make_config2(seed=seed, device=device)
+    if name == "banded8192":
+        return workloads.make_banded(seed, 8192, 2048, decay=8.0, gap=0.5, s_amp=0.3,
+                                     device=device)
     return workloads.make_config0(seed=seed, device=device)
 
 
@@ -317,6 +326,8 @@ def run_ours(args):
     h = g.Handle(n, n_occ, device=local)
     h.set_stream(stream)
     h.set_profiling(True)
+    if args.truncation > 0.0:
+        h.set_truncation(args.truncation)
 
     def step():
         h.reinit()
@@ -459,6 +470,8 @@ def run_ours(args):
                        "p99": per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)]},
         "accuracy": {"rel_frobenius_err": relerr, "abs_energy_err": abs(e - Ec),
                      "trace_err": info["trace_err"], "trace_err_raw": info["trace_err_raw"],
+                     "truncation": args.truncation,
+                     "kstage_fraction": info["kstage_fraction"],
                      "ns_iters": info["ns_iters"], "refine_iters": info["refine_iters"],
                      "z_err": info["z_err"], "idem_err": info["idem_err"],
                      "purif_iters": info["purif_iters"]},

@@ -96,6 +96,8 @@ typedef struct {
   double eps_min, eps_max; /* Gershgorin bounds of H~ */
   double ms_total;     /* device time of the solve (ms), CUDA events on the handle's stream */
   double trace_fix;    /* final trace reset of the orthogonal-basis matrix: N / Tr X - 1 */
+  double kstage_fraction; /* truncated purification: k stages the products issued over the
+                             stages of the dense products (1 without truncation) */
 } gdm_info;
 
 /* Create a handle for n_basis x n_basis problems with n_occ occupied states (f_l in {0,1})
@@ -106,6 +108,16 @@ gdm_status gdm_init(gdm_handle** h, int64_t n_basis, int64_t n_occ, int device);
 
 /* Choose the product arithmetic (default GDM_PREC_MIXED).  Invalidates a cached Z. */
 gdm_status gdm_set_precision(gdm_handle* h, gdm_precision prec);
+
+/* Truncated (sparse-regime) purification, Sec. 2.2.2: with threshold > 0 every matrix that
+ * enters a purification product (the initial guess, X^2, W and each new iterate) has its
+ * elements with |x_ij| < threshold set to zero, and the products skip the 128-wide k blocks where
+ * an operand's 128 x 128 tile is empty.  The result is then an approximation whose error grows
+ * with the threshold (about 5e-5 relative at 1e-7 and 5e-3 at 1e-5 on a local test system); it
+ * pays off only when the density matrix is local enough for whole tiles to vanish.  The
+ * Loewdin transforms stay dense.  threshold = 0 (the default) turns it off.
+ * Errors: GDM_ERR_ARG (negative or non-finite threshold). */
+gdm_status gdm_set_truncation(gdm_handle* h, double threshold);
 
 /* Select the purification map for later solves (default GDM_PURIFY_TRS4).  Errors: GDM_ERR_ARG. */
 gdm_status gdm_set_purification(gdm_handle* h, gdm_purification method);

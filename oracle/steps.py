@@ -208,6 +208,8 @@ def filter_small(A, tau):
 def trs4_purify_truncated(Ht, n_occ, tau, idem_tol=1e-13, max_iter=200, bounds=None):
     """TRS4 with threshold filtering of every matrix that enters a product: the initial guess,
     each X^2 = X X, each W, and each new iterate (X^2 W, 2X - X^2 or X^2) are filtered at tau.
+    Filtering breaks the commutation of X^2 and W, so X^2 W is symmetrised before it is
+    filtered (its antisymmetric part is of the order of tau).
     The controller follows the engine's reading of the paper: stop when Tr(X - X^2) <= idem_tol N,
     or when it stops halving below 1e-4 N (keeping the better of the last two iterates); once
     Tr(X - X^2) < 0.1 and |Tr X - N| < 0.25 the McWeeny step X^2 (3I - 2X) replaces the TRS4
@@ -237,7 +239,7 @@ def trs4_purify_truncated(Ht, n_occ, tau, idem_tol=1e-13, max_iter=200, bounds=N
         endgame = abs(idem) < 0.1 and abs(t1 - N) < 0.25
         if endgame or not trG > 1e-12 * N:
             W = filter_small(3.0 * I - 2.0 * X, tau)
-            X = filter_small(X2 @ W, tau)
+            X = filter_small(sym(X2 @ W), tau)
             continue
         g = (N - trF) / trG
         if g > 6.0:
@@ -246,7 +248,7 @@ def trs4_purify_truncated(Ht, n_occ, tau, idem_tol=1e-13, max_iter=200, bounds=N
             X = X2
         else:
             W = filter_small(g * I + (4.0 - 2.0 * g) * X + (g - 3.0) * X2, tau)
-            X = filter_small(X2 @ W, tau)
+            X = filter_small(sym(X2 @ W), tau)
     X = X * (N / np.trace(X))
     return sym(X), it
 

@@ -38,7 +38,8 @@ class gdm_info(ctypes.Structure):
                 ("trace_err", ctypes.c_double), ("trace_err_raw", ctypes.c_double),
                 ("energy", ctypes.c_double),
                 ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double),
-                ("ms_total", ctypes.c_double), ("trace_fix", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("trace_fix", ctypes.c_double),
+                ("kstage_fraction", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -88,6 +89,7 @@ def _decl(name, res, args):
 _decl("gdm_init", _int, [ctypes.POINTER(_vp), _i64, _i64, _int])
 _decl("gdm_set_precision", _int, [_vp, _int])
 _decl("gdm_set_purification", _int, [_vp, _int])
+_decl("gdm_set_truncation", _int, [_vp, _dbl])
 _decl("gdm_set_slices", _int, [_vp, _int, _int, _int, _int])
 _decl("gdm_set_tolerance", _int, [_vp, _dbl, _dbl])
 _decl("gdm_set_max_iter", _int, [_vp, _int, _int])
@@ -180,6 +182,10 @@ class Handle:
 
     def set_precision(self, prec):
         return self._check(gdm_set_precision(self._h, prec))
+
+    def set_truncation(self, threshold):
+        """Threshold filtering of the purification (0 turns it off)."""
+        return self._check(gdm_set_truncation(self._h, float(threshold)))
 
     def set_purification(self, method):
         """GDM_PURIFY_TRS4 (default), GDM_PURIFY_TRS2 or GDM_PURIFY_CANONICAL."""

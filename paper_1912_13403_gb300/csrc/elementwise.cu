@@ -439,15 +439,28 @@ __device__ __forceinline__ uint2 axpby_words(double a, uint2 x, double b, uint2 
 // y = a x + b x2 (FP64); c I is added out of line on the diagonal element.  Everything that
 // is not FP64 arithmetic stays in integer types: on GB300 a double that takes part in integer
 // selects can cost FP64-pipe instructions.
+// Threshold filtering for the sparse (truncated) purification (TruncArgs, gdm_internal.h).
+__device__ __forceinline__ bool filter_words(unsigned& whi, unsigned& wlo,
+                                             unsigned long long tau_bits) {
+  const unsigned long long mag =
+      (static_cast<unsigned long long>(whi & 0x7FFFFFFFu) << 32) | wlo;
+  const bool keep = mag >= tau_bits;
+  whi = keep ? whi : 0u;
+  wlo = keep ? wlo : 0u;
+  return keep && mag != 0ull;
+}
+
 template <int MODE, int DOT>
 __device__ __forceinline__ void form_norm_row(const uint4* __restrict__ xr,
                                               const uint4* __restrict__ x2r, uint4* yr,
                                               int npairs, int row, int lane, double a, double b,
                                               int ak, bool aneg, bool has_c, double c,
-                                              float& ss, DF& acc) {
+                                              const TruncArgs& tr, float& ss, DF& acc) {
   constexpr bool kNeedX2 = (MODE == kFormGeneral) || (DOT == kDotX2);
   const bool with_x2 = x2r != nullptr;
-  auto one = [&](int p, uint4 x, uint4 x2) {
+  const bool trunc = tr.tau_bits != 0ull;
+  // returns whether the pair keeps a non-zero element (only meaningful with truncation)
+  auto one = [&](int p, uint4 x, uint4 x2) -> bool {
     uint4 y = x;
     if (MODE == kFormPow2) {
       pow2_words(y.y, y.x, ak, aneg);
@@ -468,6 +481,12 @@ __device__ __forceinline__ void form_norm_row(const uint4* __restrict__ xr,
         y.w = d.y;
       }
     }
+    bool nz = false;
+    if (trunc) {
+      const bool k0 = filter_words(y.y, y.x, tr.tau_bits);
+      const bool k1 = filter_words(y.w, y.z, tr.tau_bits);
+      nz = k0 || k1;
+    }
     if (yr != nullptr) yr[p] = y;
     float h0, l0, h1, l1;
     split_words(y.y, y.x, h0, l0);
@@ -485,24 +504,46 @@ __device__ __forceinline__ void form_norm_row(const uint4* __restrict__ xr,
       acc = df_fma(acc, h0, l0, ph0, pl0);
       acc = df_fma(acc, h1, l1, ph1, pl1);
     }
+    return nz;
   };
-  constexpr int U = 4;  // loads of U column pairs in flight per lane
-  int p0 = lane;
-  for (; p0 + 32 * (U - 1) < npairs; p0 += 32 * U) {
+  // Warp-uniform loops: full blocks of 32 * U column pairs (U loads in flight per lane), then
+  // steps of 32 pairs.  A block of 64 pairs is one 128-column tile.
+  constexpr int U = 4;
+  uint32_t* mrow = (trunc && tr.mask != nullptr)
+                       ? tr.mask + static_cast<int64_t>(row >> 7) * tr.mask_ld : nullptr;
+  int base = 0;
+  for (; base + 32 * U <= npairs; base += 32 * U) {
     uint4 xv[U], x2v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      xv[u] = xr[p0 + 32 * u];
-      if (kNeedX2 && with_x2) x2v[u] = x2r[p0 + 32 * u];
+      xv[u] = xr[base + lane + 32 * u];
+      if (kNeedX2 && with_x2) x2v[u] = x2r[base + lane + 32 * u];
       else x2v[u] = make_uint4(0u, 0u, 0u, 0u);
     }
+    bool nz[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) one(p0 + 32 * u, xv[u], x2v[u]);
+    for (int u = 0; u < U; ++u) nz[u] = one(base + lane + 32 * u, xv[u], x2v[u]);
+    if (mrow != nullptr) {
+      const bool lo_blk = __any_sync(0xffffffffu, nz[0] || nz[1]);
+      const bool hi_blk = __any_sync(0xffffffffu, nz[2] || nz[3]);
+      if (lane == 0) {
+        if (lo_blk) mrow[base >> 6] = 1u;
+        if (hi_blk) mrow[(base >> 6) + 1] = 1u;
+      }
+    }
   }
-  for (; p0 < npairs; p0 += 32) {
-    const uint4 x = xr[p0];
-    const uint4 x2 = (kNeedX2 && with_x2) ? x2r[p0] : make_uint4(0u, 0u, 0u, 0u);
-    one(p0, x, x2);
+  for (; base < npairs; base += 32) {
+    const int p = base + lane;
+    bool nz = false;
+    if (p < npairs) {
+      const uint4 x = xr[p];
+      const uint4 x2 = (kNeedX2 && with_x2) ? x2r[p] : make_uint4(0u, 0u, 0u, 0u);
+      nz = one(p, x, x2);
+    }
+    if (mrow != nullptr) {
+      const bool any = __any_sync(0xffffffffu, nz);
+      if (lane == 0 && any) mrow[base >> 6] = 1u;
+    }
   }
 }
 
@@ -510,23 +551,24 @@ template <int MODE>
 __device__ __forceinline__ void form_norm_dispatch(int dot, const uint4* xr, const uint4* x2r,
                                                    uint4* yr, int npairs, int row, int lane,
                                                    double a, double b, int ak, bool aneg,
-                                                   bool has_c, double c, float& ss, DF& acc) {
+                                                   bool has_c, double c, const TruncArgs& tr,
+                                                   float& ss, DF& acc) {
   switch (dot) {
     case kDotSelf:
-      form_norm_row<MODE, kDotSelf>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, ss,
-                                    acc);
+      form_norm_row<MODE, kDotSelf>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, tr,
+                                    ss, acc);
       break;
     case kDotX2:
-      form_norm_row<MODE, kDotX2>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, ss,
-                                  acc);
+      form_norm_row<MODE, kDotX2>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, tr,
+                                  ss, acc);
       break;
     case kDotX:
-      form_norm_row<MODE, kDotX>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, ss,
-                                 acc);
+      form_norm_row<MODE, kDotX>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, tr,
+                                 ss, acc);
       break;
     default:
-      form_norm_row<MODE, kDotNone>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, ss,
-                                    acc);
+      form_norm_row<MODE, kDotNone>(xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c, tr,
+                                    ss, acc);
   }
 }
 
@@ -534,7 +576,7 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32, 4)
     form_norm_kernel(const double* __restrict__ X, int64_t ldx, const double* __restrict__ X2,
                      int64_t ldx2, int rows, int cols, const double* __restrict__ coef_dev,
                      double ha, double hb, double hc, double* Y, int64_t ldy, double* out_scale,
-                     const int* skip, int dot, double* row_dot) {
+                     const int* skip, int dot, double* row_dot, TruncArgs tr) {
   if (skip != nullptr && *skip != 0) return;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * kRowsPerBlock + w;
@@ -561,13 +603,13 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32, 4)
   DF acc{0.0f, 0.0f};
   if (mode == kFormPlain)
     form_norm_dispatch<kFormPlain>(dot, xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c,
-                                   ss, acc);
+                                   tr, ss, acc);
   else if (mode == kFormPow2)
     form_norm_dispatch<kFormPow2>(dot, xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c, c,
-                                  ss, acc);
+                                  tr, ss, acc);
   else
     form_norm_dispatch<kFormGeneral>(dot, xr, x2r, yr, npairs, row, lane, a, b, ak, aneg, has_c,
-                                     c, ss, acc);
+                                     c, tr, ss, acc);
   if (dot != kDotNone) {
     acc = df_warp_sum(acc);
     if (lane == 0) row_dot[row] = df_to_double(acc);
@@ -1214,10 +1256,32 @@ __global__ void identity_kernel(double* A, int64_t lda, int n) {
 cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64_t ldx2,
                            int rows, int cols, const double* coef_dev, double ha, double hb,
                            double hc, double* Y, int64_t ldy, SliceBuf* out, int nslice,
-                           const int* skip, cudaStream_t stream, int bits, int dot) {
+                           const int* skip, cudaStream_t stream, int bits, int dot,
+                           const TruncArgs* trunc) {
   if (rows <= 0) return cudaSuccess;
   if (bits < 9 || bits > 12) return cudaErrorInvalidValue;
   if (dot == kDotX2 && X2 == nullptr) return cudaErrorInvalidValue;
+  TruncArgs tr;
+  if (out != nullptr) out->mask_valid = false;
+  if (trunc != nullptr && trunc->tau_bits != 0ull) {
+    tr.tau_bits = trunc->tau_bits;
+    // the filtered values must reach memory (the element pass and later steps read them)
+    if (Y == nullptr) {
+      Y = const_cast<double*>(X);
+      ldy = ldx;
+    }
+    // tile occupancy goes to the output slice buffer when it has storage for it
+    if (out != nullptr && nslice > 0 && out->tile_mask != nullptr &&
+        out->mask_ld >= (cols + 127) / 128) {
+      tr.mask = out->tile_mask;
+      tr.mask_ld = out->mask_ld;
+      const cudaError_t e = cudaMemsetAsync(
+          tr.mask, 0, sizeof(uint32_t) * static_cast<size_t>((rows + 127) / 128) * tr.mask_ld,
+          stream);
+      if (e != cudaSuccess) return e;
+      out->mask_valid = true;
+    }
+  }
   __half* od = nullptr;
   double* osc = nullptr;
   int64_t old = 0, plane = 0;
@@ -1244,6 +1308,7 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
                          (reinterpret_cast<uintptr_t>(od) % 4 == 0)));
   const bool host_plain = (coef_dev == nullptr) && ha == 1.0 && (X2 == nullptr || hb == 0.0) &&
                           hc == 0.0;
+  if (tr.tau_bits != 0ull && !aligned) return cudaErrorInvalidValue;  // filtering: two passes
   if (aligned && (host_plain || Y != nullptr || od == nullptr)) {
     // two passes: rows (form + norm) then elements (slices), both fully parallel
     const int nb = (rows + kRowsPerBlock - 1) / kRowsPerBlock;
@@ -1252,7 +1317,7 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
     form_norm_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(
         X, ldx, X2, ldx2, rows, cols, coef_dev, ha, hb, hc, Y, ldy,
         od != nullptr ? osc : nullptr, skip, with_dot ? dot : kDotNone,
-        with_dot ? out->row_dot : nullptr);
+        with_dot ? out->row_dot : nullptr, tr);
     if (with_dot)
       out->dot_partner = (dot == kDotX2) ? X2 : (dot == kDotX ? X : (Y != nullptr ? Y : X));
     if (od != nullptr) {

@@ -38,6 +38,7 @@ enum SmallSlot {
   SM_COEF_B = 8,     // 3
   SM_COEF_X0 = 12,   // 3
   SM_RED = 16,       // 8 reduction outputs
+  SM_KCOUNT = 24,    // 1: k stages issued by masked products (as an unsigned 64-bit count)
 };
 
 gdm_status set_err(gdm_handle* h, gdm_status st, const char* fmt, ...) {
@@ -140,6 +141,17 @@ cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const dou
     a.diag = diag;
     a.coef = coef;
     a.err = h->err_dev;
+    // truncated purification: skip the k blocks where an operand tile is empty
+    if (ph == GDM_PHASE_PURIFY && h->trunc_tau > 0.0 && A.sl->mask_valid && Bt.sl->mask_valid) {
+      a.mask_a = A.sl->tile_mask;
+      a.mask_b = Bt.sl->tile_mask;
+      a.mask_ld = A.sl->mask_ld;
+      a.kcount = reinterpret_cast<unsigned long long*>(h->small + SM_KCOUNT);
+      const double t = std::ceil(static_cast<double>(n) / 128.0);
+      const double nk = std::ceil(static_cast<double>(n) /
+                                  static_cast<double>(sliced_gemm_bk(h->phase[ph].nslice)));
+      h->kstages_dense += (sym ? t * (t + 1) / 2 : t * t) * nk;
+    }
     // exact diagonal from the row dot products of the right operand's slicing pass, when that
     // pass paired its rows with the left operand (X X, X^2 W, delta delta)
     if (exact_diag && Bt.sl->row_dot != nullptr && Bt.sl->dot_partner == A.f)
@@ -199,11 +211,25 @@ cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const dou
 }
 
 // Slice `src` (FP64) into `dst` in the format of phase `ph` (no-op when that phase is FP64).
-cudaError_t slice(gdm_handle* h, const double* src, SliceBuf* dst, int ph, int dot = kDotNone) {
-  if (!sliced(h, ph)) return cudaSuccess;
+// Threshold filtering for the purification's operands when truncation is on (else null).
+const TruncArgs* purify_trunc(const gdm_handle* h, TruncArgs* tmp) {
+  if (!(h->trunc_tau > 0.0)) return nullptr;
+  double t = h->trunc_tau;
+  std::memcpy(&tmp->tau_bits, &t, sizeof(t));
+  return tmp;
+}
+
+cudaError_t slice(gdm_handle* h, const double* src, SliceBuf* dst, int ph, int dot = kDotNone,
+                  const TruncArgs* trunc = nullptr) {
   const int n = static_cast<int>(h->n);
+  if (!sliced(h, ph)) {
+    if (trunc == nullptr) return cudaSuccess;
+    // FP64 products: filter the matrix in place (no slices)
+    return form_and_slice(src, h->ld, nullptr, 0, n, n, nullptr, 1.0, 0.0, 0.0, nullptr, 0,
+                          nullptr, 0, nullptr, h->stream, 12, kDotNone, trunc);
+  }
   return form_and_slice(src, h->ld, nullptr, 0, n, n, nullptr, 1.0, 0.0, 0.0, nullptr, 0, dst,
-                        h->phase[ph].nslice, nullptr, h->stream, h->phase[ph].bits, dot);
+                        h->phase[ph].nslice, nullptr, h->stream, h->phase[ph].bits, dot, trunc);
 }
 
 int bits_for(const gdm_handle* h, int ph) { return h->phase[ph].bits; }
@@ -435,9 +461,16 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   double* X = h->f[F_X];
   double* X2 = h->f[F_X2];
   double* Xn = h->f[F_XN];
+  // truncated purification (gdm_set_truncation): every matrix entering a product is filtered
+  TruncArgs trunc_args;
+  const TruncArgs* tr = purify_trunc(h, &trunc_args);
+  h->kstages_dense = 0.0;
+  h->kstages_issued = 0.0;
+  if (tr != nullptr)
+    CK(cudaMemsetAsync(h->small + SM_KCOUNT, 0, sizeof(unsigned long long), s));
   CK(form_and_slice(Ht, ld, nullptr, 0, n, n, h->small + SM_COEF_X0, 0, 0, 0, X, ld,
                     pu_sl > 0 ? &h->sl[SL_X] : nullptr, pu_sl, nullptr, s,
-                    bits_for(h, GDM_PHASE_PURIFY), kDotSelf));
+                    bits_for(h, GDM_PHASE_PURIFY), kDotSelf, tr));
 
   // TRS4
   Trs4State init;
@@ -455,6 +488,8 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   for (it = 0; it < h->max_purif; ++it) {
     CK(product(h, {X, &h->sl[SL_X]}, {X, &h->sl[SL_X]}, X2, nullptr, nullptr, 1.0, 0.0, 0.0, true,
                GDM_PHASE_PURIFY, nullptr, true));
+    // with truncation X^2 is filtered (and sliced) before its traces are taken
+    if (tr != nullptr) CK(slice(h, X2, &h->sl[SL_X2], GDM_PHASE_PURIFY, kDotNone, tr));
     int nb = 0;
     CK(trs4_traces(X, X2, ld, n, h->partials, &nb, s));
     CK(trs4_control(h->partials, nb, h->st_dev, tol_abs, s));
@@ -479,22 +514,25 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
     if (t.branch == 4) {  // canonical: X <- X W, W = a X + b X^2 + c I (X's slices are current)
       CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefW)), 0, 0, 0,
                         W, ld, pu_sl > 0 ? &h->sl[SL_W] : nullptr, pu_sl, nullptr, s,
-                        bits_for(h, GDM_PHASE_PURIFY), kDotX));
+                        bits_for(h, GDM_PHASE_PURIFY), kDotX, tr));
       CK(product(h, {X, &h->sl[SL_X]}, {W, &h->sl[SL_W]}, Xn, nullptr, nullptr, 1.0, 0.0, 0.0,
-                 true, GDM_PHASE_PURIFY, nullptr, true));
-      CK(slice(h, Xn, &h->sl[SL_X], GDM_PHASE_PURIFY, kDotSelf));
+                 tr == nullptr, GDM_PHASE_PURIFY, nullptr, true));
+      if (tr != nullptr) CK(symmetrise(Xn, ld, n, s));
+      CK(slice(h, Xn, &h->sl[SL_X], GDM_PHASE_PURIFY, kDotSelf, tr));
     } else if (t.branch == 2 || t.branch == 3) {  // a product: F + gamma G, or McWeeny
-      CK(slice(h, X2, &h->sl[SL_X2], GDM_PHASE_PURIFY));
+      if (tr == nullptr) CK(slice(h, X2, &h->sl[SL_X2], GDM_PHASE_PURIFY));
       CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefW)), 0, 0, 0,
                         W, ld, pu_sl > 0 ? &h->sl[SL_W] : nullptr, pu_sl, nullptr, s,
-                        bits_for(h, GDM_PHASE_PURIFY), kDotX2));
+                        bits_for(h, GDM_PHASE_PURIFY), kDotX2, tr));
+      // with filtering X^2 and W no longer commute: the full product is symmetrised
       CK(product(h, {X2, &h->sl[SL_X2]}, {W, &h->sl[SL_W]}, Xn, nullptr, nullptr, 1.0, 0.0, 0.0,
-                 true, GDM_PHASE_PURIFY, nullptr, true));
-      CK(slice(h, Xn, &h->sl[SL_X], GDM_PHASE_PURIFY, kDotSelf));
+                 tr == nullptr, GDM_PHASE_PURIFY, nullptr, true));
+      if (tr != nullptr) CK(symmetrise(Xn, ld, n, s));
+      CK(slice(h, Xn, &h->sl[SL_X], GDM_PHASE_PURIFY, kDotSelf, tr));
     } else {
       CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefX)), 0, 0, 0,
                         Xn, ld, pu_sl > 0 ? &h->sl[SL_X] : nullptr, pu_sl, nullptr, s,
-                        bits_for(h, GDM_PHASE_PURIFY), kDotSelf));
+                        bits_for(h, GDM_PHASE_PURIFY), kDotSelf, tr));
     }
     std::swap(X, Xn);
   }
@@ -504,6 +542,14 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
     info->purif_iters = it;
     info->stop_reason = stop;
     info->idem_err = last_idem;
+    info->kstage_fraction = 1.0;
+  }
+  if (tr != nullptr && h->kstages_dense > 0.0) {
+    unsigned long long issued = 0;
+    CK(cudaMemcpyAsync(&issued, h->small + SM_KCOUNT, sizeof(issued), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h->kstages_issued = static_cast<double>(issued);
+    if (info) info->kstage_fraction = h->kstages_issued / h->kstages_dense;
   }
   if (stop == 3) return set_err(h, GDM_ERR_NONFINITE, "non-finite traces during purification");
 
@@ -606,9 +652,11 @@ struct PoolLayout {
     auto up = [](size_t x) { return (x + 1023) / 1024 * 1024; };
     const size_t ld = static_cast<size_t>((n + 63) / 64 * 64);
     const size_t rows_alloc = static_cast<size_t>((n + 127) / 128 * 128);
+    const size_t tiles = rows_alloc / 128;
     fbytes = up(sizeof(double) * ld * static_cast<size_t>(n));
     sdata = up(sizeof(__half) * 4 * ld * rows_alloc);
-    sscale = up(2 * sizeof(double) * rows_alloc);  // row scales, then row dot products
+    // row scales, row dot products, then the 128 x 128 tile occupancy words
+    sscale = up(2 * sizeof(double) * rows_alloc + sizeof(uint32_t) * tiles * tiles);
     pbytes = up(sizeof(double) * (kTraceTerms * static_cast<size_t>((n + 7) / 8) + 64));
     small_bytes = up(sizeof(double) * kSmall);
     st_bytes = up(sizeof(Trs4State));
@@ -640,6 +688,7 @@ gdm_status handle_reconfigure(gdm_handle* h, int64_t n, int64_t n_occ) {
     h->sl[i].cols = static_cast<int>(n);
     h->sl[i].nslice_valid = 0;
     h->sl[i].dot_partner = nullptr;
+    h->sl[i].mask_valid = false;
   }
   return GDM_OK;
 }
@@ -707,6 +756,8 @@ gdm_status gdm_init(gdm_handle** out, int64_t n_basis, int64_t n_occ, int device
     p += L.sdata;
     h->sl[i].row_scale = reinterpret_cast<double*>(p);
     h->sl[i].row_dot = h->sl[i].row_scale + h->rows_alloc;
+    h->sl[i].tile_mask = reinterpret_cast<uint32_t*>(h->sl[i].row_dot + h->rows_alloc);
+    h->sl[i].mask_ld = h->rows_alloc / 128;
     p += L.sscale;
     h->sl[i].ld = static_cast<int>(h->ld);
     h->sl[i].rows_alloc = h->rows_alloc;
@@ -749,6 +800,14 @@ gdm_status gdm_set_purification(gdm_handle* h, gdm_purification method) {
   if (method != GDM_PURIFY_TRS4 && method != GDM_PURIFY_TRS2 && method != GDM_PURIFY_CANONICAL)
     return set_err(h, GDM_ERR_ARG, "unknown purification method %d", static_cast<int>(method));
   h->purify = static_cast<int>(method);
+  return GDM_OK;
+}
+
+gdm_status gdm_set_truncation(gdm_handle* h, double threshold) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  if (!(threshold >= 0.0) || !std::isfinite(threshold))
+    return set_err(h, GDM_ERR_ARG, "truncation threshold must be finite and >= 0");
+  h->trunc_tau = threshold;
   return GDM_OK;
 }
 

@@ -33,6 +33,11 @@ struct SliceBuf {
   // dot_partner == nullptr: row_dot holds nothing for the current slices.
   double* row_dot = nullptr;     // [rows_alloc] or null (no storage)
   const double* dot_partner = nullptr;
+  // optional tile occupancy (ceil(rows/128) x mask_ld words) written by a filtering pass;
+  // mask_valid says that it describes the current slices
+  uint32_t* tile_mask = nullptr;
+  int mask_ld = 0;
+  bool mask_valid = false;
 };
 
 // Slice count and highest slice-pair order used by a product.
@@ -61,6 +66,13 @@ struct SlicedGemmArgs {
   double diag = 0.0;                  // added to the diagonal of C
   const double* coef = nullptr;       // optional device {alpha, beta}
   const double* diag_dot = nullptr;   // optional: exact sum_k A_ik Bt_ik replaces C_ii's product
+  // optional 128 x 128 tile occupancy of A and Bt (TruncArgs masks, row block x k block):
+  // k blocks where either operand's tile is empty are skipped (the first k block always runs,
+  // so every accumulator is written); kcount (optional) receives the k stages issued
+  const uint32_t* mask_a = nullptr;
+  const uint32_t* mask_b = nullptr;
+  int mask_ld = 0;
+  unsigned long long* kcount = nullptr;
   const int* skip = nullptr;          // optional device flag: non-zero -> no-op launch
   uint32_t* err = nullptr;
   int tiles_n = 0, tiles_m = 0;
@@ -73,6 +85,9 @@ int64_t launch_count();
 int build_pairs(int nslice, int max_order, SlicedGemmArgs* a);
 cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& Bt, const Precision& prec,
                         SlicedGemmArgs args, cudaStream_t stream);
+
+// K elements per pipeline stage of sliced_gemm for a format with `nslice` slices.
+int sliced_gemm_bk(int nslice);
 
 // FP64 product C = alpha * A * Bt^T + beta * D (+ mirror / transposed copy as above).
 struct F64GemmArgs {
@@ -103,13 +118,25 @@ cudaError_t f64_gemm(const F64GemmArgs& a, cudaStream_t stream);
 // (out->dot_partner then names the partner matrix; otherwise it is reset to null).
 enum { kDotNone = 0, kDotSelf = 1, kDotX2 = 2, kDotX = 3 };
 
+// Threshold filtering of the sparse (truncated) purification: values with |y| < tau become zero
+// (tau given by the bit pattern of the positive double, compared with the magnitude bits), and
+// mask[(row / 128) * mask_ld + col / 128] = 1 marks each 128 x 128 tile that keeps a non-zero
+// element.  tau_bits == 0 turns it off.  form_and_slice takes the mask from its output slice
+// buffer (tile_mask) and sets mask_valid there; it writes the filtered values in place when Y
+// is null.
+struct TruncArgs {
+  unsigned long long tau_bits = 0;
+  uint32_t* mask = nullptr;
+  int mask_ld = 0;
+};
+
 // purification maps (the values of gdm_purification)
 enum { kPurifyTrs4 = 0, kPurifyTrs2 = 1, kPurifyCanonical = 2 };
 cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64_t ldx2,
                            int rows, int cols, const double* coef_dev, double ha, double hb,
                            double hc, double* Y, int64_t ldy, SliceBuf* out, int nslice,
                            const int* skip, cudaStream_t stream, int bits = 12,
-                           int dot = kDotNone);
+                           int dot = kDotNone, const TruncArgs* trunc = nullptr);
 
 // Power iteration for lambda_max of a symmetric positive matrix (iters matrix-vector products
 // in double-float from a fixed start vector), then bounds_dev[1] <- min(bounds_dev[1],

@@ -155,6 +155,17 @@ __device__ __noinline__ double diagonal_value(double v, const double* diag_dot, 
   return v + shift;
 }
 
+// Does the k stage kb of tile (ti, tj) contribute?  Only with tile masks: the first 128-wide
+// k block always runs (so that every accumulator is written), the others when both operand
+// tiles hold a non-zero element.
+__device__ __forceinline__ bool kstage_active(const uint32_t* mask_a, const uint32_t* mask_b,
+                                              int mask_ld, int ti, int tj, int kb, int bk) {
+  if (mask_a == nullptr) return true;
+  const int k128 = (kb * bk) >> 7;
+  if (k128 == 0) return true;
+  return __ldg(mask_a + ti * mask_ld + k128) != 0u && __ldg(mask_b + tj * mask_ld + k128) != 0u;
+}
+
 template <int NSLICE, int BK, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     sliced_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
@@ -212,7 +223,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         int ti, tj;
         if (sym) upper_tile(tile, tn, ti, tj);
         else { ti = tile / tn; tj = tile % tn; }
-        for (int kb = 0; kb < nk; ++kb, ++it) {
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!kstage_active(args.mask_a, args.mask_b, args.mask_ld, ti, tj, kb, BK)) continue;
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
           if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1u, args.err, &abort_flag)) {
@@ -223,6 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint8_t* st = smem + s * Cfg::kStageBytes;
           tma_load_3d(st, &tmA, &full_bar[s], kb * BK, ti * kBM, 0);
           tma_load_3d(st + NSLICE * Cfg::kTileBytes, &tmB, &full_bar[s], kb * BK, tj * kBN, 0);
+          ++it;
         }
       }
       if (stop) {
@@ -254,6 +267,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (p < np) seen |= 1u << o;
       }
       int it = 0, tcount = 0;
+      unsigned long long issued = 0;
       bool stop = false;
       for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x, ++tcount) {
         if (tcount > 0 &&
@@ -262,7 +276,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        for (int kb = 0; kb < nk; ++kb, ++it) {
+        int ti, tj;
+        if (sym) upper_tile(tile, tn, ti, tj);
+        else { ti = tile / tn; tj = tile % tn; }
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!kstage_active(args.mask_a, args.mask_b, args.mask_ld, ti, tj, kb, BK)) continue;
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
           if (!mbar_wait_bounded(&full_bar[s], ph, args.err, &abort_flag)) {
@@ -286,9 +304,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           umma_commit(&empty_bar[s]);  // stage reusable once these MMAs have read it
+          ++it;
+          ++issued;
         }
         umma_commit(&acc_full_bar);  // accumulators of this tile final (also on abort)
       }
+      if (args.kcount != nullptr) atomicAdd(args.kcount, issued);
     }
   } else {
     // ---------------- epilogue (warps 2..9) ----------------
@@ -482,6 +503,8 @@ int build_pairs(int nslice, int max_order, SlicedGemmArgs* a) {
   return np;
 }
 
+int sliced_gemm_bk(int nslice) { return (nslice >= 4) ? 32 : 64; }
+
 cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& B, const Precision& prec,
                         SlicedGemmArgs args, cudaStream_t stream) {
   const int nslice = prec.nslice;
@@ -510,7 +533,7 @@ cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& B, const Precision& p
   // its line count (~1.5 cycles per line) as much as with its bytes, so longer lines beat a
   // deeper ring (measured: 3 slices with BK = 64 and 2 stages run 13-17% faster than with
   // BK = 32 and 4 stages).  Four slices need BK = 32 to fit two or more stages.
-  const int bk = (nslice >= 4) ? 32 : 64;
+  const int bk = sliced_gemm_bk(nslice);
   CUtensorMap ta, tb;
   if (!make_slice_map(&ta, A, bk, nslice) || !make_slice_map(&tb, B, bk, nslice))
     return cudaErrorInvalidValue;

@@ -33,6 +33,9 @@ struct gdm_handle {
   cudaStream_t own_stream = nullptr, stream = nullptr;
   gdm_precision prec = GDM_PREC_MIXED;
   int purify = 0;  // gdm_purification
+  double trunc_tau = 0.0;          // threshold filtering of the purification (0: off)
+  double kstages_dense = 0.0;      // k stages the masked products would issue without masks
+  double kstages_issued = 0.0;     // ... and issued (read back after a solve)
   gdm::Precision phase[4] = {{2, 1, 12}, {4, 3, 9}, {4, 3, 9}, {3, 3, 12}};
   double idem_tol = 1e-13, trace_tol = 1e-6;
   bool trace_correct = true;

@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 import oracle
 from oracle import steps
 from workloads import (make_config0, make_random_small, make_spectrum_problem, make_config2,
-                       make_request_problem, make_geometry_step)
+                       make_request_problem, make_geometry_step, make_banded)
 
 pytestmark = pytest.mark.gpu
 
@@ -321,3 +321,76 @@ def test_purification_method_argument_checked(g):
     with g.Handle(64, 10) as h:
         assert g.gdm_set_purification(h._h, 7) == g.GDM_ERR_ARG
         assert g.gdm_set_purification(h._h, g.GDM_PURIFY_CANONICAL) == g.GDM_OK
+
+
+# ------------------------------------------------------------------------------------------
+# Truncated (threshold-filtered) purification, the sparse regime of Sec. 2.2.2
+# ------------------------------------------------------------------------------------------
+
+def _trunc_solve(g, p, tau):
+    with g.Handle(p.n, p.n_occ) as h:
+        h.set_truncation(tau)
+        h.set_overlap(p.S)
+        h.set_hamiltonian(p.H)
+        return h.solve()
+
+
+def test_truncation_below_every_element_matches_dense(g):
+    # a threshold below every element filters nothing and skips no k block; the filtered route
+    # computes X^2 W as a full product and symmetrises it (instead of mirroring the upper
+    # triangle), so the two agree to the products' rounding
+    p = make_banded(11, 512, 128, s_amp=0.0)
+    P0, e0, i0, _ = _trunc_solve(g, p, 0.0)
+    P1, e1, i1, _ = _trunc_solve(g, p, 1e-300)
+    assert i0["kstage_fraction"] == 1.0
+    assert i1["kstage_fraction"] == 1.0
+    assert rel(P1, P0) <= 1e-8
+    assert i0["purif_iters"] == i1["purif_iters"]
+
+
+@pytest.mark.parametrize("tau", [1e-7, 1e-5])
+def test_truncated_purification_matches_oracle_route(g, tau):
+    # orthogonal basis (S = I, so the route's Z is exactly I and both sides filter the same
+    # matrices); local H with 128 x 128 tiles that vanish
+    p = make_banded(12, 1024, 256, s_amp=0.0)
+    Q = p.factors["Q"]
+    P_exact = Q[:, :p.n_occ] @ Q[:, :p.n_occ].T
+    # the same fixed number of filtered steps on both sides (before the idempotency floor, where
+    # the stopping decision is sensitive to rounding).  At tau = 1e-5 the route is smooth in its
+    # input (a 1e-10 perturbation moves the 9th iterate by ~1e-9, measured on the oracle); at
+    # tau = 1e-7 elements near the threshold flip under 1e-12 perturbations (~6e-8 at 1e-12,
+    # ~6e-7 at 1e-10), so the bound there allows the flips of the GPU's rounding
+    K = 9
+    bound_k = {1e-7: 2e-6, 1e-5: 1e-7}[tau]
+    with g.Handle(p.n, p.n_occ) as h:
+        h.set_truncation(tau)
+        h.set_max_iter(0, K)
+        h.set_overlap(p.S)
+        h.set_hamiltonian(p.H)
+        PK, _, infoK, stK = h.solve()
+    assert stK == g.GDM_ERR_NOT_CONVERGED and infoK["purif_iters"] == K
+    XK, itK = steps.trs4_purify_truncated(p.H, p.n_occ, tau, max_iter=K)
+    assert itK == K - 1
+    assert rel(PK, XK) <= bound_k, rel(PK, XK)
+    # the whole solve: both stop at the filtered idempotency floor, possibly one step apart
+    P, e, info, st = _trunc_solve(g, p, tau)
+    assert st == g.GDM_OK, info
+    X, _ = steps.trs4_purify_truncated(p.H, p.n_occ, tau)
+    err_oracle = rel(X, P_exact)
+    assert rel(P, X) <= 0.25 * err_oracle, (rel(P, X), err_oracle)
+    assert rel(P, P_exact) <= 1.5 * err_oracle + 1e-6
+    assert info["trace_err"] <= TRACE
+    # the filtered products skipped part of their k blocks (at n = 1024 only a few tiles of the
+    # iterates vanish at 1e-7, a quarter of the density matrix's at 1e-5)
+    assert info["kstage_fraction"] < {1e-7: 0.99, 1e-5: 0.9}[tau], info["kstage_fraction"]
+
+
+def test_truncated_purification_nonorthogonal_basis(g):
+    p = make_banded(13, 1024, 256, s_amp=0.3)
+    P, e, info, st = _trunc_solve(g, p, 1e-7)
+    Pc = steps.closed_form_dm(p.factors, p.n_occ)[0]
+    assert st == g.GDM_OK, info
+    assert rel(P, Pc) <= 1e-3
+    assert info["trace_err"] <= TRACE
+    with g.Handle(64, 10) as h:
+        assert g.gdm_set_truncation(h._h, -1.0) == g.GDM_ERR_ARG

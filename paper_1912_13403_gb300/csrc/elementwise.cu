@@ -425,7 +425,9 @@ __device__ __noinline__ uint2 add_on_diagonal_words(uint2 w, double c) {
   return make_uint2(static_cast<unsigned>(__double2loint(v)), static_cast<unsigned>(__double2hiint(v)));
 }
 
-// a x + b x2 on word pairs (FP64: the general forming step).
+// a x + b x2 on word pairs, the general forming step (two FP64 operations per element; a
+// double-float version of it measured 4x slower: its integer reassembly of the FP64 bits costs
+// more issue slots than GB300's FP64 pipe).
 __device__ __forceinline__ uint2 axpby_words(double a, uint2 x, double b, uint2 x2, bool with_x2) {
   double v = a * __hiloint2double(static_cast<int>(x.y), static_cast<int>(x.x));
   if (with_x2) v = fma(b, __hiloint2double(static_cast<int>(x2.y), static_cast<int>(x2.x)), v);
@@ -450,6 +452,62 @@ __device__ __forceinline__ bool filter_words(unsigned& whi, unsigned& wlo,
   return keep && mag != 0ull;
 }
 
+// One pair of columns (2p, 2p+1) of row `row`, on integer registers (uint4 = {lo0, hi0, lo1,
+// hi1}): form y from x (and x2) by MODE, add c on the diagonal element out of line, filter it
+// (truncation), write it to yr (if given) and return it in y, accumulate the FP32 norm from the
+// truncated values and, for DOT != kDotNone, the double-float row dot product.  Returns whether
+// the pair keeps a non-zero element (only meaningful with truncation).
+template <int MODE, int DOT>
+__device__ __forceinline__ bool form_pair(int p, int row, uint4 x, uint4 x2, bool with_x2,
+                                          double a, double b, int ak, bool aneg, bool has_c,
+                                          double c, const TruncArgs& tr, uint4* yr, uint4& y,
+                                          float& ss, DF& acc) {
+  y = x;
+  if (MODE == kFormPow2) {
+    pow2_words(y.y, y.x, ak, aneg);
+    pow2_words(y.w, y.z, ak, aneg);
+  } else if (MODE == kFormGeneral) {
+    const uint2 y0 = axpby_words(a, make_uint2(x.x, x.y), b, make_uint2(x2.x, x2.y), with_x2);
+    const uint2 y1 = axpby_words(a, make_uint2(x.z, x.w), b, make_uint2(x2.z, x2.w), with_x2);
+    y = make_uint4(y0.x, y0.y, y1.x, y1.y);
+  }
+  if (has_c && (2 * p == row || 2 * p + 1 == row)) {
+    if (2 * p == row) {
+      const uint2 d = add_on_diagonal_words(make_uint2(y.x, y.y), c);
+      y.x = d.x;
+      y.y = d.y;
+    } else {
+      const uint2 d = add_on_diagonal_words(make_uint2(y.z, y.w), c);
+      y.z = d.x;
+      y.w = d.y;
+    }
+  }
+  bool nz = false;
+  if (tr.tau_bits != 0ull) {
+    const bool k0 = filter_words(y.y, y.x, tr.tau_bits);
+    const bool k1 = filter_words(y.w, y.z, tr.tau_bits);
+    nz = k0 || k1;
+  }
+  if (yr != nullptr) yr[p] = y;
+  float h0, l0, h1, l1;
+  split_words(y.y, y.x, h0, l0);
+  split_words(y.w, y.z, h1, l1);
+  ss = fmaf(h0, h0, fmaf(h1, h1, ss));  // the truncated value bounds |y| from below by 2^-23
+  if (DOT != kDotNone) {
+    float ph0 = h0, pl0 = l0, ph1 = h1, pl1 = l1;
+    if (DOT == kDotX2) {
+      split_words(x2.y, x2.x, ph0, pl0);
+      split_words(x2.w, x2.z, ph1, pl1);
+    } else if (DOT == kDotX) {
+      split_words(x.y, x.x, ph0, pl0);
+      split_words(x.w, x.z, ph1, pl1);
+    }
+    acc = df_fma(acc, h0, l0, ph0, pl0);
+    acc = df_fma(acc, h1, l1, ph1, pl1);
+  }
+  return nz;
+}
+
 template <int MODE, int DOT>
 __device__ __forceinline__ void form_norm_row(const uint4* __restrict__ xr,
                                               const uint4* __restrict__ x2r, uint4* yr,
@@ -459,52 +517,10 @@ __device__ __forceinline__ void form_norm_row(const uint4* __restrict__ xr,
   constexpr bool kNeedX2 = (MODE == kFormGeneral) || (DOT == kDotX2);
   const bool with_x2 = x2r != nullptr;
   const bool trunc = tr.tau_bits != 0ull;
-  // returns whether the pair keeps a non-zero element (only meaningful with truncation)
   auto one = [&](int p, uint4 x, uint4 x2) -> bool {
-    uint4 y = x;
-    if (MODE == kFormPow2) {
-      pow2_words(y.y, y.x, ak, aneg);
-      pow2_words(y.w, y.z, ak, aneg);
-    } else if (MODE == kFormGeneral) {
-      const uint2 y0 = axpby_words(a, make_uint2(x.x, x.y), b, make_uint2(x2.x, x2.y), with_x2);
-      const uint2 y1 = axpby_words(a, make_uint2(x.z, x.w), b, make_uint2(x2.z, x2.w), with_x2);
-      y = make_uint4(y0.x, y0.y, y1.x, y1.y);
-    }
-    if (has_c && (2 * p == row || 2 * p + 1 == row)) {
-      if (2 * p == row) {
-        const uint2 d = add_on_diagonal_words(make_uint2(y.x, y.y), c);
-        y.x = d.x;
-        y.y = d.y;
-      } else {
-        const uint2 d = add_on_diagonal_words(make_uint2(y.z, y.w), c);
-        y.z = d.x;
-        y.w = d.y;
-      }
-    }
-    bool nz = false;
-    if (trunc) {
-      const bool k0 = filter_words(y.y, y.x, tr.tau_bits);
-      const bool k1 = filter_words(y.w, y.z, tr.tau_bits);
-      nz = k0 || k1;
-    }
-    if (yr != nullptr) yr[p] = y;
-    float h0, l0, h1, l1;
-    split_words(y.y, y.x, h0, l0);
-    split_words(y.w, y.z, h1, l1);
-    ss = fmaf(h0, h0, fmaf(h1, h1, ss));  // the truncated value bounds |y| from below by 2^-23
-    if (DOT != kDotNone) {
-      float ph0 = h0, pl0 = l0, ph1 = h1, pl1 = l1;
-      if (DOT == kDotX2) {
-        split_words(x2.y, x2.x, ph0, pl0);
-        split_words(x2.w, x2.z, ph1, pl1);
-      } else if (DOT == kDotX) {
-        split_words(x.y, x.x, ph0, pl0);
-        split_words(x.w, x.z, ph1, pl1);
-      }
-      acc = df_fma(acc, h0, l0, ph0, pl0);
-      acc = df_fma(acc, h1, l1, ph1, pl1);
-    }
-    return nz;
+    uint4 y;
+    return form_pair<MODE, DOT>(p, row, x, x2, with_x2, a, b, ak, aneg, has_c, c, tr, yr, y, ss,
+                                acc);
   };
   // Warp-uniform loops: full blocks of 32 * U column pairs (U loads in flight per lane), then
   // steps of 32 pairs.  A block of 64 pairs is one 128-column tile.
@@ -673,6 +689,303 @@ __global__ void __launch_bounds__(kSliceThreads)
     for (int s = 0; s < 4; ++s)
       if (s < nslice) orow[s * plane2 + p] = half_pair(d0[s], d1[s]);
   }
+}
+
+// Forming and slicing in one pass, one block per row: every thread loads its kFusedPPT column
+// pairs at once (the whole row is in flight in one round trip), forms them in registers, writes
+// Y, reduces the FP32 norm (and the row dot product) over the block in a fixed order, and
+// writes the slices from the same registers, so the formed row is never read back.
+constexpr int kFusedPPT = 8;
+static_assert(kFusedMaxCols == 2 * 512 * kFusedPPT, "fused slicing: up to 512 threads per row");
+
+template <int MODE, int DOT, int THREADS, bool HAS_X2>
+__device__ __forceinline__ void form_slice_row(const uint4* xr, const uint4* x2r, uint4* yr,
+                                               int npairs, int row, double a, double b, int ak,
+                                               bool aneg, bool has_c, double c,
+                                               const TruncArgs& tr, __half* out, int64_t out_ld,
+                                               int64_t plane, int nslice, int bits,
+                                               double* out_scale, double* row_dot, float* red_ss,
+                                               DF* red_dot, int* shift_sh) {
+  constexpr bool kNeedX2 = HAS_X2 && ((MODE == kFormGeneral) || (DOT == kDotX2));
+  const bool with_x2 = HAS_X2;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint4 v[kFusedPPT], v2[kNeedX2 ? kFusedPPT : 1];
+#pragma unroll
+  for (int i = 0; i < kFusedPPT; ++i) {
+    const int p = i * THREADS + threadIdx.x;
+    v[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (p < npairs) v[i] = xr[p];
+    if (kNeedX2) {
+      v2[i] = make_uint4(0u, 0u, 0u, 0u);
+      if (p < npairs) v2[i] = x2r[p];
+    }
+  }
+  uint32_t* mrow = (tr.tau_bits != 0ull && tr.mask != nullptr)
+                       ? tr.mask + static_cast<int64_t>(row >> 7) * tr.mask_ld : nullptr;
+  float ss = 0.0f;
+  DF acc{0.0f, 0.0f};
+#pragma unroll
+  for (int i = 0; i < kFusedPPT; ++i) {
+    const int p0 = i * THREADS + w * 32;  // warp-uniform: the warp's first pair
+    if (p0 < npairs) {
+      const int p = p0 + lane;
+      bool nz = false;
+      if (p < npairs) {
+        uint4 y;
+        nz = form_pair<MODE, DOT>(p, row, v[i], kNeedX2 ? v2[i] : v[i], with_x2, a, b, ak, aneg,
+                                  has_c, c, tr, yr, y, ss, acc);
+        v[i] = y;
+      }
+      if (mrow != nullptr) {
+        // 32 pairs = half a 128-column tile
+        const bool any = __any_sync(0xffffffffu, nz);
+        if (lane == 0 && any) mrow[p0 >> 6] = 1u;
+      }
+    }
+  }
+  // block reductions in a fixed order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (DOT != kDotNone) acc = df_warp_sum(acc);
+  if (lane == 0) {
+    red_ss[w] = ss;
+    if (DOT != kDotNone) red_dot[w] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    DF d{0.0f, 0.0f};
+    for (int j = 0; j < THREADS / 32; ++j) {
+      t += red_ss[j];
+      if (DOT != kDotNone) d = df_add(d, red_dot[j]);
+    }
+    if (DOT != kDotNone) row_dot[row] = df_to_double(d);
+    int e = 0;
+    unsigned long long scb;
+    if (t > 0.0f && isfinite(t)) {
+      // the norm from truncated values is low by at most 2^-23 relative: the 0.2% margin covers
+      // it and the FP32 accumulation, so 2^e > ||y||
+      frexpf(sqrtf(t * 1.002f) * 1.0001f, &e);
+      scb = static_cast<unsigned long long>(e + 1023) << 52;  // 2^e
+    } else {
+      scb = isfinite(t) ? (1023ull << 52) : 0x7FF8000000000000ull;  // 1, or NaN for NaN / Inf
+    }
+    out_scale[row] = __longlong_as_double(static_cast<long long>(scb));
+    // digits of round(y 2^(11 - e + bits (nslice - 1))); a NaN row gets all-zero slices
+    shift_sh[0] = (scb >> 52 == 0x7FF) ? -100000 : 11 - e + bits * (nslice - 1);
+  }
+  __syncthreads();
+  const int p2 = shift_sh[0];
+  uint32_t* orow = reinterpret_cast<uint32_t*>(out + row * out_ld);
+  const int64_t plane2 = plane >> 1;
+#pragma unroll
+  for (int i = 0; i < kFusedPPT; ++i) {
+    const int p = i * THREADS + threadIdx.x;
+    if (p < npairs) {
+      int d0[4] = {0, 0, 0, 0}, d1[4] = {0, 0, 0, 0};
+      if (p2 > -1000) {
+        slice_digits(static_cast<long long>((static_cast<unsigned long long>(v[i].y) << 32) | v[i].x),
+                     p2, nslice, bits, d0);
+        slice_digits(static_cast<long long>((static_cast<unsigned long long>(v[i].w) << 32) | v[i].z),
+                     p2, nslice, bits, d1);
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        if (s < nslice) orow[s * plane2 + p] = half_pair(d0[s], d1[s]);
+    }
+  }
+}
+
+template <int MODE, int THREADS, bool HAS_X2>
+__device__ __forceinline__ void form_slice_dispatch(int dot, const uint4* xr, const uint4* x2r,
+                                                    uint4* yr, int npairs, int row, double a,
+                                                    double b, int ak, bool aneg, bool has_c,
+                                                    double c, const TruncArgs& tr, __half* out,
+                                                    int64_t out_ld, int64_t plane, int nslice,
+                                                    int bits, double* out_scale,
+                                                    double* row_dot, float* red_ss, DF* red_dot,
+                                                    int* shift_sh) {
+#define GDM_FSR(D)                                                                              \
+  form_slice_row<MODE, D, THREADS, HAS_X2>(xr, x2r, yr, npairs, row, a, b, ak, aneg, has_c, c, tr, out, \
+                                   out_ld, plane, nslice, bits, out_scale, row_dot, red_ss,     \
+                                   red_dot, shift_sh)
+  switch (dot) {
+    case kDotSelf: GDM_FSR(kDotSelf); break;
+    case kDotX2: GDM_FSR(kDotX2); break;
+    case kDotX: GDM_FSR(kDotX); break;
+    default: GDM_FSR(kDotNone);
+  }
+#undef GDM_FSR
+}
+
+template <int THREADS, bool HAS_X2>
+__global__ void __launch_bounds__(THREADS)
+    form_slice_fused_kernel(const double* X, int64_t ldx, const double* X2, int64_t ldx2,
+                            int rows, int cols, const double* __restrict__ coef_dev, double ha,
+                            double hb, double hc, double* Y, int64_t ldy, __half* out,
+                            double* out_scale, int64_t out_ld, int64_t plane, int nslice,
+                            int bits, const int* skip, int dot, double* row_dot, TruncArgs tr) {
+  __shared__ float red_ss[THREADS / 32];
+  __shared__ DF red_dot[THREADS / 32];
+  __shared__ int shift_sh[1];
+  if (skip != nullptr && *skip != 0) return;
+  const int row = blockIdx.x;
+  if (row >= rows) return;
+  double a = ha, b = hb, c = hc;
+  if (coef_dev != nullptr) {
+    a = coef_dev[0];
+    b = coef_dev[1];
+    c = coef_dev[2];
+  }
+  // the forming arithmetic, decided once per block (uniform)
+  int ak = 0;
+  bool aneg = false;
+  const bool no_x2 = (!HAS_X2 || b == 0.0);
+  const bool has_c = (c != 0.0);
+  int mode = kFormGeneral;
+  if (no_x2 && a == 1.0) mode = kFormPlain;
+  else if (no_x2 && pow2_coef(a, ak, aneg)) mode = kFormPow2;
+  const uint4* xr = reinterpret_cast<const uint4*>(X + row * ldx);
+  const uint4* x2r = HAS_X2 ? reinterpret_cast<const uint4*>(X2 + row * ldx2) : nullptr;
+  uint4* yr = (Y != nullptr) ? reinterpret_cast<uint4*>(Y + row * ldy) : nullptr;
+  const int npairs = cols >> 1;
+  if (mode == kFormPlain)
+    form_slice_dispatch<kFormPlain, THREADS, HAS_X2>(dot, xr, x2r, yr, npairs, row, a, b, ak, aneg, has_c,
+                                             c, tr, out, out_ld, plane, nslice, bits, out_scale,
+                                             row_dot, red_ss, red_dot, shift_sh);
+  else if (mode == kFormPow2)
+    form_slice_dispatch<kFormPow2, THREADS, HAS_X2>(dot, xr, x2r, yr, npairs, row, a, b, ak, aneg, has_c,
+                                            c, tr, out, out_ld, plane, nslice, bits, out_scale,
+                                            row_dot, red_ss, red_dot, shift_sh);
+  else
+    form_slice_dispatch<kFormGeneral, THREADS, HAS_X2>(dot, xr, x2r, yr, npairs, row, a, b, ak, aneg,
+                                               has_c, c, tr, out, out_ld, plane, nslice, bits,
+                                               out_scale, row_dot, red_ss, red_dot, shift_sh);
+}
+
+// The TRS4 trace terms and the slicing of X^2 in one pass, one block per row: X^2's row is
+// sliced like form_slice_row (plain forming, no row dot), and the row's trace terms go to
+// partials[row * kTraceTerms + k]: X_rr, X2_rr, <X2_r, X_r>, ||X2_r||^2, ||X_r||^2 (double-float
+// sums, diagonals exact).  Both rows are read once.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+    slice_traces_kernel(const double* X2, const double* X, int64_t ld, int n, __half* out,
+                        double* out_scale, int64_t out_ld, int64_t plane, int nslice, int bits,
+                        double* partials, const int* skip) {
+  __shared__ float red_ss[THREADS / 32];
+  __shared__ DF red_dot[3][THREADS / 32];
+  __shared__ unsigned long long diag_sh[2];
+  __shared__ int shift_sh;
+  if (skip != nullptr && *skip != 0) return;
+  const int row = blockIdx.x;
+  if (row >= n) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int npairs = n >> 1;
+  const uint4* yr = reinterpret_cast<const uint4*>(X2 + row * ld);
+  const uint4* xr = reinterpret_cast<const uint4*>(X + row * ld);
+  uint4 v[kFusedPPT], x[kFusedPPT];
+#pragma unroll
+  for (int i = 0; i < kFusedPPT; ++i) {
+    const int p = i * THREADS + threadIdx.x;
+    v[i] = make_uint4(0u, 0u, 0u, 0u);
+    x[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (p < npairs) {
+      v[i] = yr[p];
+      x[i] = xr[p];
+    }
+  }
+  float ss = 0.0f;
+  DF a3{0.0f, 0.0f}, a4{0.0f, 0.0f}, a5{0.0f, 0.0f};
+#pragma unroll
+  for (int i = 0; i < kFusedPPT; ++i) {
+    const int p = i * THREADS + threadIdx.x;
+    if (p < npairs) {
+      if (2 * p == row || 2 * p + 1 == row) {  // the diagonal elements, bit for bit
+        const bool lo = (2 * p == row);
+        diag_sh[0] = lo ? ((static_cast<unsigned long long>(x[i].y) << 32) | x[i].x)
+                        : ((static_cast<unsigned long long>(x[i].w) << 32) | x[i].z);
+        diag_sh[1] = lo ? ((static_cast<unsigned long long>(v[i].y) << 32) | v[i].x)
+                        : ((static_cast<unsigned long long>(v[i].w) << 32) | v[i].z);
+      }
+      float h0, l0, h1, l1, g0, k0, g1, k1;
+      split_words(v[i].y, v[i].x, h0, l0);
+      split_words(v[i].w, v[i].z, h1, l1);
+      split_words(x[i].y, x[i].x, g0, k0);
+      split_words(x[i].w, x[i].z, g1, k1);
+      ss = fmaf(h0, h0, fmaf(h1, h1, ss));
+      a3 = df_fma(df_fma(a3, h0, l0, g0, k0), h1, l1, g1, k1);
+      a4 = df_fma(df_fma(a4, h0, l0, h0, l0), h1, l1, h1, l1);
+      a5 = df_fma(df_fma(a5, g0, k0, g0, k0), g1, k1, g1, k1);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  a3 = df_warp_sum(a3);
+  a4 = df_warp_sum(a4);
+  a5 = df_warp_sum(a5);
+  if (lane == 0) {
+    red_ss[w] = ss;
+    red_dot[0][w] = a3;
+    red_dot[1][w] = a4;
+    red_dot[2][w] = a5;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    DF d3{0.0f, 0.0f}, d4{0.0f, 0.0f}, d5{0.0f, 0.0f};
+    for (int j = 0; j < THREADS / 32; ++j) {
+      t += red_ss[j];
+      d3 = df_add(d3, red_dot[0][j]);
+      d4 = df_add(d4, red_dot[1][j]);
+      d5 = df_add(d5, red_dot[2][j]);
+    }
+    double* pr = partials + static_cast<int64_t>(row) * kTraceTerms;
+    pr[0] = __longlong_as_double(static_cast<long long>(diag_sh[0]));
+    pr[1] = __longlong_as_double(static_cast<long long>(diag_sh[1]));
+    pr[2] = df_to_double(d3);
+    pr[3] = df_to_double(d4);
+    pr[4] = df_to_double(d5);
+    int e = 0;
+    unsigned long long scb;
+    if (t > 0.0f && isfinite(t)) {
+      frexpf(sqrtf(t * 1.002f) * 1.0001f, &e);  // 2^e > ||y|| (see form_slice_row)
+      scb = static_cast<unsigned long long>(e + 1023) << 52;
+    } else {
+      scb = isfinite(t) ? (1023ull << 52) : 0x7FF8000000000000ull;
+    }
+    out_scale[row] = __longlong_as_double(static_cast<long long>(scb));
+    shift_sh = (scb >> 52 == 0x7FF) ? -100000 : 11 - e + bits * (nslice - 1);
+  }
+  __syncthreads();
+  const int p2 = shift_sh;
+  uint32_t* orow = reinterpret_cast<uint32_t*>(out + row * out_ld);
+  const int64_t plane2 = plane >> 1;
+#pragma unroll
+  for (int i = 0; i < kFusedPPT; ++i) {
+    const int p = i * THREADS + threadIdx.x;
+    if (p < npairs) {
+      int d0[4] = {0, 0, 0, 0}, d1[4] = {0, 0, 0, 0};
+      if (p2 > -1000) {
+        slice_digits(static_cast<long long>((static_cast<unsigned long long>(v[i].y) << 32) | v[i].x),
+                     p2, nslice, bits, d0);
+        slice_digits(static_cast<long long>((static_cast<unsigned long long>(v[i].w) << 32) | v[i].z),
+                     p2, nslice, bits, d1);
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        if (s < nslice) orow[s * plane2 + p] = half_pair(d0[s], d1[s]);
+    }
+  }
+}
+
+// Row dot products of W = a X + b X^2 + c I with X^2 from the per-row trace terms of
+// slice_traces_kernel: <W_i, X2_i> = a <X_i, X2_i> + b ||X2_i||^2 + c (X2)_ii.
+__global__ void w_row_dots_kernel(const double* __restrict__ partials, int n,
+                                  const double* __restrict__ coef, double* row_dot) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double* p = partials + static_cast<int64_t>(i) * kTraceTerms;
+  row_dot[i] = coef[0] * p[2] + coef[1] * p[3] + coef[2] * p[1];
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1309,7 +1622,33 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
   const bool host_plain = (coef_dev == nullptr) && ha == 1.0 && (X2 == nullptr || hb == 0.0) &&
                           hc == 0.0;
   if (tr.tau_bits != 0ull && !aligned) return cudaErrorInvalidValue;  // filtering: two passes
-  if (aligned && (host_plain || Y != nullptr || od == nullptr)) {
+  const int npairs = cols / 2;
+  if (aligned && od != nullptr && cols <= kFusedMaxCols) {
+    // one pass: form, norm, slices (the row stays in registers)
+    const bool with_dot = dot != kDotNone && out->row_dot != nullptr;
+    const int d = with_dot ? dot : kDotNone;
+    double* rd = with_dot ? out->row_dot : nullptr;
+    count_launch();
+#define GDM_FUSED(T)                                                                             \
+  if (X2 != nullptr)                                                                             \
+    form_slice_fused_kernel<T, true><<<rows, T, 0, stream>>>(                                    \
+        X, ldx, X2, ldx2, rows, cols, coef_dev, ha, hb, hc, Y, ldy, od, osc, old, plane, nslice, \
+        bits, skip, d, rd, tr);                                                                  \
+  else                                                                                           \
+    form_slice_fused_kernel<T, false><<<rows, T, 0, stream>>>(                                   \
+        X, ldx, X2, ldx2, rows, cols, coef_dev, ha, hb, hc, Y, ldy, od, osc, old, plane, nslice, \
+        bits, skip, d, rd, tr)
+    if (npairs <= 128 * kFusedPPT) {
+      GDM_FUSED(128);
+    } else if (npairs <= 256 * kFusedPPT) {
+      GDM_FUSED(256);
+    } else {
+      GDM_FUSED(512);
+    }
+#undef GDM_FUSED
+    if (with_dot)
+      out->dot_partner = (dot == kDotX2) ? X2 : (dot == kDotX ? X : (Y != nullptr ? Y : X));
+  } else if (aligned && (host_plain || Y != nullptr || od == nullptr)) {
     // two passes: rows (form + norm) then elements (slices), both fully parallel
     const int nb = (rows + kRowsPerBlock - 1) / kRowsPerBlock;
     const bool with_dot = dot != kDotNone && od != nullptr && out->row_dot != nullptr;
@@ -1384,6 +1723,53 @@ cudaError_t trs4_traces(const double* X, const double* X2, int64_t ld, int n, do
   trs4_traces_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(X, X2, ld, n, partials);
   *nblocks = nb;
   return cudaGetLastError();
+}
+
+cudaError_t slice_traces(const double* X2, const double* X, int64_t ld, int n, SliceBuf* out,
+                         int nslice, int bits, double* partials, int* nrows, cudaStream_t stream) {
+  *nrows = 0;
+  if (n <= 0) return cudaSuccess;
+  if (!slice_traces_fits(X2, X, ld, n, out, nslice)) return cudaErrorInvalidValue;
+  out->mask_valid = false;
+  out->rows = n;
+  out->cols = n;
+  out->nslice_valid = nslice;
+  out->bits = bits;
+  out->dot_partner = nullptr;
+  const int64_t plane = static_cast<int64_t>(out->ld) * out->rows_alloc;
+  const int npairs = n / 2;
+  count_launch();
+  if (npairs <= 128 * kFusedPPT)
+    slice_traces_kernel<128><<<n, 128, 0, stream>>>(X2, X, ld, n, out->data, out->row_scale,
+                                                   out->ld, plane, nslice, bits, partials,
+                                                   nullptr);
+  else if (npairs <= 256 * kFusedPPT)
+    slice_traces_kernel<256><<<n, 256, 0, stream>>>(X2, X, ld, n, out->data, out->row_scale,
+                                                   out->ld, plane, nslice, bits, partials,
+                                                   nullptr);
+  else
+    slice_traces_kernel<512><<<n, 512, 0, stream>>>(X2, X, ld, n, out->data, out->row_scale,
+                                                   out->ld, plane, nslice, bits, partials,
+                                                   nullptr);
+  *nrows = n;
+  return cudaGetLastError();
+}
+
+cudaError_t w_row_dots(const double* partials, int n, const double* coef_dev, SliceBuf* w,
+                       const double* X2, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  w_row_dots_kernel<<<(n + 255) / 256, 256, 0, stream>>>(partials, n, coef_dev, w->row_dot);
+  w->dot_partner = X2;
+  return cudaGetLastError();
+}
+
+bool slice_traces_fits(const double* X2, const double* X, int64_t ld, int n, const SliceBuf* out,
+                       int nslice) {
+  return out != nullptr && nslice >= 1 && nslice <= 4 && n % 2 == 0 && ld % 2 == 0 &&
+         n <= kFusedMaxCols && out->ld >= n && out->rows_alloc >= n && out->ld % 2 == 0 &&
+         ((reinterpret_cast<uintptr_t>(X2) | reinterpret_cast<uintptr_t>(X)) & 15) == 0 &&
+         (reinterpret_cast<uintptr_t>(out->data) & 3) == 0;
 }
 
 cudaError_t dot_partials(const double* A, int64_t lda, const double* B, int64_t ldb, int rows,

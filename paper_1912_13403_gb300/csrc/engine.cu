@@ -13,6 +13,7 @@
 //   4. TRS4 purification X <- f(X)                           (Eq. ntpoly_purification; Table 1)
 //   5. P = Z X Z^T, Tr(P S), Tr(P H)                          (Sec. 4, back-transform)
 // Products run through the sliced tensor-core kernel (mixed precision) or the FP64 kernel.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstddef>
@@ -109,6 +110,13 @@ void collect_profile(gdm_handle* h) {
   h->prof_pending.clear();
 }
 
+// The device error word and the split-k counters (an aborted launch can leave a counter set).
+cudaError_t clear_device_flags(gdm_handle* h, cudaStream_t s) {
+  return cudaMemsetAsync(h->err_dev, 0,
+                         sizeof(uint32_t) * (1 + static_cast<size_t>(kSplitTiles) * kEpilogueWarps),
+                         s);
+}
+
 // Tensor-pipe work of one sliced launch: slice pairs x computed tile area x 2 K
 double sliced_flops(const gdm_handle* h, int ph, bool sym) {
   const double n = static_cast<double>(h->n);
@@ -141,6 +149,10 @@ cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const dou
     a.diag = diag;
     a.coef = coef;
     a.err = h->err_dev;
+    a.splitk_ws = h->split_ws;
+    a.splitk_cnt = h->split_cnt;
+    a.splitk_slots = h->split_slots;
+    a.splitk_tiles = kSplitTiles;
     // truncated purification: skip the k blocks where an operand tile is empty
     if (ph == GDM_PHASE_PURIFY && h->trunc_tau > 0.0 && A.sl->mask_valid && Bt.sl->mask_valid) {
       a.mask_a = A.sl->tile_mask;
@@ -368,7 +380,7 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
   Op zc = {Zc, &h->sl[SL_Z]};
   Op zct = zc;
   const int nref = mixed(h) ? h->n_refine : 1;
-  double derr = 0.0;
+  double derr = 0.0, derr_prev = INFINITY;
   for (int r = 0; r <= nref; ++r) {
     double* T = h->f[F_T];
     double* Dl = h->f[F_U];
@@ -384,6 +396,12 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
     derr = std::sqrt(d2);
     if (!std::isfinite(derr)) return set_err(h, GDM_ERR_NONFINITE, "non-finite Z^T S Z");
     if (r == nref || derr == 0.0) break;
+    // The step is third order: ||delta'||_F <= (5/16) ||delta||_F^3.  After a step taken from
+    // ||delta||_F <= 1e-3 its remainder (<= 3.2e-10) lies below the rounding floor that the
+    // sliced products leave in Z^T S Z, so this delta is that floor and another step cannot
+    // lower it.
+    if (derr_prev <= 1e-3) break;
+    derr_prev = derr;
     CK(slice(h, Dl, &h->sl[SL_B], GDM_PHASE_REFINE, kDotSelf));
     CK(product(h, {Dl, &h->sl[SL_B]}, {Dl, &h->sl[SL_B]}, F, nullptr, Dl, 0.375, -0.5, 1.0, true,
                GDM_PHASE_REFINE, nullptr, true));                    // F = I - d/2 + 3d^2/8
@@ -421,7 +439,7 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   const int64_t ld = h->ld;
   cudaStream_t s = h->stream;
   gdm_status st;
-  CK(cudaMemsetAsync(h->err_dev, 0, sizeof(uint32_t), s));
+  CK(clear_device_flags(h, s));
   if (!h->z_valid) {
     st = compute_z(h, info);
     if (st != GDM_OK) return st;
@@ -488,10 +506,20 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   for (it = 0; it < h->max_purif; ++it) {
     CK(product(h, {X, &h->sl[SL_X]}, {X, &h->sl[SL_X]}, X2, nullptr, nullptr, 1.0, 0.0, 0.0, true,
                GDM_PHASE_PURIFY, nullptr, true));
-    // with truncation X^2 is filtered (and sliced) before its traces are taken
-    if (tr != nullptr) CK(slice(h, X2, &h->sl[SL_X2], GDM_PHASE_PURIFY, kDotNone, tr));
+    // with truncation X^2 is filtered (and sliced) before its traces are taken; without it the
+    // traces and X^2's slices come from one pass over X and X^2
     int nb = 0;
-    CK(trs4_traces(X, X2, ld, n, h->partials, &nb, s));
+    bool x2_sliced = false, row_terms = false;
+    if (tr != nullptr) {
+      CK(slice(h, X2, &h->sl[SL_X2], GDM_PHASE_PURIFY, kDotNone, tr));
+      x2_sliced = true;
+    } else if (pu_sl > 0 && slice_traces_fits(X2, X, ld, n, &h->sl[SL_X2], pu_sl)) {
+      CK(slice_traces(X2, X, ld, n, &h->sl[SL_X2], pu_sl, bits_for(h, GDM_PHASE_PURIFY),
+                      h->partials, &nb, s));
+      x2_sliced = true;
+      row_terms = true;
+    }
+    if (nb == 0) CK(trs4_traces(X, X2, ld, n, h->partials, &nb, s));
     CK(trs4_control(h->partials, nb, h->st_dev, tol_abs, s));
     CK(cudaMemcpyAsync(h->st_host, h->st_dev, sizeof(Trs4State), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -520,10 +548,18 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
       if (tr != nullptr) CK(symmetrise(Xn, ld, n, s));
       CK(slice(h, Xn, &h->sl[SL_X], GDM_PHASE_PURIFY, kDotSelf, tr));
     } else if (t.branch == 2 || t.branch == 3) {  // a product: F + gamma G, or McWeeny
-      if (tr == nullptr) CK(slice(h, X2, &h->sl[SL_X2], GDM_PHASE_PURIFY));
-      CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefW)), 0, 0, 0,
-                        W, ld, pu_sl > 0 ? &h->sl[SL_W] : nullptr, pu_sl, nullptr, s,
-                        bits_for(h, GDM_PHASE_PURIFY), kDotX2, tr));
+      if (!x2_sliced) CK(slice(h, X2, &h->sl[SL_X2], GDM_PHASE_PURIFY));
+      // W itself is needed only with filtering or FP64 products (the sliced product takes its
+      // diagonal from the row dot products with X^2)
+      const bool need_w = tr != nullptr || pu_sl == 0 || n % 2 != 0 || n > kFusedMaxCols;
+      // W's row dot products with X^2 follow from the per-row trace terms when slice_traces
+      // produced them (no filtering): a <X_i, X2_i> + b ||X2_i||^2 + c (X2)_ii
+      const bool dots_from_traces = row_terms;
+      const double* coefW = st_field(h, offsetof(Trs4State, coefW));
+      CK(form_and_slice(X, ld, X2, ld, n, n, coefW, 0, 0, 0, need_w ? W : nullptr, ld,
+                        pu_sl > 0 ? &h->sl[SL_W] : nullptr, pu_sl, nullptr, s,
+                        bits_for(h, GDM_PHASE_PURIFY), dots_from_traces ? kDotNone : kDotX2, tr));
+      if (dots_from_traces) CK(w_row_dots(h->partials, n, coefW, &h->sl[SL_W], X2, s));
       // with filtering X^2 and W no longer commute: the full product is symmetrised
       CK(product(h, {X2, &h->sl[SL_X2]}, {W, &h->sl[SL_W]}, Xn, nullptr, nullptr, 1.0, 0.0, 0.0,
                  tr == nullptr, GDM_PHASE_PURIFY, nullptr, true));
@@ -647,7 +683,8 @@ namespace {
 
 // Byte layout of a handle's single device allocation for capacity n.
 struct PoolLayout {
-  size_t fbytes, sdata, sscale, pbytes, small_bytes, st_bytes, total;
+  size_t fbytes, sdata, sscale, pbytes, small_bytes, st_bytes, flag_bytes, split_slots,
+      split_bytes, total;
   explicit PoolLayout(int64_t n) {
     auto up = [](size_t x) { return (x + 1023) / 1024 * 1024; };
     const size_t ld = static_cast<size_t>((n + 63) / 64 * 64);
@@ -657,11 +694,16 @@ struct PoolLayout {
     sdata = up(sizeof(__half) * 4 * ld * rows_alloc);
     // row scales, row dot products, then the 128 x 128 tile occupancy words
     sscale = up(2 * sizeof(double) * rows_alloc + sizeof(uint32_t) * tiles * tiles);
-    pbytes = up(sizeof(double) * (kTraceTerms * static_cast<size_t>((n + 7) / 8) + 64));
+    pbytes = up(sizeof(double) * (kTraceTerms * static_cast<size_t>(n) + 64));
     small_bytes = up(sizeof(double) * kSmall);
     st_bytes = up(sizeof(Trs4State));
+    // the device error word, then the split-k counters
+    flag_bytes = up(sizeof(uint32_t) * (1 + static_cast<size_t>(kSplitTiles) * kEpilogueWarps));
+    // split-k partial sums: a part per SM at most, and never more than 4 per tile
+    split_slots = std::min<size_t>(kSplitTiles, 4 * tiles * tiles);
+    split_bytes = up(sizeof(long long) * 128 * 128 * split_slots);
     total = F_COUNT * fbytes + SL_COUNT * (sdata + sscale) + pbytes + small_bytes + st_bytes +
-            up(sizeof(uint32_t));
+            flag_bytes + split_bytes;
   }
 };
 
@@ -771,6 +813,10 @@ gdm_status gdm_init(gdm_handle** out, int64_t n_basis, int64_t n_occ, int device
   h->st_dev = reinterpret_cast<Trs4State*>(p);
   p += L.st_bytes;
   h->err_dev = reinterpret_cast<uint32_t*>(p);
+  h->split_cnt = h->err_dev + 1;
+  p += L.flag_bytes;
+  h->split_ws = reinterpret_cast<long long*>(p);
+  h->split_slots = static_cast<int>(L.split_slots);
   if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMallocHost(&h->host_buf, sizeof(double) * kSmall) != cudaSuccess ||
       cudaMallocHost(&h->st_host, sizeof(Trs4State)) != cudaSuccess ||
@@ -945,7 +991,7 @@ gdm_status gdm_get_edm(gdm_handle* h, double* Q, int64_t ld, gdm_mem mem) {
   if (mem != GDM_MEM_HOST && mem != GDM_MEM_DEVICE) return set_err(h, GDM_ERR_ARG, "bad mem kind");
   CK(cudaSetDevice(h->device));
   cudaStream_t s = h->stream;
-  CK(cudaMemsetAsync(h->err_dev, 0, sizeof(uint32_t), s));
+  CK(clear_device_flags(h, s));
   // Q = P H P: T = P H (H symmetric, so it is its own transposed operand), then Q = T P^T with
   // P symmetric; both products run in the transform phase's format.
   double* P = h->f[F_XN];
@@ -978,7 +1024,7 @@ gdm_status gdm_extrapolate_dm(gdm_handle* h, const double* S_new, int64_t lds, g
   CK(cudaSetDevice(h->device));
   cudaStream_t s = h->stream;
   const int64_t ld = h->ld;
-  CK(cudaMemsetAsync(h->err_dev, 0, sizeof(uint32_t), s));
+  CK(clear_device_flags(h, s));
   // X0 = Z0^{-1} P0 Z0^{-T}, the last solve's projector in the orthogonal basis, is still in
   // F_X; keep it in F_H (the Hamiltonian belongs to the old geometry and is dropped)
   CK(cudaMemcpyAsync(h->f[F_H], h->f[F_X], sizeof(double) * ld * h->n, cudaMemcpyDeviceToDevice,

@@ -9,6 +9,7 @@
 namespace gdm {
 
 constexpr int kMaxPairs = 16;
+constexpr int kEpilogueWarps = 8;   // split-k counters per tile (one per epilogue warp)
 
 // Error word written by kernels (never a trap): bit flags, OR-ed atomically.
 enum DeviceError : uint32_t {
@@ -54,6 +55,12 @@ struct SlicedGemmArgs {
   int num_pairs = 0, nacc = 0, tmem_cols = 0;
   int shift = 12;                     // weight of order o is 2^(-shift * o)
   int8_t pair_s[kMaxPairs] = {}, pair_t[kMaxPairs] = {}, pair_o[kMaxPairs] = {};
+  // MMA instructions per 16-wide k step (built from the pairs by build_pairs): A slice, first B
+  // slice, N = 256 over B slices t and t+1 (whose orders' accumulators are adjacent), whether
+  // it opens its accumulators
+  int num_ins = 0;
+  int8_t ins_s[kMaxPairs] = {}, ins_t[kMaxPairs] = {}, ins_wide[kMaxPairs] = {},
+         ins_open[kMaxPairs] = {};
   const double* row_scale_a = nullptr;
   const double* row_scale_b = nullptr;
   double* C = nullptr;
@@ -73,6 +80,13 @@ struct SlicedGemmArgs {
   const uint32_t* mask_b = nullptr;
   int mask_ld = 0;
   unsigned long long* kcount = nullptr;
+  // k split of the last, partial wave of tiles (sliced_gemm sets split and full_tiles when the
+  // caller provides the workspace): splitk_slots slots of 128 x 128 int64 partial sums, and
+  // kEpilogueWarps zero-initialised counters per split tile, which the kernel leaves at zero
+  int split = 1, full_tiles = 0;
+  long long* splitk_ws = nullptr;
+  uint32_t* splitk_cnt = nullptr;
+  int splitk_slots = 0, splitk_tiles = 0;
   const int* skip = nullptr;          // optional device flag: non-zero -> no-op launch
   uint32_t* err = nullptr;
   int tiles_n = 0, tiles_m = 0;
@@ -132,6 +146,10 @@ struct TruncArgs {
 
 // purification maps (the values of gdm_purification)
 enum { kPurifyTrs4 = 0, kPurifyTrs2 = 1, kPurifyCanonical = 2 };
+// Widest row (columns) that form_and_slice forms and slices in one pass (the row stays in
+// registers); wider or unaligned rows take two passes, which need Y when the forming is not
+// plain and a row dot product is asked for.
+constexpr int kFusedMaxCols = 8192;
 cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64_t ldx2,
                            int rows, int cols, const double* coef_dev, double ha, double hb,
                            double hc, double* Y, int64_t ldy, SliceBuf* out, int nslice,
@@ -154,6 +172,16 @@ cudaError_t gershgorin(const double* A, int64_t lda, int n, double* partials, do
 // Per-block partial sums over rows of: Tr X, Tr X2, <X2, X>, ||X2||^2, ||X||^2
 // (partials: kTraceTerms doubles per block, `nblocks` returned through *nblocks).
 constexpr int kTraceTerms = 5;
+// TRS4 trace terms per row (partials: n x kTraceTerms) and the slices of X2 in one pass;
+// slice_traces_fits says whether the shapes and alignments allow it.
+cudaError_t slice_traces(const double* X2, const double* X, int64_t ld, int n, SliceBuf* out,
+                         int nslice, int bits, double* partials, int* nrows, cudaStream_t stream);
+bool slice_traces_fits(const double* X2, const double* X, int64_t ld, int n, const SliceBuf* out,
+                       int nslice);
+// w->row_dot[i] = <W_i, X2_i> for W = coef[0] X + coef[1] X2 + coef[2] I, from slice_traces'
+// per-row terms (so the slicing of W needs no row dot); records X2 as w's dot partner.
+cudaError_t w_row_dots(const double* partials, int n, const double* coef_dev, SliceBuf* w,
+                       const double* X2, cudaStream_t stream);
 cudaError_t trs4_traces(const double* X, const double* X2, int64_t ld, int n, double* partials,
                         int* nblocks, cudaStream_t stream);
 

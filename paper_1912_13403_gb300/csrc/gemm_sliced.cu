@@ -19,13 +19,20 @@
 // of this route that is B itself).
 //
 // Kernel shape: persistent, one CTA per SM, each CTA walks the 128x128 output tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ...  10 warps.  Warp 0: TMA producer (a 3-D box loads all
-// slices of a 128 x BK panel at once, BK = 64 for up to 3 slices); its stage ring runs on
-// across tiles, so the next tile's operands stream in while the current tile's epilogue runs.  Warp 1: TMEM allocator and the
-// single MMA-issuing thread; it waits for the epilogue to release the accumulators before the
-// next tile.  Warps 2-9: epilogue, two warps per TMEM lane quarter (32*(warp%4) ...), each
-// covering 64 of the 128 columns.  Symmetric mode computes only tiles on or above the diagonal
-// and writes the mirror image.
+// blockIdx.x, blockIdx.x + gridDim.x, ...  The slice pairs of one 16-wide k step go out as few,
+// wide MMAs: A slice s times two adjacent B slices is one M = 128, N = 256 instruction (the two
+// B panels are adjacent in shared memory and the two orders' accumulators are adjacent in
+// TMEM), which cuts the instructions per k step (3 slices: 8 pair MMAs become 5) and the
+// shared-memory reads of A.  12 warps.  Warp 0: TMA producer (a 3-D box loads all slices of a
+// 128 x BK panel at once, BK = 64 for up to 3 slices); its stage ring runs on across tiles, so
+// the next tile's operands stream in while the current tile's epilogue runs.  Warp 1: TMEM
+// allocator and the single MMA-issuing thread.  Warps 4-11: epilogue, two warps per TMEM lane
+// quarter (32*(warp%4) ...), each covering 64 of the 128 columns; a warp reads all of its
+// accumulator columns into int64 registers first and releases TMEM, so that the conversion and
+// the stores overlap the next tile's MMAs.  Formats with at most two orders keep two
+// accumulator sets in TMEM (the MMAs never wait for the epilogue); with one set, the tiles of
+// the last, partial wave are split along k (sliced_gemm).  Symmetric mode computes only tiles
+// on or above the diagonal and writes the mirror image.
 #include <atomic>
 #include <cstdio>
 #include <mutex>
@@ -39,8 +46,19 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBN = 128;
-constexpr int kThreads = 320;
-constexpr int kEpiWarps = 8;
+// 12 warps: warpgroup 0 = TMA producer (warp 0), MMA issuer (warp 1) and two idle warps;
+// warpgroups 1-2 = the 8 epilogue warps.  Launched with 168 registers a thread, the control
+// warpgroup gives registers to the epilogue (4 x 32 x 104 + 8 x 32 x 200 = 384 x 168), which
+// then holds a whole 32 x 64 accumulator block as int64 without spilling.
+constexpr int kThreads = 384;
+constexpr int kEpiWarps = kEpilogueWarps;
+constexpr int kEpiWarp0 = 4;
+constexpr int kLaunchRegs = 168;
+constexpr int kCtrlRegs = 104;
+constexpr int kEpiRegs = 200;
+static_assert(4 * 32 * kCtrlRegs + kEpiWarps * 32 * kEpiRegs == kThreads * kLaunchRegs,
+              "register split must equal the launch allocation");
+static_assert(kLaunchRegs * kThreads <= 65536, "launch registers");
 constexpr int kStageCols = 8;  // epilogue staging: 32 rows x 8 columns per warp
 constexpr int kPairsUsed = 10;  // most slice pairs of a format (4 slices, orders 0..3)
 
@@ -84,14 +102,18 @@ __device__ __forceinline__ void upper_tile(int idx, int nt, int& ti, int& tj) {
 // Every accumulator holds an integer value: products of integer slices, summed in FP32 (exact
 // below 2^24, and FP32 values at or above 2^24 are integers too).
 
-// int64 value of an integer-valued FP32 given by its bits.
-__device__ __forceinline__ long long f32_integer(uint32_t bits) {
-  const int E = static_cast<int>((bits >> 23) & 0xFF);
-  if (E < 127) return 0;  // |v| < 1: the value is 0
-  const long long m = static_cast<long long>((bits & 0x7FFFFFu) | 0x800000u);
-  const int sh = E - 150;
-  const long long v = (sh >= 0) ? (m << sh) : (m >> (-sh));
-  return (bits >> 31) ? -v : v;
+// int64 value of an integer-valued FP32 with |v| < 2^44, in eight FP32 / integer instructions:
+// v = H 2^22 + L with H = round(v / 2^22) and |L| <= 2^21, both read off the bit pattern of a
+// sum with a bias 1.5 * 2^(23 + k), which rounds to a multiple of 2^k (all steps exact).
+__device__ __forceinline__ long long f32_int_exact(uint32_t bits) {
+  const float v = __uint_as_float(bits);
+  const float kBigBias = 52776558133248.0f;  // 1.5 * 2^45: multiples of 2^22
+  const float kBias = 12582912.0f;           // 1.5 * 2^23: multiples of 1
+  const float hb = v + kBigBias;
+  const int H = __float_as_int(hb) - 0x56400000;
+  const float l = v - (hb - kBigBias);
+  const int L = __float_as_int(l + kBias) - 0x4B400000;
+  return static_cast<long long>(H) * 4194304LL + L;
 }
 
 // finiteness from the bit pattern (integer compare, no FP64 instruction)
@@ -166,6 +188,25 @@ __device__ __forceinline__ bool kstage_active(const uint32_t* mask_a, const uint
   return __ldg(mask_a + ti * mask_ld + k128) != 0u && __ldg(mask_b + tj * mask_ld + k128) != 0u;
 }
 
+// Work unit u of the launch -> output tile, k-block range and split part (-1: whole tile).
+// The tiles of the last, partial wave are split along k into args.split parts, so that every
+// CTA runs the same number of whole tiles plus at most one part (see sliced_gemm).
+__device__ __forceinline__ void unit_of(int u, const SlicedGemmArgs& a, int nk, int& tile,
+                                        int& kb0, int& kb1, int& part) {
+  if (a.split <= 1 || u < a.full_tiles) {
+    tile = u;
+    kb0 = 0;
+    kb1 = nk;
+    part = -1;
+    return;
+  }
+  const int v = u - a.full_tiles;
+  tile = a.full_tiles + v / a.split;
+  part = v % a.split;
+  kb0 = part * nk / a.split;
+  kb1 = (part + 1) * nk / a.split;
+}
+
 template <int NSLICE, int BK, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     sliced_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
@@ -174,8 +215,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
-  __shared__ __align__(8) uint64_t acc_full_bar;
-  __shared__ __align__(8) uint64_t acc_empty_bar;
+  __shared__ __align__(8) uint64_t acc_full_bar[2];
+  __shared__ __align__(8) uint64_t acc_empty_bar[2];
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
 
@@ -188,17 +229,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   const bool sym = (args.mode & kGemmSym) != 0;
   const int tn = args.tiles_n;
   const int ntiles = sym ? tn * (tn + 1) / 2 : args.tiles_m * tn;
+  const int nunits =
+      args.split > 1 ? args.full_tiles + (ntiles - args.full_tiles) * args.split : ntiles;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const uint32_t ncols = static_cast<uint32_t>(args.tmem_cols);
+  // two accumulator sets when a set takes at most half of TMEM (at most 2 orders): the MMAs of
+  // the next tile then run while the epilogue drains this one
+  const int nbuf = (args.nacc * kBN * 2 <= args.tmem_cols) ? 2 : 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&acc_full_bar, 1);
-    mbar_init(&acc_empty_bar, kEpiWarps);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full_bar[b], 1);
+      mbar_init(&acc_empty_bar[b], kEpiWarps);
+    }
     abort_flag = 0;
     fence_barrier_init();
   }
@@ -211,7 +259,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tbase = tmem_base_sh;
   const int nk = (args.K + BK - 1) / BK;
-
+  if (warp < kEpiWarp0) {
+    // ---------------- control warpgroup: producer, MMA issuer, two idle warps ----------------
+    setmaxnreg_dec<kCtrlRegs>();
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer: one stage ring across all tiles of this CTA -----------
@@ -219,11 +269,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       tma_prefetch_desc(&tmB);
       int it = 0;
       bool stop = false;
-      for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
+      for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x) {
+        int tile, kb0, kb1, part;
+        unit_of(u, args, nk, tile, kb0, kb1, part);
         int ti, tj;
         if (sym) upper_tile(tile, tn, ti, tj);
         else { ti = tile / tn; tj = tile % tn; }
-        for (int kb = 0; kb < nk; ++kb) {
+        for (int kb = kb0; kb < kb1; ++kb) {
           if (!kstage_active(args.mask_a, args.mask_b, args.mask_ld, ti, tj, kb, BK)) continue;
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
@@ -248,38 +300,42 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer (one thread) ----------------
-      // Everything but the stage base is fixed per launch: per-pair descriptor offsets (16-byte
-      // units), accumulator columns and whether the pair opens its order's accumulator; the
-      // unrolled issue loop is then two adds per MMA.
-      constexpr uint32_t idesc = idesc_f16_f32(kBM, kBN);
+      // Everything but the stage base is fixed per launch: per-instruction descriptor offsets
+      // (16-byte units), accumulator columns, instruction descriptors (N = 128 or 256) and
+      // whether the instruction opens its accumulators; the unrolled issue loop is then two adds
+      // per MMA.
+      const uint32_t idesc_n[2] = {idesc_f16_f32(kBM, kBN), idesc_f16_f32(kBM, 2 * kBN)};
       const uint64_t desc_fixed = smem_desc(0u, BK);
-      uint32_t offa[kPairsUsed], offb[kPairsUsed], dcol[kPairsUsed], opens[kPairsUsed];
-      const int np = args.num_pairs;
-      uint32_t seen = 0;
+      uint32_t offa[kPairsUsed], offb[kPairsUsed], dcol[kPairsUsed], opens[kPairsUsed],
+          idsc[kPairsUsed];
+      const int ni = args.num_ins;
 #pragma unroll
       for (int p = 0; p < kPairsUsed; ++p) {
-        const int pp = p < np ? p : 0;
-        const int o = args.pair_o[pp];
-        offa[p] = (static_cast<uint32_t>(args.pair_s[pp]) * Cfg::kTileBytes) >> 4;
-        offb[p] = (static_cast<uint32_t>(args.pair_t[pp]) * Cfg::kTileBytes) >> 4;
-        dcol[p] = static_cast<uint32_t>(o * kBN);
-        opens[p] = ((seen >> o) & 1u) ? 0u : 1u;
-        if (p < np) seen |= 1u << o;
+        const int pp = p < ni ? p : 0;
+        offa[p] = (static_cast<uint32_t>(args.ins_s[pp]) * Cfg::kTileBytes) >> 4;
+        offb[p] = (static_cast<uint32_t>(args.ins_t[pp]) * Cfg::kTileBytes) >> 4;
+        dcol[p] = static_cast<uint32_t>((args.ins_s[pp] + args.ins_t[pp]) * kBN);
+        opens[p] = static_cast<uint32_t>(args.ins_open[pp]);
+        idsc[p] = idesc_n[args.ins_wide[pp] ? 1 : 0];
       }
       int it = 0, tcount = 0;
       unsigned long long issued = 0;
       bool stop = false;
-      for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x, ++tcount) {
-        if (tcount > 0 &&
-            !mbar_wait_bounded(&acc_empty_bar, (tcount - 1) & 1u, args.err, &abort_flag)) {
+      for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x, ++tcount) {
+        const int buf = tcount % nbuf, use = tcount / nbuf;
+        if (use > 0 &&
+            !mbar_wait_bounded(&acc_empty_bar[buf], (use - 1) & 1u, args.err, &abort_flag)) {
           stop = true;
           break;
         }
         tc_fence_after();
+        const uint32_t tacc = tbase + static_cast<uint32_t>(buf * args.nacc * kBN);
+        int tile, kb0, kb1, part;
+        unit_of(u, args, nk, tile, kb0, kb1, part);
         int ti, tj;
         if (sym) upper_tile(tile, tn, ti, tj);
         else { ti = tile / tn; tj = tile % tn; }
-        for (int kb = 0; kb < nk; ++kb) {
+        for (int kb = kb0; kb < kb1; ++kb) {
           if (!kstage_active(args.mask_a, args.mask_b, args.mask_ld, ti, tj, kb, BK)) continue;
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
@@ -292,14 +348,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t ad0 = desc_fixed | static_cast<uint64_t>((a0 >> 4) & 0x3FFFu);
           const uint64_t bd0 =
               desc_fixed | static_cast<uint64_t>(((a0 + NSLICE * Cfg::kTileBytes) >> 4) & 0x3FFFu);
+          // instruction outer, k step inner: consecutive MMAs read adjacent 32-byte columns of
+          // the same 128-byte operand rows (measured: the k-step-outer order runs 2.5x slower)
 #pragma unroll
           for (int p = 0; p < kPairsUsed; ++p) {
-            if (p < np) {
+            if (p < ni) {
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint32_t acc = (kb > 0 || kk > 0 || opens[p] == 0u) ? 1u : 0u;
-                umma_f16(tbase + dcol[p], ad0 + offa[p] + 2u * kk, bd0 + offb[p] + 2u * kk, idesc,
-                         acc);
+                const uint32_t acc = (kb > kb0 || kk > 0 || opens[p] == 0u) ? 1u : 0u;
+                umma_f16(tacc + dcol[p], ad0 + offa[p] + 2u * kk, bd0 + offb[p] + 2u * kk,
+                         idsc[p], acc);
               }
             }
           }
@@ -307,15 +365,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++it;
           ++issued;
         }
-        umma_commit(&acc_full_bar);  // accumulators of this tile final (also on abort)
+        umma_commit(&acc_full_bar[buf]);  // accumulators of this tile final (also on abort)
       }
       if (args.kcount != nullptr) atomicAdd(args.kcount, issued);
     }
+  }
   } else {
-    // ---------------- epilogue (warps 2..9) ----------------
+    setmaxnreg_inc<kEpiRegs>();
+    // ---------------- epilogue (warps 4..11) ----------------
     const int q = warp & 3;          // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;  // which 64 of the 128 columns
-    double* stage = staging_all + (warp - 2) * (32 * (kStageCols + 1));
+    const int ew = warp - kEpiWarp0;
+    const int half = ew >> 2;        // which 64 of the 128 columns
+    double* stage = staging_all + ew * (32 * (kStageCols + 1));
     double alpha = args.alpha, beta = args.beta;
     if (args.coef != nullptr) {
       alpha = args.coef[0];
@@ -325,11 +386,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool alpha_neg = false;
     const bool pow2_alpha = pow2_scalar(alpha, alpha_k, alpha_neg);
     int tcount = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++tcount) {
+      int tile, kb0, kb1, part;
+      unit_of(u, args, nk, tile, kb0, kb1, part);
       int ti, tj;
       if (sym) upper_tile(tile, tn, ti, tj);
       else { ti = tile / tn; tj = tile % tn; }
-      const bool ok = mbar_wait_bounded(&acc_full_bar, tcount & 1u, args.err, &abort_flag);
+      const int buf = tcount % nbuf, use = tcount / nbuf;
+      const bool ok = mbar_wait_bounded(&acc_full_bar[buf], use & 1u, args.err, &abort_flag);
+      const uint32_t tacc = tbase + static_cast<uint32_t>(buf * args.nacc * kBN);
       tc_fence_after();
       if (!ok || abort_flag) break;
       const bool diag_tile = (ti == tj);
@@ -339,26 +404,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool sa_ok = finite_bits(sa);
       const int ex_base = pow2_exponent(sa) - 22 - args.shift * (args.nacc - 1) +
                           (pow2_alpha ? alpha_k : 0);
-      for (int c = 0; c < 2; ++c) {
-        const int ccol = half * 64 + c * 32;  // column offset inside the tile
-        long long T[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) T[j] = 0;
-        for (int o = 0; o < args.nacc; ++o) {  // Horner in 2^shift, order 0 first
-          uint32_t r[32];
-          tmem_ld_32x32b_x32(tbase + (static_cast<uint32_t>(q * 32) << 16) +
-                                 static_cast<uint32_t>(o * kBN + ccol),
-                             r);
-          tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 32; ++j) T[j] = (T[j] << args.shift) + f32_integer(r[j]);
-        }
-        if (c == 1) {
-          // every TMEM read of this warp for this tile is done: release the accumulators early
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&acc_empty_bar);
-        }
+      // finished integer sums T (row grow, 32 columns from ccol) -> C (and mirror / C^T)
+      auto store_chunk = [&](int ccol, const long long* T) {
         const int c0 = tj * kBN + ccol;
 #pragma unroll
         for (int sc = 0; sc < 32 / kStageCols; ++sc) {
@@ -403,6 +450,93 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           __syncwarp();
         }
+      };
+      // a split part leaves its sums in its workspace slot, column-major in the tile
+      // (coalesced: lane = row); the last part to finish adds them up and stores the tile
+      long long* wsp = nullptr;
+      if (part >= 0)
+        wsp = args.splitk_ws +
+              (static_cast<int64_t>(tile - args.full_tiles) * args.split + part) * (kBM * kBN) +
+              q * 32 + lane;
+      // Every TMEM read of this warp first (its 64 columns, 16 per load, Horner in 2^shift with
+      // order 0 first), then the accumulators are released, then the conversion and the stores
+      // run while the MMAs of the next tile proceed.
+      long long T0[32], T1[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        T0[j] = 0;
+        T1[j] = 0;
+      }
+      const uint32_t trow = tacc + (static_cast<uint32_t>(q * 32) << 16) +
+                            static_cast<uint32_t>(half * 64);
+      for (int o = 0; o < args.nacc; ++o) {
+        const uint32_t tcol = trow + static_cast<uint32_t>(o * kBN);
+        uint32_t r[16];
+        tmem_ld_32x32b_x16(tcol, r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) T0[j] = (T0[j] << args.shift) + f32_int_exact(r[j]);
+        tmem_ld_32x32b_x16(tcol + 16u, r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) T0[16 + j] = (T0[16 + j] << args.shift) + f32_int_exact(r[j]);
+        tmem_ld_32x32b_x16(tcol + 32u, r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) T1[j] = (T1[j] << args.shift) + f32_int_exact(r[j]);
+        tmem_ld_32x32b_x16(tcol + 48u, r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) T1[16 + j] = (T1[16 + j] << args.shift) + f32_int_exact(r[j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty_bar[buf]);
+      if (wsp != nullptr) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          wsp[(half * 64 + j) * kBM] = T0[j];
+          wsp[(half * 64 + 32 + j) * kBM] = T1[j];
+        }
+      } else {
+        // one copy of the store code in the instruction stream
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+          store_chunk(half * 64 + 32 * c, T0);
+          if (c == 0) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) T0[j] = T1[j];
+          }
+        }
+      }
+      if (wsp != nullptr) {
+        // publish this part's sums, then count it in; no CTA ever waits for another
+        __threadfence();
+        __syncwarp();
+        uint32_t* cnt = args.splitk_cnt + (tile - args.full_tiles) * kEpiWarps + ew;
+        unsigned prev = 0u;
+        if (lane == 0) prev = atomicAdd(cnt, 1u);
+        prev = __shfl_sync(0xffffffffu, prev, 0);
+        if (prev + 1u == static_cast<unsigned>(args.split)) {
+          if (lane == 0) *cnt = 0u;  // every part has counted in: ready for the next launch
+          __threadfence();
+          const long long* wst =
+              args.splitk_ws +
+              static_cast<int64_t>(tile - args.full_tiles) * args.split * (kBM * kBN) + q * 32 +
+              lane;
+          for (int c = 0; c < 2; ++c) {
+            const int ccol = half * 64 + c * 32;
+            long long T[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) T[j] = 0;
+            for (int pp = 0; pp < args.split; ++pp) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                T[j] += __ldcg(wst + static_cast<int64_t>(pp) * (kBM * kBN) + (ccol + j) * kBM);
+            }
+            store_chunk(ccol, T);
+          }
+        }
       }
     }
   }
@@ -437,6 +571,20 @@ EncodeTiledFn get_encode_fn() {
   return fn;
 }
 
+// SMs of the current device (one persistent CTA each)
+int device_sms() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static int cache[64] = {};
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (cache[dev] == 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = n > 0 ? n : 148;
+  }
+  return cache[dev];
+}
+
 // 3-D map over slices: dims (K, rows, nslice), box (bk, 128, nslice), FP16, swizzle = bk*2 B.
 bool make_slice_map(CUtensorMap* map, const SliceBuf& sb, int bk, int nslice) {
   EncodeTiledFn enc = get_encode_fn();
@@ -462,15 +610,15 @@ cudaError_t launch_cfg(const CUtensorMap& ta, const CUtensorMap& tb, const Slice
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(Cfg::kSmemBytes));
   if (e != cudaSuccess) return e;
+  // the register split inside the kernel assumes exactly kLaunchRegs registers a thread at launch
+  static const int regs = [&] {
+    cudaFuncAttributes fa;
+    return cudaFuncGetAttributes(&fa, kern) == cudaSuccess ? fa.numRegs : -1;
+  }();
+  if (regs != kLaunchRegs) return cudaErrorInvalidConfiguration;
   count_launch();
-  static int num_sms = 0;
-  if (num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (num_sms <= 0) num_sms = 148;
-  }
-  const int blocks = grid < num_sms ? grid : num_sms;
+  const int sms = device_sms();
+  const int blocks = grid < sms ? grid : sms;
   kern<<<blocks, kThreads, Cfg::kSmemBytes, stream>>>(ta, tb, a);
   return cudaGetLastError();
 }
@@ -498,8 +646,29 @@ int build_pairs(int nslice, int max_order, SlicedGemmArgs* a) {
       }
     }
   a->num_pairs = np;
+  // MMA instructions: for each A slice s, the B slices t = 0, 1, ... in twos where both pairs
+  // exist (one N = 256 MMA over B slices t and t+1, which are adjacent 128-row panels in shared
+  // memory, into the adjacent accumulators of orders s+t and s+t+1), else one N = 128 MMA; a
+  // two-slice MMA that would open one accumulator and add into the other is split.
+  int ni = 0;
+  uint32_t opened = 0;
+  for (int s = 0; s < nslice; ++s) {
+    for (int t = 0; t < nslice && s + t <= max_order && ni < kMaxPairs;) {
+      const int o = s + t;
+      bool wide = t + 1 < nslice && o + 1 <= max_order;
+      if (wide && ((opened >> o) & 1u) != ((opened >> (o + 1)) & 1u)) wide = false;
+      a->ins_s[ni] = static_cast<int8_t>(s);
+      a->ins_t[ni] = static_cast<int8_t>(t);
+      a->ins_wide[ni] = wide ? 1 : 0;
+      a->ins_open[ni] = ((opened >> o) & 1u) ? 0 : 1;
+      opened |= (wide ? 3u : 1u) << o;
+      ++ni;
+      t += wide ? 2 : 1;
+    }
+  }
+  a->num_ins = ni;
   a->nacc = max_order + 1;
-  a->tmem_cols = (a->nacc <= 2) ? 256 : 512;
+  a->tmem_cols = 512;  // at most 2 orders: two accumulator sets (double buffering)
   return np;
 }
 
@@ -526,14 +695,40 @@ cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& B, const Precision& p
   const int tn = (args.N + kBN - 1) / kBN;
   args.tiles_n = tn;
   args.tiles_m = tm;
-  const int grid = (args.mode & kGemmSym) ? tn * (tn + 1) / 2 : tm * tn;
-  if (grid == 0) return cudaSuccess;
+  const int ntiles = (args.mode & kGemmSym) ? tn * (tn + 1) / 2 : tm * tn;
+  if (ntiles == 0) return cudaSuccess;
+  const int bk = sliced_gemm_bk(nslice);
+
+  // k split of the last wave: with W whole waves of tiles over the SMs and `tail` tiles left,
+  // the tail tiles run as `split` k-parts each (tail x split <= SMs), so the launch takes
+  // W + 1/split tile times instead of W + 1 (n = 4096, symmetric: 528 tiles = 3 x 152 + 72,
+  // split 2).  Not with tile masks (a part could skip all of its k blocks).
+  args.split = 1;
+  args.full_tiles = ntiles;
+  const int sms = device_sms();
+  const int nk = (args.K + bk - 1) / bk;
+  // Only for formats with one accumulator set (three or more orders): with two sets the
+  // epilogue already overlaps the next tile's MMAs, and the parts' extra epilogue work costs more
+  // than the shorter tail saves (measured on the two-slice Newton-Schulz products).
+  const bool one_acc_set = args.nacc * kBN * 2 > args.tmem_cols;
+  if (one_acc_set && args.splitk_ws != nullptr && args.splitk_cnt != nullptr &&
+      args.mask_a == nullptr && args.mask_b == nullptr) {
+    const int tail = ntiles % sms;
+    int sp = tail > 0 ? sms / tail : 1;
+    if (sp > 4) sp = 4;
+    if (sp > nk) sp = nk;
+    if (sp >= 2 && tail * sp <= args.splitk_slots && tail <= args.splitk_tiles) {
+      args.split = sp;
+      args.full_tiles = ntiles - tail;
+    }
+  }
+  const int grid = args.split > 1 ? args.full_tiles + (ntiles - args.full_tiles) * args.split
+                                  : ntiles;
 
   // 128-byte TMA lines (BK = 64) wherever two stages fit: the TMA's cost per stage grows with
   // its line count (~1.5 cycles per line) as much as with its bytes, so longer lines beat a
   // deeper ring (measured: 3 slices with BK = 64 and 2 stages run 13-17% faster than with
   // BK = 32 and 4 stages).  Four slices need BK = 32 to fit two or more stages.
-  const int bk = sliced_gemm_bk(nslice);
   CUtensorMap ta, tb;
   if (!make_slice_map(&ta, A, bk, nslice) || !make_slice_map(&tb, B, bk, nslice))
     return cudaErrorInvalidValue;

@@ -13,6 +13,7 @@ namespace gdm {
 
 enum FBuf { F_H, F_S, F_Z, F_ZT, F_X, F_X2, F_XN, F_T, F_U, F_V, F_COUNT };
 enum SBuf { SL_S, SL_Z, SL_ZT, SL_A, SL_B, SL_X, SL_X2, SL_W, SL_COUNT };
+constexpr int kSplitTiles = 160;  // split-k: most tiles split at once (>= the SM count)
 constexpr int kSmall = 4096;  // doubles of small device scratch beyond the partials
 
 // Device bytes gdm_init allocates for capacity n (one cudaMalloc).
@@ -48,6 +49,11 @@ struct gdm_handle {
   double* small = nullptr;     // kSmall doubles: coefficients, bounds, reductions
   gdm::Trs4State* st_dev = nullptr;
   uint32_t* err_dev = nullptr;
+  // split-k of the products' last wave: int64 partial-sum slots and the per-tile counters
+  // (kSplitTiles x kEpilogueWarps words right after err_dev, cleared with it)
+  long long* split_ws = nullptr;
+  uint32_t* split_cnt = nullptr;
+  int split_slots = 0;
   double* host_buf = nullptr;  // pinned: kSmall doubles
   gdm::Trs4State* st_host = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

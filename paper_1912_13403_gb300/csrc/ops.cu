@@ -12,15 +12,17 @@ using namespace gdm;
 
 namespace {
 
+constexpr int kSplitSlotsOps = 160;  // split-k slots and counted tiles (>= the SM count)
+
 struct Scratch {
   cudaStream_t s;
-  void* ptrs[16] = {};
+  void* ptrs[32] = {};
   int n = 0;
   explicit Scratch(cudaStream_t st) : s(st) {}
   template <class T>
   T* get(size_t bytes) {
     void* p = nullptr;
-    if (n >= 16 || cudaMallocAsync(&p, bytes, s) != cudaSuccess) return nullptr;
+    if (n >= 32 || cudaMallocAsync(&p, bytes, s) != cudaSuccess) return nullptr;
     ptrs[n++] = p;
     return static_cast<T*>(p);
   }
@@ -99,6 +101,21 @@ cudaError_t run_product(Scratch& sc, const double* A, int64_t lda, const double*
   p.nslice = nslice;
   p.max_order = max_order;
   p.bits = bits;
+  // split-k workspace for the last wave of tiles (counters start at zero)
+  {
+    const size_t tiles = static_cast<size_t>((m + 127) / 128) * ((n + 127) / 128);
+    const int slots = static_cast<int>(tiles * 4 < kSplitSlotsOps ? tiles * 4 : kSplitSlotsOps);
+    long long* ws = sc.get<long long>(sizeof(long long) * 128 * 128 * slots);
+    uint32_t* cnt = sc.get<uint32_t>(sizeof(uint32_t) * kSplitSlotsOps * kEpilogueWarps);
+    if (ws != nullptr && cnt != nullptr &&
+        cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * kSplitSlotsOps * kEpilogueWarps, sc.s) ==
+            cudaSuccess) {
+      a.splitk_ws = ws;
+      a.splitk_cnt = cnt;
+      a.splitk_slots = slots;
+      a.splitk_tiles = kSplitSlotsOps;
+    }
+  }
   e = sliced_gemm(sa, sb, p, a, sc.s);
   if (e != cudaSuccess || !sym) return e;
   return diag_fix(A, lda, Bt, ldb, C, ldc, m, k, alpha, beta, D, ldd, 0.0, coef, sc.s);

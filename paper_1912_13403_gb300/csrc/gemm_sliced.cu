@@ -405,15 +405,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int ex_base = pow2_exponent(sa) - 22 - args.shift * (args.nacc - 1) +
                           (pow2_alpha ? alpha_k : 0);
       // finished integer sums T (row grow, 32 columns from ccol) -> C (and mirror / C^T)
-      auto store_chunk = [&](int ccol, const long long* T) {
+      // (a loop over groups of 8 columns, not unrolled, with T shifted down by 8 after each
+      // group: one copy of the per-element code, small enough for the instruction cache;
+      // destroys T)
+      auto store_chunk = [&](int ccol, long long (&T)[32]) {
         const int c0 = tj * kBN + ccol;
-#pragma unroll
+#pragma unroll 1
         for (int sc = 0; sc < 32 / kStageCols; ++sc) {
           // thread = row: finished values; mirror / transposed writes are coalesced here
 #pragma unroll
           for (int jj = 0; jj < kStageCols; ++jj) {
-            const int j = sc * kStageCols + jj;
-            const int gcol = c0 + j;
+            const int j = jj;
+            const int gcol = c0 + sc * kStageCols + jj;
             double val = 0.0;
             if (grow < args.M && gcol < args.N) {
               const double sb = args.row_scale_b[gcol];
@@ -449,6 +452,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                   stage[rr * (kStageCols + 1) + cc];
           }
           __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 32 - kStageCols; ++j) T[j] = T[j + kStageCols];
         }
       };
       // a split part leaves its sums in its workspace slot, column-major in the tile

@@ -141,8 +141,8 @@ def job_throughput(units_per_rank, total_ms_this_rank, device="cpu"):
 PHASES = ("newton_schulz", "refine", "transform", "purify")
 
 # DRAM bytes (read + write) per purification product launch at n=4096 from one ncu capture of
-# the current sliced_gemm_kernel<3,64,2>; None until that kernel has been captured.
-PURIFY_TRAFFIC_N4096 = None
+# the current sliced_gemm_kernel<3,64,2> (average of X X and X^2 W: 371.2 and 489.4 MB).
+PURIFY_TRAFFIC_N4096 = 430.3e6
 
 
 def traffic_bytes(n):
@@ -482,7 +482,8 @@ def run_ours(args):
                      "unit": "TFLOP/s", "frac": achieved_pu / peak if peak else None,
                      "traffic": traffic_bytes(n),
                      "kernel": "sliced_gemm_kernel<3,64,2>: TRS4 products X X and X^2 W "
-                               "(tcgen05 kind::f16, 8 slice pairs, upper-triangle tiles)",
+                               "(tcgen05 kind::f16, 8 slice pairs as 5 MMAs per k-step, "
+                               "upper-triangle tiles)",
                      "flops_per_launch": pfl / pl if pl else None,
                      "ms_per_launch": pms / pl if pl else None,
                      "peak_source": "%s bf16 sustained (fp16 = bf16 rate)" % peaks["source"],

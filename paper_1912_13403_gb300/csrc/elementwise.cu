@@ -988,6 +988,114 @@ __global__ void w_row_dots_kernel(const double* __restrict__ partials, int n,
   row_dot[i] = coef[0] * p[2] + coef[1] * p[3] + coef[2] * p[1];
 }
 
+// sum_j (A - I)_ij^2 (minus_identity), sum_j A_ij^2 or sum_j A_ij B_ij for one row per block,
+// all of the row's loads in flight at once (like the forming/slicing kernels), double-float sums
+// (no FP64 instruction) into partials[row].
+template <int THREADS, bool HAS_B>
+__global__ void __launch_bounds__(THREADS)
+    dot_rows_kernel(const double* A, int64_t lda, const double* B, int64_t ldb, int cols,
+                    int minus_identity, double* partials) {
+  __shared__ DF red[THREADS / 32];
+  const int row = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int npairs = cols >> 1;
+  const uint4* ar = reinterpret_cast<const uint4*>(A + row * lda);
+  const uint4* br = HAS_B ? reinterpret_cast<const uint4*>(B + row * ldb) : nullptr;
+  uint4 va[kFusedPPT], vb[HAS_B ? kFusedPPT : 1];
+#pragma unroll
+  for (int i = 0; i < kFusedPPT; ++i) {
+    const int p = i * THREADS + threadIdx.x;
+    va[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (p < npairs) va[i] = ar[p];
+    if (HAS_B) {
+      vb[i] = make_uint4(0u, 0u, 0u, 0u);
+      if (p < npairs) vb[i] = br[p];
+    }
+  }
+  DF acc{0.0f, 0.0f};
+#pragma unroll
+  for (int i = 0; i < kFusedPPT; ++i) {
+    const int p = i * THREADS + threadIdx.x;
+    if (p < npairs) {
+      uint4 x = va[i];
+      if (minus_identity && (2 * p == row || 2 * p + 1 == row)) {
+        if (2 * p == row) {
+          const uint2 d = add_on_diagonal_words(make_uint2(x.x, x.y), -1.0);
+          x.x = d.x;
+          x.y = d.y;
+        } else {
+          const uint2 d = add_on_diagonal_words(make_uint2(x.z, x.w), -1.0);
+          x.z = d.x;
+          x.w = d.y;
+        }
+      }
+      float h0, l0, h1, l1;
+      split_words(x.y, x.x, h0, l0);
+      split_words(x.w, x.z, h1, l1);
+      if (HAS_B) {
+        float g0, k0, g1, k1;
+        split_words(vb[i].y, vb[i].x, g0, k0);
+        split_words(vb[i].w, vb[i].z, g1, k1);
+        acc = df_fma(df_fma(acc, h0, l0, g0, k0), h1, l1, g1, k1);
+      } else {
+        acc = df_fma(df_fma(acc, h0, l0, h0, l0), h1, l1, h1, l1);
+      }
+    }
+  }
+  acc = df_warp_sum(acc);
+  if (lane == 0) red[w] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DF t{0.0f, 0.0f};
+    for (int j = 0; j < THREADS / 32; ++j) t = df_add(t, red[j]);
+    partials[row] = df_to_double(t);
+  }
+}
+
+// y = A x for the power iteration, one row per block with all of the row's loads in flight;
+// x as double-float (xh + xl), sums in double-float; partials[row] = y_row^2.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+    matvec_rows_kernel(const double* A, int64_t lda, int n, const float* __restrict__ xh,
+                       const float* __restrict__ xl, double* y, double* partials) {
+  __shared__ DF red[THREADS / 32];
+  const int row = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int npairs = n >> 1;
+  const uint4* ar = reinterpret_cast<const uint4*>(A + row * lda);
+  const float2* xh2 = reinterpret_cast<const float2*>(xh);
+  const float2* xl2 = reinterpret_cast<const float2*>(xl);
+  uint4 va[kFusedPPT];
+#pragma unroll
+  for (int i = 0; i < kFusedPPT; ++i) {
+    const int p = i * THREADS + threadIdx.x;
+    va[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (p < npairs) va[i] = ar[p];
+  }
+  DF acc{0.0f, 0.0f};
+#pragma unroll
+  for (int i = 0; i < kFusedPPT; ++i) {
+    const int p = i * THREADS + threadIdx.x;
+    if (p < npairs) {
+      const float2 bh = xh2[p], bl = xl2[p];
+      float h0, l0, h1, l1;
+      split_words(va[i].y, va[i].x, h0, l0);
+      split_words(va[i].w, va[i].z, h1, l1);
+      acc = df_fma(df_fma(acc, h0, l0, bh.x, bl.x), h1, l1, bh.y, bl.y);
+    }
+  }
+  acc = df_warp_sum(acc);
+  if (lane == 0) red[w] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DF t{0.0f, 0.0f};
+    for (int j = 0; j < THREADS / 32; ++j) t = df_add(t, red[j]);
+    const double yi = df_to_double(t);
+    y[row] = yi;
+    partials[row] = yi * yi;
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // Gershgorin: lo_i = a_ii - sum_{j != i} |a_ij|, hi_i = a_ii + sum_{j != i} |a_ij|
 // ------------------------------------------------------------------------------------------
@@ -1690,14 +1798,25 @@ cudaError_t power_bound(const double* A, int64_t lda, int n, int iters, double f
   float* xh = reinterpret_cast<float*>(work);
   float* xl = xh + n;
   double* y = work + n;  // n doubles after the two float vectors (n doubles of room)
-  const int nb = (n + kRowsPerBlock - 1) / kRowsPerBlock;
+  // one block per row (partials: one value per row) when the row fits in registers and the
+  // float vectors are 8-byte aligned (n even), else one warp per row
+  const bool rows_fit = n % 2 == 0 && n <= kFusedMaxCols && lda % 2 == 0 &&
+                        (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+  const int nb = rows_fit ? n : (n + kRowsPerBlock - 1) / kRowsPerBlock;
   count_launch();
   power_init_kernel<<<(n + 255) / 256, 256, 0, stream>>>(n, xh, xl);
   count_launch();
   power_scale_kernel<<<1, 1024, 0, stream>>>(y, n, partials, 0, xh, xl, est_dev, 1);
   for (int k = 0; k < iters; ++k) {
     count_launch();
-    matvec_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, n, xh, xl, y, partials);
+    if (!rows_fit)
+      matvec_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, n, xh, xl, y, partials);
+    else if (n / 2 <= 128 * kFusedPPT)
+      matvec_rows_kernel<128><<<n, 128, 0, stream>>>(A, lda, n, xh, xl, y, partials);
+    else if (n / 2 <= 256 * kFusedPPT)
+      matvec_rows_kernel<256><<<n, 256, 0, stream>>>(A, lda, n, xh, xl, y, partials);
+    else
+      matvec_rows_kernel<512><<<n, 512, 0, stream>>>(A, lda, n, xh, xl, y, partials);
     count_launch();
     power_scale_kernel<<<1, 1024, 0, stream>>>(y, n, partials, nb, xh, xl, est_dev, 0);
   }
@@ -1775,6 +1894,32 @@ bool slice_traces_fits(const double* X2, const double* X, int64_t ld, int n, con
 cudaError_t dot_partials(const double* A, int64_t lda, const double* B, int64_t ldb, int rows,
                          int cols, int minus_identity, double* partials, int* nblocks,
                          cudaStream_t stream) {
+  const bool rows_fit =
+      cols % 2 == 0 && cols <= kFusedMaxCols && lda % 2 == 0 &&
+      ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
+      (B == nullptr || (ldb % 2 == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0));
+  if (rows_fit && rows > 0) {
+    // one block per row: partials holds one value per row
+    const int npairs = cols / 2;
+    count_launch();
+#define GDM_DOTROWS(T)                                                                         \
+  if (B != nullptr)                                                                            \
+    dot_rows_kernel<T, true><<<rows, T, 0, stream>>>(A, lda, B, ldb, cols, minus_identity,     \
+                                                     partials);                                \
+  else                                                                                         \
+    dot_rows_kernel<T, false><<<rows, T, 0, stream>>>(A, lda, B, ldb, cols, minus_identity,    \
+                                                      partials)
+    if (npairs <= 128 * kFusedPPT) {
+      GDM_DOTROWS(128);
+    } else if (npairs <= 256 * kFusedPPT) {
+      GDM_DOTROWS(256);
+    } else {
+      GDM_DOTROWS(512);
+    }
+#undef GDM_DOTROWS
+    *nblocks = rows;
+    return cudaGetLastError();
+  }
   const int nb = (rows + kRowsPerBlock - 1) / kRowsPerBlock;
   count_launch();
   dot_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, B, ldb, rows, cols, minus_identity,

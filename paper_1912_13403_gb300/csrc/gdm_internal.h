@@ -159,7 +159,7 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
 // Power iteration for lambda_max of a symmetric positive matrix (iters matrix-vector products
 // in double-float from a fixed start vector), then bounds_dev[1] <- min(bounds_dev[1],
 // factor * estimate); the estimate is also written to *est_dev.  `work` holds >= 2 n doubles,
-// `partials` >= ceil(n / 8).
+// `partials` >= n.
 cudaError_t power_bound(const double* A, int64_t lda, int n, int iters, double factor,
                         double* work, double* partials, double* bounds_dev, double* est_dev,
                         cudaStream_t stream);
@@ -185,8 +185,10 @@ cudaError_t w_row_dots(const double* partials, int n, const double* coef_dev, Sl
 cudaError_t trs4_traces(const double* X, const double* X2, int64_t ld, int n, double* partials,
                         int* nblocks, cudaStream_t stream);
 
-// Deterministic sum of partial dot products: out[0] = sum_ij A_ij B_ij (B null -> A_ij^2),
-// with an optional -1 on the diagonal of A first when `minus_identity` (||A - I||^2).
+// Deterministic partial dot products of sum_ij A_ij B_ij (B null -> A_ij^2), with an optional
+// -1 on the diagonal of A first when `minus_identity` (||A - I||^2): one partial per row (rows of
+// at most kFusedMaxCols columns), else one per block of rows; *nblocks gives the count, and
+// partials must hold `rows` doubles.
 cudaError_t dot_partials(const double* A, int64_t lda, const double* B, int64_t ldb, int rows,
                          int cols, int minus_identity, double* partials, int* nblocks,
                          cudaStream_t stream);

@@ -301,6 +301,7 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
   double *Yn = h->f[F_X2], *Zn = h->f[F_V];
   SliceBuf *sY = &h->sl[SL_X], *sZ = &h->sl[SL_Z], *sM = &h->sl[SL_A], *sMt = &h->sl[SL_B];
   const double rn = std::sqrt(static_cast<double>(n));
+  const double ns_handoff = (mixed(h) && h->n_refine >= 2) ? 0.05 : 0.0;
   double prev = INFINITY, res = INFINITY;
   int it = 0;
   bool converged = false;
@@ -329,6 +330,9 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
     converged = false;
     bool diverged = false;
     for (it = 0; it < h->max_ns; ++it) {
+      // M = Y Z in full, with M^T: Y and Z commute only up to rounding, and making M symmetric
+      // (one T for both updates) let that error grow until the iteration diverged for
+      // cond(S) = 1e3 (measured)
       CK(product(h, {Y, sY}, {Z, sZ}, M, Mt, nullptr, 1.0, 0.0, 0.0, false,
                  GDM_PHASE_NEWTON_SCHULZ));
       double r2 = 0.0;
@@ -344,7 +348,10 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
                        "Newton-Schulz for S^-1/2 diverged (residual %g): S not positive definite",
                        res);
       }
-      if (res <= 1e-13 * rn || (res < 1e-2 * rn && res > 0.5 * prev)) {
+      // With two or more refinement steps to follow, stop once ||I - M||_F <= 0.05: the
+      // refinement's third-order steps take 0.05 to about (5/8) 0.05^3 = 7.8e-5 and then below the
+      // rounding floor, which is what the last two Newton-Schulz steps would have done.
+      if (res <= ns_handoff || res <= 1e-13 * rn || (res < 1e-2 * rn && res > 0.5 * prev)) {
         converged = true;
         break;
       }
@@ -396,10 +403,11 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
     derr = std::sqrt(d2);
     if (!std::isfinite(derr)) return set_err(h, GDM_ERR_NONFINITE, "non-finite Z^T S Z");
     if (r == nref || derr == 0.0) break;
-    // The step is third order: ||delta'||_F <= (5/16) ||delta||_F^3.  After a step taken from
-    // ||delta||_F <= 1e-3 its remainder (<= 3.2e-10) lies below the rounding floor that the
-    // sliced products leave in Z^T S Z, so this delta is that floor and another step cannot
-    // lower it.
+    // The step is third order: with F = I - delta/2 + 3 delta^2/8 (delta symmetric, so F
+    // commutes with it), delta' = (I + delta) F^2 - I = (5/8) delta^3 - (15/64) delta^4 +
+    // (9/64) delta^5.  After a step taken from ||delta||_F <= 1e-3 the remainder (<= 6.3e-10)
+    // lies below the rounding floor that the sliced products leave in Z^T S Z, so this delta is
+    // that floor and another step cannot lower it.
     if (derr_prev <= 1e-3) break;
     derr_prev = derr;
     CK(slice(h, Dl, &h->sl[SL_B], GDM_PHASE_REFINE, kDotSelf));

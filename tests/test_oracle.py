@@ -466,6 +466,25 @@ def test_newton_schulz_and_refinement():
     assert e1 <= 10 * e0 ** 2                     # quadratic (in fact cubic) contraction
 
 
+def test_refinement_remainder_is_the_closed_form_polynomial():
+    # For Z commuting with S, delta = Z S Z - I and one refinement step leave
+    # delta' = (I + delta) F^2 - I = (5/8) delta^3 - (15/64) delta^4 + (9/64) delta^5 exactly,
+    # F = I - delta/2 + 3 delta^2/8 (the engine's handover rule from Newton-Schulz rests on the
+    # leading coefficient 5/8).
+    p = make_spectrum_problem(13, 48, 12, cond_S=1e2, gap=0.3)
+    w, V = np.linalg.eigh(p.S)
+    e = np.linspace(-0.02, 0.03, 48)               # Z = S^{-1/2} (I + e), same eigenvectors
+    Z = (V * (w ** -0.5 * np.sqrt(1.0 + e))) @ V.T
+    I = np.eye(48)
+    d = Z @ p.S @ Z - I
+    Zr = steps.inv_sqrt_refine(Z, p.S)
+    d1 = Zr @ p.S @ Zr - I
+    d2 = d @ d
+    poly = 0.625 * d2 @ d - (15.0 / 64.0) * d2 @ d2 + (9.0 / 64.0) * d2 @ d2 @ d
+    assert np.linalg.norm(d1 - poly) <= 1e-6 * np.linalg.norm(poly)
+    assert np.linalg.norm(d1) <= 0.625 * np.linalg.norm(d) ** 3 * 1.01
+
+
 def test_mcweeny_fixes_projectors_and_moves_eigenvalues_to_0_1():
     rng = np.random.default_rng(9)
     Q = haar_orthogonal(rng, 20)

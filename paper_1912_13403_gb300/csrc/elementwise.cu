@@ -166,7 +166,13 @@ __device__ __forceinline__ void pow2_words(unsigned& whi, unsigned& wlo, int k, 
 // for s >= 1 and |d[0]| <= 2^11 when |y| < 2^(11 + bits (nslice - 1) - p).  From the bit
 // pattern yb with integer operations: the rounding is one 64-bit add and shift, each digit a
 // bit field plus a carry.
-__device__ __forceinline__ void slice_digits(long long yb, int p, int nslice, int bits, int* d) {
+// NS / BITS fix the slice count and width at compile time (0: taken from the arguments), so
+// that the shifts and masks of the common formats are constants.
+template <int NS, int BITS>
+__device__ __forceinline__ void slice_digits_t(long long yb, int p, int nslice_rt, int bits_rt,
+                                               int* d) {
+  const int nslice = NS ? NS : nslice_rt;
+  const int bits = BITS ? BITS : bits_rt;
   const unsigned long long ub = static_cast<unsigned long long>(yb);
   const int E = static_cast<int>((ub >> 52) & 0x7FF);
   unsigned long long mant = ub & ((1ULL << 52) - 1);
@@ -193,6 +199,10 @@ __device__ __forceinline__ void slice_digits(long long yb, int p, int nslice, in
 #pragma unroll
     for (int s = 0; s < 4; ++s) d[s] = -d[s];
   }
+}
+
+__device__ __forceinline__ void slice_digits(long long yb, int p, int nslice, int bits, int* d) {
+  slice_digits_t<0, 0>(yb, p, nslice, bits, d);
 }
 
 // Two integers |m| <= 2048 as an FP16 pair (low half = m0): the integers become floats by the
@@ -698,6 +708,49 @@ __global__ void __launch_bounds__(kSliceThreads)
 constexpr int kFusedPPT = 8;
 static_assert(kFusedMaxCols == 2 * 512 * kFusedPPT, "fused slicing: up to 512 threads per row");
 
+// The slices of a row held in registers (kFusedPPT column pairs a thread): digits of
+// round(y 2^p2) (p2 <= -1000: an all-zero row), written as FP16 pairs, one plane per slice.
+template <int NS, int BITS, int THREADS>
+__device__ __forceinline__ void write_row_slices(const uint4 (&v)[kFusedPPT], int npairs, int p2,
+                                                 uint32_t* orow, int64_t plane2, int nslice,
+                                                 int bits) {
+  const int ns = NS ? NS : nslice;
+#pragma unroll
+  for (int i = 0; i < kFusedPPT; ++i) {
+    const int p = i * THREADS + threadIdx.x;
+    if (p < npairs) {
+      int d0[4] = {0, 0, 0, 0}, d1[4] = {0, 0, 0, 0};
+      if (p2 > -1000) {
+        slice_digits_t<NS, BITS>(
+            static_cast<long long>((static_cast<unsigned long long>(v[i].y) << 32) | v[i].x), p2,
+            nslice, bits, d0);
+        slice_digits_t<NS, BITS>(
+            static_cast<long long>((static_cast<unsigned long long>(v[i].w) << 32) | v[i].z), p2,
+            nslice, bits, d1);
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        if (s < ns) orow[s * plane2 + p] = half_pair(d0[s], d1[s]);
+    }
+  }
+}
+
+// the route's formats (Newton-Schulz 2 x 12 bits, purification 3 x 12, refinement and
+// transforms 4 x 9) with constant shifts; any other format at run time
+template <int THREADS>
+__device__ __forceinline__ void write_row_slices_any(const uint4 (&v)[kFusedPPT], int npairs,
+                                                     int p2, uint32_t* orow, int64_t plane2,
+                                                     int nslice, int bits) {
+  if (nslice == 3 && bits == 12)
+    write_row_slices<3, 12, THREADS>(v, npairs, p2, orow, plane2, nslice, bits);
+  else if (nslice == 2 && bits == 12)
+    write_row_slices<2, 12, THREADS>(v, npairs, p2, orow, plane2, nslice, bits);
+  else if (nslice == 4 && bits == 9)
+    write_row_slices<4, 9, THREADS>(v, npairs, p2, orow, plane2, nslice, bits);
+  else
+    write_row_slices<0, 0, THREADS>(v, npairs, p2, orow, plane2, nslice, bits);
+}
+
 template <int MODE, int DOT, int THREADS, bool HAS_X2>
 __device__ __forceinline__ void form_slice_row(const uint4* xr, const uint4* x2r, uint4* yr,
                                                int npairs, int row, double a, double b, int ak,
@@ -778,22 +831,7 @@ __device__ __forceinline__ void form_slice_row(const uint4* xr, const uint4* x2r
   const int p2 = shift_sh[0];
   uint32_t* orow = reinterpret_cast<uint32_t*>(out + row * out_ld);
   const int64_t plane2 = plane >> 1;
-#pragma unroll
-  for (int i = 0; i < kFusedPPT; ++i) {
-    const int p = i * THREADS + threadIdx.x;
-    if (p < npairs) {
-      int d0[4] = {0, 0, 0, 0}, d1[4] = {0, 0, 0, 0};
-      if (p2 > -1000) {
-        slice_digits(static_cast<long long>((static_cast<unsigned long long>(v[i].y) << 32) | v[i].x),
-                     p2, nslice, bits, d0);
-        slice_digits(static_cast<long long>((static_cast<unsigned long long>(v[i].w) << 32) | v[i].z),
-                     p2, nslice, bits, d1);
-      }
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-        if (s < nslice) orow[s * plane2 + p] = half_pair(d0[s], d1[s]);
-    }
-  }
+  write_row_slices_any<THREADS>(v, npairs, p2, orow, plane2, nslice, bits);
 }
 
 template <int MODE, int THREADS, bool HAS_X2>
@@ -811,7 +849,9 @@ __device__ __forceinline__ void form_slice_dispatch(int dot, const uint4* xr, co
                                    red_dot, shift_sh)
   switch (dot) {
     case kDotSelf: GDM_FSR(kDotSelf); break;
-    case kDotX2: GDM_FSR(kDotX2); break;
+    case kDotX2:  // needs X2 (form_and_slice refuses it without)
+      if constexpr (HAS_X2) GDM_FSR(kDotX2);
+      break;
     case kDotX: GDM_FSR(kDotX); break;
     default: GDM_FSR(kDotNone);
   }
@@ -960,22 +1000,7 @@ __global__ void __launch_bounds__(THREADS)
   const int p2 = shift_sh;
   uint32_t* orow = reinterpret_cast<uint32_t*>(out + row * out_ld);
   const int64_t plane2 = plane >> 1;
-#pragma unroll
-  for (int i = 0; i < kFusedPPT; ++i) {
-    const int p = i * THREADS + threadIdx.x;
-    if (p < npairs) {
-      int d0[4] = {0, 0, 0, 0}, d1[4] = {0, 0, 0, 0};
-      if (p2 > -1000) {
-        slice_digits(static_cast<long long>((static_cast<unsigned long long>(v[i].y) << 32) | v[i].x),
-                     p2, nslice, bits, d0);
-        slice_digits(static_cast<long long>((static_cast<unsigned long long>(v[i].w) << 32) | v[i].z),
-                     p2, nslice, bits, d1);
-      }
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-        if (s < nslice) orow[s * plane2 + p] = half_pair(d0[s], d1[s]);
-    }
-  }
+  write_row_slices_any<THREADS>(v, npairs, p2, orow, plane2, nslice, bits);
 }
 
 // Row dot products of W = a X + b X^2 + c I with X^2 from the per-row trace terms of

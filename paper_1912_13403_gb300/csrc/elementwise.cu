@@ -1347,7 +1347,8 @@ __device__ void reduce_terms(const double* partials, int nblocks, int nterms, do
   }
 }
 
-__global__ void reduce_kernel(const double* partials, int nblocks, int nterms, double* out) {
+__global__ void __launch_bounds__(1024) reduce_kernel(const double* partials, int nblocks, int nterms,
+                                                    double* out) {
   __shared__ double red[32];
   reduce_terms(partials, nblocks, nterms, out, red);
 }
@@ -1956,7 +1957,7 @@ cudaError_t dot_partials(const double* A, int64_t lda, const double* B, int64_t 
 cudaError_t reduce_partials(const double* partials, int nblocks, int nterms, double* out_dev,
                             cudaStream_t stream) {
   count_launch();
-  reduce_kernel<<<1, 256, 0, stream>>>(partials, nblocks, nterms, out_dev);
+  reduce_kernel<<<1, 1024, 0, stream>>>(partials, nblocks, nterms, out_dev);
   return cudaGetLastError();
 }
 

@@ -58,6 +58,21 @@ def test_product_matches_fp64(g, fmt, m, n, k):
     _check_product(C.cpu().numpy(), A, Bt, FORMATS[fmt])
 
 
+@pytest.mark.parametrize("fmt", [(3, 3, 12), (2, 1, 12), (4, 3, 9)])
+@pytest.mark.parametrize("k", [8200, 8201])
+def test_product_wide_rows(g, fmt, k):
+    # rows wider than the one-pass slicing kernel holds (8192 columns): the two-pass row / element
+    # slicing (even k) and the per-row generic slicing (odd k); the bound grows like sqrt(K)
+    rng = np.random.default_rng(k)
+    A = rng.standard_normal((130, k))
+    Bt = rng.standard_normal((131, k))
+    A[3] *= 1e-3
+    C = torch.zeros((130, 131), dtype=torch.float64, device="cuda")
+    g.op_product(_dev(A), _dev(Bt), C, nslice=fmt[0], max_order=fmt[1], slice_bits=fmt[2])
+    torch.cuda.synchronize()
+    _check_product(C.cpu().numpy(), A, Bt, 4.0 * FORMATS[fmt])
+
+
 @pytest.mark.parametrize("fmt", [(0, 0, 12), (3, 3, 12), (2, 1, 12), (4, 3, 9)])
 @pytest.mark.parametrize("n", [128, 300, 515])
 def test_symmetric_product_is_exactly_symmetric(g, fmt, n):

@@ -30,8 +30,8 @@
 // quarter (32*(warp%4) ...), each covering 64 of the 128 columns; a warp reads all of its
 // accumulator columns into int64 registers first and releases TMEM, so that the conversion and
 // the stores overlap the next tile's MMAs.  Formats with at most two orders keep two
-// accumulator sets in TMEM (the MMAs never wait for the epilogue); with one set, the tiles of
-// the last, partial wave are split along k (sliced_gemm).  Symmetric mode computes only tiles
+// accumulator sets in TMEM (the MMAs never wait for the epilogue); the tiles of the last,
+// partial wave are split along k (sliced_gemm).  Symmetric mode computes only tiles
 // on or above the diagonal and writes the mirror image.
 #include <atomic>
 #include <cstdio>
@@ -712,11 +712,7 @@ cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& B, const Precision& p
   args.full_tiles = ntiles;
   const int sms = device_sms();
   const int nk = (args.K + bk - 1) / bk;
-  // Only for formats with one accumulator set (three or more orders): with two sets the
-  // epilogue already overlaps the next tile's MMAs, and the parts' extra epilogue work costs more
-  // than the shorter tail saves (measured on the two-slice Newton-Schulz products).
-  const bool one_acc_set = args.nacc * kBN * 2 > args.tmem_cols;
-  if (one_acc_set && args.splitk_ws != nullptr && args.splitk_cnt != nullptr &&
+  if (args.splitk_ws != nullptr && args.splitk_cnt != nullptr &&
       args.mask_a == nullptr && args.mask_b == nullptr) {
     const int tail = ntiles % sms;
     int sp = tail > 0 ? sms / tail : 1;

@@ -1,8 +1,10 @@
 // Memory-bound kernels of the density-matrix route: forming + slicing, Gershgorin bounds,
 // the TRS4 trace reductions and controller, dot products, symmetrisation.
 //
-// All of them stream n x n FP64 matrices once (or twice for forming + slicing, the second
-// pass hitting L1/L2); rows map to blocks or warps so every global access is coalesced.
+// All of them stream n x n FP64 matrices once.  Rows of up to kFusedMaxCols columns map to one
+// block each, with every load of the row in flight at once and the row kept in registers for
+// the later steps (norm, slices); wider or unaligned rows take the warp-per-row and two-pass
+// kernels.  Every global access is coalesced.
 #include <cmath>
 
 #include "common.cuh"
@@ -1185,7 +1187,8 @@ __global__ void minmax_reduce_kernel(const double* partials, int nblocks, double
 }
 
 // ------------------------------------------------------------------------------------------
-// TRS4 traces, one warp per row
+// TRS4 traces, one warp per row (rows that slice_traces_kernel does not take: odd or wider than
+// kFusedMaxCols, or filtered purification)
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRowsPerBlock * 32)
     trs4_traces_kernel(const double* __restrict__ X, const double* __restrict__ X2, int64_t ld,

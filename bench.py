@@ -5,10 +5,13 @@ A step is one cold solve of the whole route on a resident (H, S) pair: gdm_reini
 Newton-Schulz + refinement for Z, H~ = Z^T H Z, Gershgorin bounds, TRS4 purification,
 back-transform, Tr(P S) / Tr(P H), P written to device memory.  Default workload: the dense
 all-electron-like insulator (n = 4096, n_occ = 1024, cond(S) = 1e3, gap 0.2), synthetic inputs
-from `workloads`.  Multi-GPU: one process per GPU, independent problems per rank (replicas, no
-collective in the data path), value = all solves / max-over-ranks time.
+from `workloads`.  The default line also carries sub-records for the DFTB-like n = 8192 system,
+the 64-problem batch and the serving stream (--no-subrecords leaves them out).  Multi-GPU: one
+process per GPU, independent problems per rank (replicas, no collective in the data path),
+value = all solves / max-over-ranks time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --peaks        # GEMM peaks per dtype (torch.matmul, 8192^3) as one JSON line
 """
 from __future__ import annotations
 
@@ -60,17 +63,21 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="config1")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--no-fp64-ref", action="store_true", help="skip the all-FP64 GPU solve")
+    ap.add_argument("--no-fp64-ref", action="store_true", help="skip the all-FP64 GPU solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--truncation", type=float, default=0.0,
                     help="threshold filtering of the purification (0: off)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the TRS2 / canonical purification solves")
+    ap.add_argument("--no-subrecords", action="store_true",
+                    help="config1 line without the config2 / config3 / config4 sub-records")
     ap.add_argument("--concurrency", type=int, default=4, help="batch / server worker count")
-    ap.add_argument("--requests", type=int, default=200, help="config4: requests per phase")
+    ap.add_argument("--requests", type=int, default=120, help="config4: requests per phase")
     ap.add_argument("--rate", type=float, default=200.0, help="config4: offered req/s")
     ap.add_argument("--cache", default="/tmp/gdm_bench_inputs",
                     help="directory for generated inputs ('' disables)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure torch.matmul peaks per dtype at 8192^3 and exit")
     return ap.parse_args()
 
 
@@ -141,41 +148,25 @@ def job_throughput(units_per_rank, total_ms_this_rank, device="cpu"):
 PHASES = ("newton_schulz", "refine", "transform", "purify")
 
 # DRAM bytes (read + write) per purification product launch at n=4096 from one ncu capture of
-# the current sliced_gemm_kernel<3,64,2> (average of X X and X^2 W: 371.2 and 489.4 MB).
-PURIFY_TRAFFIC_N4096 = 430.3e6
-
-
-def traffic_bytes(n):
-    if PURIFY_TRAFFIC_N4096 is None or n != 4096:
-        return None
-    return PURIFY_TRAFFIC_N4096
+# sliced_gemm_kernel<3,64,2> (profiles/sliced_gemm_purify_n4096.md: X X 371.2 MB, X^2 W 489.4 MB)
+# and the capture's tensor-pipe activity (share of active cycles).
+PURIFY_NCU_N4096 = dict(traffic=430.3e6, tensor_pipe_active=0.766,
+                        source="profiles/sliced_gemm_purify_n4096.md")
 
 
 def measured_peaks():
     """Roofline denominators: MEASURED_PEAKS.json when present, else the machine's fallback."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     out = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0,
-               source="fallback")
+               source="fallback", peak_sm_mhz=None)
     try:
         with open(path) as f:
             d = json.load(f)
-
-        def find(keys, default):
-            for k, v in d.items():
-                kl = k.lower()
-                if all(s in kl for s in keys) and isinstance(v, (int, float)):
-                    return float(v)
-            return default
-        out["hbm_gbs"] = find(["hbm"], out["hbm_gbs"])
-        sus = find(["bf16", "sustain"], None)
-        burst = None
-        for k, v in d.items():
-            if "bf16" in k.lower() and "sustain" not in k.lower() and isinstance(v, (int, float)):
-                burst = float(v)
-        if burst:
-            out["bf16_tflops"] = burst
-        if sus:
-            out["bf16_tflops_sustained"] = sus
+        out["hbm_gbs"] = float(d.get("hbm_gbs", out["hbm_gbs"]))
+        out["bf16_tflops"] = float(d.get("bf16_tflops", out["bf16_tflops"]))
+        out["bf16_tflops_sustained"] = float(d.get("bf16_tflops_sustained",
+                                                   out["bf16_tflops_sustained"]))
+        out["peak_sm_mhz"] = (d.get("clocks_under_load") or {}).get("sm_mhz_median")
         out["source"] = "measured"
     except Exception:
         pass
@@ -238,54 +229,137 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def pct(vals, q):
+    s = sorted(vals)
+    return s[min(len(s) - 1, max(0, int(math.ceil(q * len(s))) - 1))]
+
+
+def rel_err(P, Pref):
+    import torch
+    return float(torch.linalg.norm(P - Pref) / torch.linalg.norm(Pref))
+
+
+def closed_form_gpu(p, torch, np):
+    """Closed form of a constructed input on the device (cuBLAS FP64):
+    C = S^{-1/2} Q_occ, P = C C^T, E = sum lam_occ."""
+    U = torch.from_numpy(p.factors["S_U"]).cuda()
+    sw = torch.from_numpy(p.factors["S_w"]).cuda()
+    Qo = torch.from_numpy(np.ascontiguousarray(p.factors["Q"][:, :p.n_occ])).cuda()
+    C = (U * sw.rsqrt()[None, :]) @ (U.T @ Qo)
+    return C @ C.T, float(np.sum(p.factors["lam"][:p.n_occ]))
+
+
 # ------------------------------------------------------------------------------------------
-# CPU oracle baseline (bounded sample)
+# GEMM peaks per dtype (one-off measurement)
 # ------------------------------------------------------------------------------------------
 
-def cpu_baseline_sample(workload, n_sample=512):
-    """Time the FP64 CPU oracle (Jacobi) on the same recipe at n_sample and scale to the
-    workload's n by the O(n^3) cost; returns (solves/s, seconds of the sample, cores)."""
-    import oracle
-    import workloads
-    w = WORKLOADS[workload]
-    n, n_occ = w["n"], w["n_occ"]
-    ns = min(n_sample, n)
-    occ = max(1, int(round(ns * n_occ / n)))
-    if workload == "config1":
-        p = workloads.make_spectrum_problem(101, ns, occ, cond_S=1e3, gap=0.2)
-    elif workload == "config2":
-        p = workloads.make_config2(102, n=ns, n_occ=occ)
-    else:
-        p = workloads.make_config0(seed=103, n=ns, n_occ=occ)
+def run_peaks(args):
+    import torch
+    torch.cuda.set_device(0)
+    n = 8192
+    out = {"what": "torch.matmul %d^3 (2 n^3 flops), best of 10 after 3 warm-up, CUDA events"
+                   % n}
+    cases = [("bf16", torch.bfloat16, False), ("fp16", torch.float16, False),
+             ("tf32", torch.float32, True), ("fp32", torch.float32, False),
+             ("fp64", torch.float64, False)]
+    sampler = ClockSampler(0)
+    sampler.start()
+    for name, dt, tf32 in cases:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda").to(dt)
+        b = torch.randn(n, n, device="cuda").to(dt)
+        reps = 3 if dt == torch.float64 else 10
+        for _ in range(2):
+            a @ b
+        best = float("inf")
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out[name + "_tflops"] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+        del a, b
+    try:
+        a = torch.randint(-8, 8, (n, n), device="cuda", dtype=torch.int8)
+        b = torch.randint(-8, 8, (n, n), device="cuda", dtype=torch.int8)
+        torch._int_mm(a, b.t().contiguous())
+        best = float("inf")
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch._int_mm(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out["int8_tops"] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+    except Exception as e:  # not every build exposes an int8 GEMM
+        out["int8_tops"] = None
+        out["int8_note"] = str(e)[:120]
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out["clocks"] = sampler.stop()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle: the reference arm and the cpu_baseline
+# ------------------------------------------------------------------------------------------
+
+ORACLE_SAMPLE = ("one full solve of the CPU oracle's LAPACK statement of the definition "
+                 "(eigh of S, Z = S^-1/2, H~ = Z H Z, eigh of H~, P = C_occ C_occ^T; numpy "
+                 "float64) on the benchmark's own input at n=%d")
+
+
+def oracle_solve(p):
+    """One full oracle solve of problem p; returns (result dict, seconds, BLAS threads)."""
+    from oracle.lapack import blas_threads, density_matrix_eigh
     t0 = time.perf_counter()
-    r = oracle.density_matrix(p.H, p.S, p.n_occ)
+    r = density_matrix_eigh(p.H, p.S, p.n_occ)
     dt = time.perf_counter() - t0
-    assert r["status"] == "OK", r["status"]
-    scale = (n / ns) ** 3
-    return 1.0 / (dt * scale), dt, oracle.num_threads(), ns
+    if r["status"] != "OK":
+        raise RuntimeError("oracle status %s" % r["status"])
+    return r, dt, blas_threads()
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, solving the same input as our arm,
+    one full solve per step."""
     rank, world, local = dist_info()
     if rank != 0:
         return 0
     w = WORKLOADS[args.workload]
-    vals = []
+    if args.workload in ("config3", "config4"):
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the reference arm runs the single-solve workloads (config0-2)"}))
+        return 0
+    device = None
+    try:
+        import torch
+        if torch.cuda.is_available():
+            device = "cuda"  # input generation only; the oracle itself runs on the host
+    except Exception:
+        pass
+    p = make_problem(args.workload, seed=1, device=device, cache_dir=args.cache)
+    times = []
+    cores = None
     for i in range(args.warmup + args.steps):
-        v, dt, cores, ns = cpu_baseline_sample(args.workload)
+        _, dt, cores = oracle_solve(p)
         if i >= args.warmup:
-            vals.append((v, dt))
-    value = statistics.median(v for v, _ in vals)
-    ms = 1e3 / value
-    sample = ("FP64 CPU oracle (cyclic Jacobi of S and H~, P = C_occ C_occ^T) on the %s recipe "
-              "at n=%d per step, scaled by (n/%d)^3 to n=%d" % (args.workload, ns, ns, w["n"]))
+            times.append(dt)
+    total = sum(times)
+    value = args.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["desc"], "n": w["n"], "n_occ": w["n_occ"]},
+            "latency_ms": {"p50": 1e3 * statistics.median(times), "p99": 1e3 * pct(times, 0.99)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": ORACLE_SAMPLE % w["n"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -293,8 +367,135 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------------------
-# our engine
+# the plain all-FP64 chain in torch (cuBLAS DGEMM): a baseline arm, not the product path
 # ------------------------------------------------------------------------------------------
+
+def torch_fp64_route(H, S, n_occ, torch):
+    """The same route with every product a torch.matmul in float64: coupled Newton-Schulz for
+    S^{-1/2} (scale 1.25 x a power-iteration estimate of lambda_max), H~ = Z H Z, Gershgorin
+    bounds, TRS4 (F + gamma G, 2X - X^2, X^2) with the McWeeny endgame once every eigenvalue is
+    within 0.113 of 0 or 1, back-transform.  Returns (P, newton-schulz iterations,
+    purification iterations)."""
+    n = H.shape[0]
+    I = torch.eye(n, dtype=torch.float64, device=H.device)
+    v = torch.ones(n, dtype=torch.float64, device=H.device)
+    for _ in range(12):
+        v = S @ v
+        v = v / torch.linalg.norm(v)
+    c = 1.25 * float(v @ (S @ v))
+    Y, Z = S / c, I.clone()
+    prev, it = float("inf"), 0
+    for it in range(100):
+        M = Z @ Y
+        T = 0.5 * (3.0 * I - M)
+        res = float(torch.linalg.norm(I - M))
+        if res <= 1e-13 * math.sqrt(n) or (res < 1e-2 * math.sqrt(n) and res > 0.5 * prev):
+            break
+        prev = res
+        Y, Z = Y @ T, T @ Z
+    Z = 0.5 * (Z + Z.T) / math.sqrt(c)
+    Ht = Z @ H @ Z
+    Ht = 0.5 * (Ht + Ht.T)
+    d = torch.diagonal(Ht)
+    r = Ht.abs().sum(1) - d.abs()
+    lo, hi = float((d - r).min()), float((d + r).max())
+    X = (hi * I - Ht) / (hi - lo)
+    N = float(n_occ)
+    prev_idem, k = float("inf"), 0
+    for k in range(200):
+        X2 = X @ X
+        t1, t2 = float(torch.trace(X)), float(torch.trace(X2))
+        t3, t4 = float((X2 * X).sum()), float((X2 * X2).sum())
+        idem = t1 - float((X * X).sum())
+        if abs(idem) <= 1e-13 * N or (abs(idem) < 1e-4 * N and abs(idem) > 0.5 * abs(prev_idem)):
+            break
+        prev_idem = idem
+        trG = t2 - 2.0 * t3 + t4
+        if (abs(idem) < 0.1 and abs(t1 - N) < 0.25) or not trG > 1e-14 * N:
+            X = X2 @ (3.0 * I - 2.0 * X)
+        else:
+            g = (N - (4.0 * t3 - 3.0 * t4)) / trG
+            if g > 6.0:
+                X = 2.0 * X - X2
+            elif g < 0.0:
+                X = X2
+            else:
+                X = X2 @ (g * I + (4.0 - 2.0 * g) * X + (g - 3.0) * X2)
+        X = 0.5 * (X + X.T)
+    X = X * (N / float(torch.trace(X)))
+    P = Z @ X @ Z
+    return 0.5 * (P + P.T), it, k
+
+
+# ------------------------------------------------------------------------------------------
+# our engine: one workload, timed
+# ------------------------------------------------------------------------------------------
+
+def timed_solves(g, torch, h, S, H, P, stream, warmup, steps):
+    """warmup + steps cold solves on `stream`; returns (per-step ms, total ms, last outputs)."""
+    def step():
+        h.reinit()
+        h.set_overlap(S)
+        h.set_hamiltonian(H)
+        return h.solve(P)
+
+    out = None
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            out = step()
+    torch.cuda.synchronize()
+    for kind in range(6):
+        h.profile(kind, reset=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    with torch.cuda.stream(stream):
+        evs[0].record(stream)
+        for k in range(steps):
+            out = step()
+            evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+    return per, evs[0].elapsed_time(evs[-1]), out
+
+
+def phase_profile(h, steps, n):
+    """Per phase of the route: launches, device ms, issued and algorithmic TFLOP/s per solve."""
+    out = {}
+    for ph, name in enumerate(PHASES):
+        l, ms, fl, al = h.profile(2 + ph, algorithmic=True)
+        out[name] = {"launches_per_step": l / steps, "ms_per_step": ms / steps,
+                     "tflops_issued": (fl / (ms / 1e3)) / 1e12 if ms > 0 else 0.0,
+                     "tflops_algorithmic": (al / (ms / 1e3)) / 1e12 if ms > 0 else 0.0,
+                     "issued_per_algorithmic": fl / al if al > 0 else None}
+    return out
+
+
+def roofline_record(h, steps, n, peaks, sm_mhz):
+    """Roofline of the dominant kernel, the purification products (sliced_gemm_kernel<3,64,2>,
+    X X and X^2 W, both symmetric): algorithmic work n^3 per launch (the route's count, upper
+    triangle only) over the launches' live CUDA-event time on the handle's stream."""
+    l, ms, fl, al = h.profile(2 + PHASES.index("purify"), algorithmic=True)
+    if l == 0 or ms <= 0:
+        return None
+    sec = ms / 1e3
+    peak = peaks["bf16_tflops_sustained"]
+    achieved = al / sec / 1e12
+    issued = fl / sec / 1e12
+    ncu = PURIFY_NCU_N4096 if n == 4096 else None
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": ncu["traffic"] if ncu else None,
+            "kernel": "sliced_gemm_kernel<3,64,2>: TRS4 products X X and X^2 W (tcgen05 "
+                      "kind::f16, 3 FP16 slices, 8 slice pairs as 5 MMAs per k-step, "
+                      "upper-triangle tiles)",
+            "algorithmic_flops_per_launch": al / l, "ms_per_launch": ms / l,
+            "launches_per_step": l / steps,
+            "issued_tflops": issued, "issued_frac": issued / peak,
+            "issued_per_algorithmic": fl / al,
+            "ncu_tensor_pipe_active": ncu["tensor_pipe_active"] if ncu else None,
+            "ncu_source": ncu["source"] if ncu else None,
+            "peak_source": "%s bf16 sustained (fp16 runs at the bf16 rate); peak measured at a "
+                           "median SM clock of %s MHz, this run at %s MHz"
+                           % (peaks["source"], peaks["peak_sm_mhz"], sm_mhz)}
+
 
 def run_ours(args):
     import numpy as np
@@ -313,14 +514,7 @@ def run_ours(args):
     H = torch.from_numpy(p.H).cuda()
     S = torch.from_numpy(p.S).cuda()
     P = torch.empty_like(H)
-    # closed form of the construction (H C = S C Lambda with C = S^{-1/2} Q): accuracy report
-    U = torch.from_numpy(p.factors["S_U"]).cuda()
-    sw = torch.from_numpy(p.factors["S_w"]).cuda()
-    Qo = torch.from_numpy(np.ascontiguousarray(p.factors["Q"][:, :n_occ])).cuda()
-    C = (U * sw.rsqrt()[None, :]) @ (U.T @ Qo)
-    Pc = C @ C.T
-    Ec = float(np.sum(p.factors["lam"][:n_occ]))
-    del U, sw, Qo, C
+    Pc, Ec = closed_form_gpu(p, torch, np)
 
     stream = torch.cuda.Stream()
     h = g.Handle(n, n_occ, device=local)
@@ -329,44 +523,27 @@ def run_ours(args):
     if args.truncation > 0.0:
         h.set_truncation(args.truncation)
 
-    def step():
-        h.reinit()
-        h.set_overlap(S)
-        h.set_hamiltonian(H)
-        return h.solve(P)
-
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            _, e, info, st = step()
-    torch.cuda.synchronize()
-    for kind in range(6):
-        h.profile(kind, reset=True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = g.gdm_launch_count()
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    with torch.cuda.stream(stream):
-        evs[0].record(stream)
-        for k in range(args.steps):
-            _, e, info, st = step()
-            evs[k + 1].record(stream)
-    torch.cuda.synchronize()
+    per, total_ms, (_, e, info, st) = timed_solves(g, torch, h, S, H, P, stream, args.warmup,
+                                                   args.steps)
     launches = g.gdm_launch_count() - launches0
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    prof_launch, prof_ms, prof_flops = h.profile(0)
-    phase_prof = {name: h.profile(2 + ph) for ph, name in enumerate(PHASES)}
     value, total_ms = job_throughput(args.steps, total_ms, device="cuda")
-
-    # accuracy of the last timed solve
-    relerr = float(torch.linalg.norm(P - Pc) / torch.linalg.norm(Pc))
+    _, prof_ms, prof_flops, prof_alg = h.profile(0, algorithmic=True)
+    per_phase = phase_profile(h, args.steps, n)
+    peaks = measured_peaks()
+    roof = roofline_record(h, args.steps, n, peaks, clocks["sm_mhz"] if clocks else None)
+    relerr = rel_err(P, Pc)
+    alg_per_solve = prof_alg / args.steps
+    P_last = P.cpu().numpy()  # the last timed solve's result (P is reused below)
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     Hh = torch.from_numpy(p.H).pin_memory()
@@ -389,7 +566,7 @@ def run_ours(args):
     h2.close()
     e2e_val = world / e2e_s if world > 1 else 1.0 / e2e_s
 
-    # all-FP64 GPU path on the same input (one solve) for the mixed / FP64 comparison
+    # all-FP64 GPU paths on the same input: this library's FP64 kernel and torch.matmul (cuBLAS)
     fp64 = None
     if not args.no_fp64_ref and rank == 0:
         h3 = g.Handle(n, n_occ, device=local)
@@ -401,12 +578,23 @@ def run_ours(args):
         t0 = time.perf_counter()
         _, e3, info3, st3 = h3.solve(P3)
         torch.cuda.synchronize()
-        fp64_s = time.perf_counter() - t0
-        fp64 = {"s_per_solve": fp64_s,
-                "rel_err": float(torch.linalg.norm(P3 - Pc) / torch.linalg.norm(Pc)),
-                "mixed_speedup": fp64_s / (total_ms / args.steps / 1e3)}
+        own_s = time.perf_counter() - t0
+        own_err = rel_err(P3, Pc)
         h3.close()
         del P3
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P4, ns4, it4 = torch_fp64_route(H, S, n_occ, torch)
+        torch.cuda.synchronize()
+        torch_s = time.perf_counter() - t0
+        torch_err = rel_err(P4, Pc)
+        del P4
+        mixed_s = total_ms / args.steps / 1e3
+        fp64 = {"own_kernel": {"s_per_solve": own_s, "rel_err": own_err},
+                "torch_matmul_f64": {"s_per_solve": torch_s, "rel_err": torch_err,
+                                     "ns_iters": ns4, "purif_iters": it4},
+                "faster_fp64_s_per_solve": min(own_s, torch_s),
+                "mixed_speedup": min(own_s, torch_s) / mixed_s}
 
     # the other purification maps of the paper (Sec. 2.2.2) on the same input and harness
     variants = None
@@ -416,46 +604,40 @@ def run_ours(args):
             hv = g.Handle(n, n_occ, device=local)
             hv.set_stream(stream)
             hv.set_purification(code)
-            times = []
-            with torch.cuda.stream(stream):
-                for k in range(3):
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    hv.reinit()
-                    hv.set_overlap(S)
-                    hv.set_hamiltonian(H)
-                    _, ev, infov, stv = hv.solve(P)
-                    e1.record(stream)
-                    torch.cuda.synchronize()
-                    if k > 0:
-                        times.append(e0.elapsed_time(e1))
-            variants[name] = {
-                "ms_per_solve": sum(times) / len(times), "purif_iters": infov["purif_iters"],
-                "rel_frobenius_err": float(torch.linalg.norm(P - Pc) / torch.linalg.norm(Pc)),
-                "trace_err": infov["trace_err"], "status": stv}
+            pv, _, (_, ev, infov, stv) = timed_solves(g, torch, hv, S, H, P, stream, 1, 2)
+            variants[name] = {"ms_per_solve": sum(pv) / len(pv),
+                              "purif_iters": infov["purif_iters"],
+                              "rel_frobenius_err": rel_err(P, Pc),
+                              "trace_err": infov["trace_err"], "status": stv}
             hv.close()
         variants["trs4"] = {"ms_per_solve": total_ms / args.steps,
                             "purif_iters": info["purif_iters"], "rel_frobenius_err": relerr,
                             "trace_err": info["trace_err"], "status": st}
 
-    peaks = measured_peaks()
-    peak = peaks["bf16_tflops_sustained"]
-    achieved = (prof_flops / (prof_ms / 1e3)) / 1e12 if prof_ms > 0 else 0.0
-    # the roofline's kernel: the purification products (sliced_gemm_kernel<3,32,4>), the
-    # largest share of the step's device time
-    pl, pms, pfl = phase_prof["purify"]
-    achieved_pu = (pfl / (pms / 1e3)) / 1e12 if pms > 0 else 0.0
-    per_phase = {name: {"launches_per_step": l / args.steps, "ms_per_step": ms / args.steps,
-                        "tflops": (fl / (ms / 1e3)) / 1e12 if ms > 0 else 0.0}
-                 for name, (l, ms, fl) in phase_prof.items()}
-    cpu = None
+    # the CPU oracle: one full solve of the same input (timed on the host cores) and the parity
+    # of the last timed GPU solve against it
+    cpu, oracle_err = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt, cores, ns = cpu_baseline_sample(args.workload)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "FP64 CPU oracle (cyclic Jacobi) on the same recipe at n=%d (%.1f s), "
-                         "scaled by (%d/%d)^3" % (ns, dt, n, ns)}
-    per_sorted = sorted(per)
+        r, dt, cores = oracle_solve(p)
+        oracle_err = float(np.linalg.norm(P_last - r["P"]) / np.linalg.norm(r["P"]))
+        cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": (ORACLE_SAMPLE % n) + " (%.1f s)" % dt}
+
+    sub = {}
+    if args.workload == "config1" and not args.no_subrecords and rank == 0 and world == 1:
+        h.close()
+        del H, S, P, Pc
+        torch.cuda.empty_cache()
+        for name, fn in (("config2", config2_record), ("config3", batch_record),
+                         ("config4", serving_record)):
+            try:
+                sub[name] = fn(args, local)
+            except Exception as ex:  # a failed sub-record must not lose the main line
+                sub[name] = {"error": "%s: %s" % (type(ex).__name__, str(ex)[:200])}
+            torch.cuda.empty_cache()
+    else:
+        h.close()
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -466,28 +648,22 @@ def run_ours(args):
                            "TRS4, back-transform, Tr(PS), Tr(PH)",
                    "l2": "inputs larger than L2 (H and S %.0f MB each)" % (n * n * 8 / 1e6),
                    "parallelism": "replicas x%d" % world},
-        "latency_ms": {"p50": per_sorted[len(per) // 2],
-                       "p99": per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)]},
-        "accuracy": {"rel_frobenius_err": relerr, "abs_energy_err": abs(e - Ec),
+        "latency_ms": {"p50": statistics.median(per), "p99": pct(per, 0.99)},
+        "accuracy": {"rel_frobenius_err": relerr, "rel_frobenius_err_vs_oracle": oracle_err,
+                     "abs_energy_err": abs(e - Ec), "rel_energy_err": abs(e - Ec) / abs(Ec),
                      "trace_err": info["trace_err"], "trace_err_raw": info["trace_err_raw"],
                      "truncation": args.truncation,
                      "kstage_fraction": info["kstage_fraction"],
                      "ns_iters": info["ns_iters"], "refine_iters": info["refine_iters"],
                      "z_err": info["z_err"], "idem_err": info["idem_err"],
                      "purif_iters": info["purif_iters"]},
-        "tflops_tensor_pipe": achieved,
-        "gemm_ms_per_step": prof_ms / args.steps,
+        "tflops": {"algorithmic_per_solve": alg_per_solve,
+                   "algorithmic": alg_per_solve / (total_ms / args.steps / 1e3) / 1e12,
+                   "gemm_algorithmic": (prof_alg / (prof_ms / 1e3)) / 1e12 if prof_ms else None,
+                   "gemm_issued": (prof_flops / (prof_ms / 1e3)) / 1e12 if prof_ms else None,
+                   "gemm_ms_per_step": prof_ms / args.steps},
         "gemm_by_phase": per_phase,
-        "roofline": {"bound": "tensor", "achieved": achieved_pu, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved_pu / peak if peak else None,
-                     "traffic": traffic_bytes(n),
-                     "kernel": "sliced_gemm_kernel<3,64,2>: TRS4 products X X and X^2 W "
-                               "(tcgen05 kind::f16, 8 slice pairs as 5 MMAs per k-step, "
-                               "upper-triangle tiles)",
-                     "flops_per_launch": pfl / pl if pl else None,
-                     "ms_per_launch": pms / pl if pl else None,
-                     "peak_source": "%s bf16 sustained (fp16 = bf16 rate)" % peaks["source"],
-                     "launches_per_step": pl / args.steps},
+        "roofline": roof,
         "fp64_gpu_path": fp64,
         "purification_variants": variants,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * n * n * 8,
@@ -496,7 +672,7 @@ def run_ours(args):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
-    h.close()
+    line.update(sub)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -504,35 +680,70 @@ def run_ours(args):
     return 0
 
 
-def _closed_form_gpu(p, torch, np):
-    U = torch.from_numpy(p.factors["S_U"]).cuda()
-    sw = torch.from_numpy(p.factors["S_w"]).cuda()
-    Qo = torch.from_numpy(np.ascontiguousarray(p.factors["Q"][:, :p.n_occ])).cuda()
-    C = (U * sw.rsqrt()[None, :]) @ (U.T @ Qo)
-    return C @ C.T, float(np.sum(p.factors["lam"][:p.n_occ]))
+# ------------------------------------------------------------------------------------------
+# sub-records: config2 (n = 8192), config3 (batch), config4 (serving)
+# ------------------------------------------------------------------------------------------
+
+def config2_record(args, local, steps=3, warmup=2):
+    """The DFTB-like n = 8192 system: cold solves on resident inputs, algorithmic and issued
+    tensor rates, the purification products' share of the measured peak, error against the
+    closed form."""
+    import numpy as np
+    import torch
+    import paper_1912_13403_gb300 as g
+    w = WORKLOADS["config2"]
+    p = make_problem("config2", seed=1, device="cuda", cache_dir=None)
+    H = torch.from_numpy(p.H).cuda()
+    S = torch.from_numpy(p.S).cuda()
+    P = torch.empty_like(H)
+    Pc, Ec = closed_form_gpu(p, torch, np)
+    stream = torch.cuda.Stream()
+    h = g.Handle(w["n"], w["n_occ"], device=local)
+    h.set_stream(stream)
+    h.set_profiling(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    per, total_ms, (_, e, info, st) = timed_solves(g, torch, h, S, H, P, stream, warmup, steps)
+    clocks = sampler.stop()
+    _, prof_ms, prof_flops, prof_alg = h.profile(0, algorithmic=True)
+    peaks = measured_peaks()
+    roof = roofline_record(h, steps, w["n"], peaks, clocks["sm_mhz"] if clocks else None)
+    rec = {"workload": w["desc"], "status": st, "steps": steps, "warmup": warmup,
+           "solves_per_s": steps / (total_ms / 1e3),
+           "latency_ms": {"p50": statistics.median(per), "p99": pct(per, 0.99)},
+           "rel_frobenius_err": rel_err(P, Pc), "rel_energy_err": abs(e - Ec) / abs(Ec),
+           "trace_err": info["trace_err"], "trace_err_raw": info["trace_err_raw"],
+           "ns_iters": info["ns_iters"], "purif_iters": info["purif_iters"],
+           "tflops_algorithmic": prof_alg / steps / (total_ms / steps / 1e3) / 1e12,
+           "gemm_tflops_issued": (prof_flops / (prof_ms / 1e3)) / 1e12 if prof_ms else None,
+           "gemm_by_phase": phase_profile(h, steps, w["n"]),
+           "purify_roofline": roof, "clocks": clocks}
+    h.close()
+    return rec
 
 
-def run_batch(args):
+def batch_record(args, local, steps=None, warmup=None):
     """config3: every step is one gdm_solve_batch over the 64 resident problems."""
     import numpy as np
     import torch
     import paper_1912_13403_gb300 as g
     import workloads
+    steps = steps or (args.steps if args.workload == "config3" else 3)
+    warmup = warmup or (args.warmup if args.workload == "config3" else 1)
     rank, world, local = dist_info()
-    torch.cuda.set_device(local)
     probs = workloads.make_batch_config3(seed=3 + 100 * rank, device="cuda")
     items = []
     for p in probs:
         items.append((torch.from_numpy(p.H).cuda(), torch.from_numpy(p.S).cuda(), p.n_occ,
                       torch.empty((p.n, p.n), dtype=torch.float64, device="cuda")))
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         st, res = g.solve_batch(items, concurrency=args.concurrency, device=local)
     torch.cuda.synchronize()
     launches0 = g.gdm_launch_count()
     sampler = ClockSampler(local)
     sampler.start()
     times = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         t0 = time.perf_counter()
         st, res = g.solve_batch(items, concurrency=args.concurrency, device=local)
         torch.cuda.synchronize()
@@ -541,47 +752,40 @@ def run_batch(args):
     launches = g.gdm_launch_count() - launches0
     errs, tr = [], []
     for p, it, r in zip(probs, items, res):
-        Pc, Ec = _closed_form_gpu(p, torch, np)
-        errs.append(float(torch.linalg.norm(it[3] - Pc) / torch.linalg.norm(Pc)))
-        tr.append(r["info"]["trace_err_raw"])
+        Pc, Ec = closed_form_gpu(p, torch, np)
+        errs.append(rel_err(it[3], Pc))
+        tr.append(r["info"]["trace_err"])
     total = sum(times)
-    value = world * len(probs) * args.steps / total
-    flops = sum(4.0 * p.n ** 3 for p in probs)  # nominal FP64-equivalent work per problem
-    lat = sorted(r["latency_ms"] for r in res)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16-slices(f32-acc)+f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS["config3"]["desc"], "problems": len(probs),
-                       "n_range": [min(p.n for p in probs), max(p.n for p in probs)],
-                       "concurrency": args.concurrency, "status": st},
-            "latency_ms_per_problem": {"p50": lat[len(lat) // 2], "p99": lat[-1]},
-            "accuracy": {"max_rel_frobenius_err": max(errs), "max_trace_err_raw": max(tr)},
+    lat = [r["latency_ms"] for r in res]
+    return {"workload": WORKLOADS["config3"]["desc"], "status": st, "steps": steps,
+            "warmup": warmup, "problems": len(probs),
+            "n_range": [min(p.n for p in probs), max(p.n for p in probs)],
+            "concurrency": args.concurrency,
+            "solves_per_s": world * len(probs) * steps / total,
+            "ms_per_batch": 1e3 * total / steps,
+            "latency_ms_per_problem": {"p50": statistics.median(lat), "p99": pct(lat, 0.99)},
+            "max_rel_frobenius_err": max(errs), "max_trace_err": max(tr),
             "gpu_launches": launches, "clocks": clocks}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
 
 
-def run_serving(args):
+def serving_record(args, local):
     """config4: Poisson arrivals at --rate req/s, then at 70% of the measured capacity."""
     import numpy as np
     import torch
     import paper_1912_13403_gb300 as g
     import workloads
     rank, world, local = dist_info()
-    torch.cuda.set_device(local)
     reqs = workloads.make_request_stream(seed=4 + 100 * rank, count=args.requests,
                                          rate=args.rate)
     # a pool of distinct inputs from the request recipe (sizes spread over the range); each
-    # request uses the pool member closest to its own size class
+    # request uses the pool member closest to its own size
     sizes = sorted({int(round(256 * 32 ** (k / 11.0))) for k in range(12)})
     pool = []
     for k, n in enumerate(sizes):
         q = workloads.make_request_problem(dict(seed=4000 + k, n=n, n_occ=int(round(0.25 * n)),
                                                 gap=0.2), device="cuda")
         pool.append((torch.from_numpy(q.H).pin_memory(), torch.from_numpy(q.S).pin_memory(),
-                     q.n_occ, n))
+                     q.n_occ, n, q))
 
     def pick(n):
         return min(pool, key=lambda it: abs(math.log(it[3]) - math.log(n)))
@@ -601,14 +805,13 @@ def run_serving(args):
         res = [(srv.wait(t, -1.0), lag) for t, lag in tickets]
         wall = time.perf_counter() - t0
         srv.close()
-        lat = sorted(r["latency_ms"] + 1e3 * lag for r, lag in res)
+        lat = [r["latency_ms"] + 1e3 * lag for r, lag in res]
         ok = sum(1 for r, _ in res if r["status"] == g.GDM_OK)
         return {"requests": len(res), "ok": ok, "wall_s": wall, "throughput": len(res) / wall,
-                "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1,
-                                                               int(0.99 * len(lat)))]}
+                "offered_rate": len(arrivals) / max(arrivals[-1][0], 1e-9),
+                "p50_ms": statistics.median(lat), "p99_ms": pct(lat, 0.99)}
 
-    warm = [(0.0, dict(n=n)) for n in sizes]
-    phase(warm)
+    phase([(0.0, dict(n=n)) for n in sizes])  # warm-up: one request per size
     stated = phase([(r["arrival_s"], r) for r in reqs])
     cap = stated["throughput"]
     rng = np.random.default_rng(44)
@@ -617,26 +820,40 @@ def run_serving(args):
         t += rng.exponential(1.0 / (0.7 * cap))
         arr.append((t, r))
     relaxed = phase(arr)
-    line = {"metric": METRIC, "value": stated["throughput"], "unit": UNIT, "n_gpus": world,
-            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * stated["wall_s"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16-slices(f32-acc)+f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS["config4"]["desc"], "offered_rate": args.rate,
-                       "slots": args.concurrency, "input_pool": sizes},
-            "serving_stated_load": stated, "serving_70pct_capacity": relaxed}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
+    # accuracy of each pool member served alone (the server's results equal solo solves; see
+    # tests/test_gpu_batch_server.py)
+    errs = []
+    for Hh, Sh, n_occ, n, q in pool:
+        Pc, _ = closed_form_gpu(q, torch, np)
+        errs.append(rel_err(outs[n].cuda(), Pc))
+    return {"workload": WORKLOADS["config4"]["desc"], "offered_rate": args.rate,
+            "slots": args.concurrency, "input_pool_sizes": sizes,
+            "stated_load": stated, "at_70pct_of_capacity": relaxed,
+            "max_rel_frobenius_err": max(errs)}
 
 
 def main():
     args = parse()
+    if args.peaks:
+        return run_peaks(args)
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "config3":
-        return run_batch(args)
-    if args.workload == "config4":
-        return run_serving(args)
+    if args.workload in ("config3", "config4"):
+        import torch
+        rank, world, local = dist_info()
+        torch.cuda.set_device(local)
+        rec = (batch_record if args.workload == "config3" else serving_record)(args, local)
+        value = rec["solves_per_s"] if args.workload == "config3" else \
+            rec["stated_load"]["throughput"]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f16-slices(f32-acc)+f64", "data": "synthetic",
+                "config": {"workload": WORKLOADS[args.workload]["desc"]}}
+        line.update(rec)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return 0
     return run_ours(args)
 
 

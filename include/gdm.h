@@ -101,8 +101,10 @@ typedef struct {
 } gdm_info;
 
 /* Create a handle for n_basis x n_basis problems with n_occ occupied states (f_l in {0,1})
- * on CUDA device `device`.  Allocates the device workspace (about 14 * 8 * n^2 bytes; 0.9 GB
- * at n = 2048, 15 GB at n = 8192).  Requires 1 <= n_basis, 0 < n_occ < n_basis.  Errors:
+ * on CUDA device `device`.  Allocates the device workspace in one piece: ten n x ld FP64
+ * matrices and eight slice buffers of 4 x n x ld FP16 (ld = n rounded up to 64), about 144 n^2
+ * bytes, plus 21 MB of split-k workspace (0.63 GB at n = 2048, 2.4 GB at n = 4096, 9.7 GB at
+ * n = 8192).  Requires 1 <= n_basis <= 65536, 0 < n_occ < n_basis.  Errors:
  * GDM_ERR_ARG, GDM_ERR_OOM, GDM_ERR_CUDA (no *h is created on error). */
 gdm_status gdm_init(gdm_handle** h, int64_t n_basis, int64_t n_occ, int device);
 
@@ -151,6 +153,12 @@ gdm_status gdm_set_profiling(gdm_handle* h, int enable);
  * reset != 0 zeroes the totals of that kind afterwards. */
 gdm_status gdm_get_profile(gdm_handle* h, int kind, int64_t* launches, double* ms, double* flops,
                            int reset);
+
+/* gdm_get_profile plus the algorithmic work of the same launches in *alg_flops (may be NULL):
+ * n^3 per symmetric product (only its upper triangle is formed) and 2 n^3 per full product,
+ * whatever the slice format - the work the route's roofline is quoted in. */
+gdm_status gdm_get_profile_ex(gdm_handle* h, int kind, int64_t* launches, double* ms,
+                              double* flops, double* alg_flops, int reset);
 
 /* Kernels launched by this library since it was loaded (all handles and threads). */
 int64_t gdm_launch_count(void);

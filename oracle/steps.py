@@ -18,9 +18,9 @@ Each function is the plain numpy statement of one step, in the paper's order:
 The paper's Sec. 2.2.2 also names 2nd-order trace resetting, canonical purification and the
 generalised hole-particle canonical purification, without formulas; `trs2_step` and
 `canonical_step` state the maps of the cited methods that are built, `hole_particle_step` the
-hole-particle form that turns out to coincide with the canonical step.  `trs4_purify_truncated`
-is the sparse regime the same section describes: every matrix entering a product is filtered at
-a threshold (elements below it set to zero).
+hole-particle form that turns out to coincide with the canonical step.  `trs4_filtered_step` and
+`trs4_purify_truncated` are the sparse regime the same section describes: every matrix entering
+a product is filtered at a threshold (elements below it set to zero).
 Closed forms for the synthetic inputs are at the end.  Matrix products are numpy matmul
 (a library primitive); there is no blocking, fusion or reordering beyond the formulas.
 """
@@ -205,52 +205,64 @@ def filter_small(A, tau):
     return np.where(np.abs(A) >= tau, A, 0.0)
 
 
-def trs4_purify_truncated(Ht, n_occ, tau, idem_tol=1e-13, max_iter=200, bounds=None):
-    """TRS4 with threshold filtering of every matrix that enters a product: the initial guess,
-    each X^2 = X X, each W, and each new iterate (X^2 W, 2X - X^2 or X^2) are filtered at tau.
-    Filtering breaks the commutation of X^2 and W, so X^2 W is symmetrised before it is
-    filtered (its antisymmetric part is of the order of tau).
-    The controller follows the engine's reading of the paper: stop when Tr(X - X^2) <= idem_tol N,
-    or when it stops halving below 1e-4 N (keeping the better of the last two iterates); once
-    Tr(X - X^2) < 0.1 and |Tr X - N| < 0.25 the McWeeny step X^2 (3I - 2X) replaces the TRS4
-    step; the final iterate is rescaled to Tr X = N.  tau = 0 is plain TRS4 with this controller.
-    Returns (P~, iterations)."""
-    n = Ht.shape[0]
-    I = np.eye(n)
+def trs4_filtered_step(X, n_occ, tau):
+    """One TRS4 step of the sparse regime: the paper's 4th-order trace-resetting map with every
+    matrix that enters a product filtered at tau.  X (already filtered) enters X X; the product
+    is filtered, and that filtered matrix is X^2 wherever the map uses it.  With
+    F = X^2 (4X - 3X^2) and G = X^2 (I - X)^2 the traces are
+    Tr F = 4 <X^2, X> - 3 ||X^2||^2 and Tr G = Tr X^2 - 2 <X^2, X> + ||X^2||^2, and
+    gamma = (N - Tr F) / Tr G.  Then
+      gamma > 6:  X <- filter(2X - X^2)
+      gamma < 0:  X <- X^2 (already filtered)
+      otherwise:  F + gamma G = X^2 W with W = gamma I + (4 - 2 gamma) X + (gamma - 3) X^2;
+                  W is filtered (it enters the product), X^2 W is formed, symmetrised (the
+                  filtered X^2 and W need not commute) and filtered.
+    Returns (X_next, dict(X2=filtered X^2, gamma, branch, W=filtered W or None))."""
+    n = X.shape[0]
+    X2 = filter_small(X @ X, tau)
+    t2, t3, t4 = float(np.trace(X2)), float(np.sum(X2 * X)), float(np.sum(X2 * X2))
+    trF = 4.0 * t3 - 3.0 * t4
+    trG = t2 - 2.0 * t3 + t4
+    g = (n_occ - trF) / trG if trG != 0.0 else float("inf")
+    info = dict(X2=X2, gamma=g, W=None, trF=trF, trG=trG)
+    if g > 6.0:
+        info["branch"] = "2X-X2"
+        return filter_small(2.0 * X - X2, tau), info
+    if g < 0.0:
+        info["branch"] = "X2"
+        return X2, info
+    W = filter_small(g * np.eye(n) + (4.0 - 2.0 * g) * X + (g - 3.0) * X2, tau)
+    info.update(branch="F+gG", W=W)
+    return filter_small(sym(X2 @ W), tau), info
+
+
+def trs4_purify_truncated(Ht, n_occ, tau, max_iter=200, bounds=None, idem_tol=1e-13):
+    """The filtered TRS4 route from the filtered initial guess (Eq. ntpoly_scale_hamiltonian):
+    `trs4_filtered_step` until the idempotency error e = Tr(X - X^2) (X^2 the filtered square)
+    has not reached a new low for five steps in a row: filtering leaves a floor of the order of
+    the threshold's effect, and steps past it only move X along that floor, so the iterate with
+    the smallest |e| is returned.
+    The loop also ends at e <= idem_tol N, or when Tr G is exactly zero (gamma undefined: X is
+    a projector).  tau = 0 is plain TRS4.  Returns (P~, iterations)."""
     lo, hi = gershgorin_bounds(Ht) if bounds is None else bounds
     X = filter_small(initial_guess(Ht, lo, hi), tau)
-    N = float(n_occ)
-    prev_X, prev_idem = None, np.inf
+    best, best_e = X, np.inf
+    rises = 0
     it = 0
     for it in range(max_iter):
         X2 = filter_small(X @ X, tau)
-        t1, t2 = np.trace(X), np.trace(X2)
-        t3, t4 = np.sum(X2 * X), np.sum(X2 * X2)
-        idem = t1 - np.sum(X * X)
-        if abs(idem) <= idem_tol * N:
-            break
-        if abs(idem) < 1e-4 * N and abs(idem) > 0.5 * abs(prev_idem):
-            if abs(idem) > abs(prev_idem):
-                X = prev_X
-            break
-        prev_X, prev_idem = X, idem
-        trF = 4.0 * t3 - 3.0 * t4
-        trG = t2 - 2.0 * t3 + t4
-        endgame = abs(idem) < 0.1 and abs(t1 - N) < 0.25
-        if endgame or not trG > 1e-12 * N:
-            W = filter_small(3.0 * I - 2.0 * X, tau)
-            X = filter_small(sym(X2 @ W), tau)
-            continue
-        g = (N - trF) / trG
-        if g > 6.0:
-            X = filter_small(2.0 * X - X2, tau)
-        elif g < 0.0:
-            X = X2
+        e = abs(float(np.trace(X) - np.trace(X2)))
+        trG = float(np.trace(X2) - 2.0 * np.sum(X2 * X) + np.sum(X2 * X2))
+        if e < best_e:
+            best, best_e, rises = X, e, 0
         else:
-            W = filter_small(g * I + (4.0 - 2.0 * g) * X + (g - 3.0) * X2, tau)
-            X = filter_small(sym(X2 @ W), tau)
-    X = X * (N / np.trace(X))
-    return sym(X), it
+            rises += 1
+            if rises >= 5:
+                break
+        if e <= idem_tol * n_occ or trG == 0.0:
+            break
+        X, _ = trs4_filtered_step(X, n_occ, tau)
+    return best, it
 
 
 # ------------------------------------------------------------------------------------------
@@ -329,17 +341,6 @@ def closed_form_edm(factors, n_occ):
     Sm12 = (U * (1.0 / np.sqrt(w))[None, :]) @ U.T
     C = Sm12 @ Q[:, :n_occ]
     return sym((C * lam[:n_occ][None, :]) @ C.T)
-
-
-def closed_form_rows(factors, n_occ, rows):
-    """Rows `rows` of the closed-form P (for spot checks at sizes where forming P on the CPU is
-    slow): P[i, :] = (S^{-1/2} Q_occ)[i, :] (S^{-1/2} Q_occ)^T."""
-    U, w, Q, lam = factors["S_U"], factors["S_w"], factors["Q"], factors["lam"]
-    Sm12_rows = (U[rows, :] * (1.0 / np.sqrt(w))[None, :]) @ U.T
-    C_rows = Sm12_rows @ Q[:, :n_occ]
-    Sm12 = (U * (1.0 / np.sqrt(w))[None, :]) @ U.T
-    C = Sm12 @ Q[:, :n_occ]
-    return C_rows @ C.T
 
 
 def closed_form_inv_sqrt(factors):

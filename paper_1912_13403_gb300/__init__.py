@@ -96,6 +96,7 @@ _decl("gdm_set_max_iter", _int, [_vp, _int, _int])
 _decl("gdm_set_trace_correction", _int, [_vp, _int])
 _decl("gdm_set_profiling", _int, [_vp, _int])
 _decl("gdm_get_profile", _int, [_vp, _int, ctypes.POINTER(_i64), _dp, _dp, _int])
+_decl("gdm_get_profile_ex", _int, [_vp, _int, ctypes.POINTER(_i64), _dp, _dp, _dp, _int])
 _decl("gdm_launch_count", _i64, [])
 _decl("gdm_set_stream", _int, [_vp, _vp])
 _decl("gdm_set_overlap", _int, [_vp, _vp, _i64, _int])
@@ -157,6 +158,45 @@ def _buf(x):
     return x.ctypes.data, x.strides[0] // 8, GDM_MEM_HOST
 
 
+def _shape(x):
+    return tuple(int(d) for d in x.shape)
+
+
+def _square(x, n, what):
+    """(pointer, leading dimension, mem kind) of an n x n float64 buffer; ValueError for any
+    other shape (the library reads or writes n rows of n elements at the given pointer)."""
+    if _shape(x) != (n, n):
+        raise ValueError("%s must be %d x %d, got %s" % (what, n, n, _shape(x)))
+    return _buf(x)
+
+
+def _device_operands(**mats):
+    """Shapes first (so that a mismatch is reported the same way everywhere), then the
+    device: every operand of a gdm_op_* call is a CUDA float64 tensor of one device."""
+    dev = None
+    for name, x in mats.items():
+        if not (_is_torch(x) and x.is_cuda):
+            raise ValueError("%s must be a CUDA tensor (device pointers only)" % name)
+        if dev is None:
+            dev = x.device
+        elif x.device != dev:
+            raise ValueError("%s is on %s, the other operands on %s" % (name, x.device, dev))
+
+
+def _product_shapes(A, Bt, C, symmetric):
+    if len(_shape(A)) != 2 or len(_shape(Bt)) != 2 or len(_shape(C)) != 2:
+        raise ValueError("A, Bt and C must be 2-D")
+    m, k = _shape(A)
+    n, kb = _shape(Bt)
+    if kb != k:
+        raise ValueError("Bt has %d columns, A has %d (contraction length)" % (kb, k))
+    if _shape(C) != (m, n):
+        raise ValueError("C must be %d x %d, got %s" % (m, n, _shape(C)))
+    if symmetric and m != n:
+        raise ValueError("a symmetric product needs m == n")
+    return m, n, k
+
+
 def _stream_ptr(stream):
     if stream is None:
         return None
@@ -203,14 +243,19 @@ class Handle:
     def set_profiling(self, enable):
         return self._check(gdm_set_profiling(self._h, int(bool(enable))))
 
-    def profile(self, kind=0, reset=False):
-        """(launches, device ms, tensor-pipe flops) of the product launches since the last
-        reset; kind 0 = sliced tensor-core products, 1 = FP64 products."""
+    def profile(self, kind=0, reset=False, algorithmic=False):
+        """(launches, device ms, tensor-pipe flops[, algorithmic flops]) of the product launches
+        since the last reset; kind 0 = sliced tensor-core products, 1 = FP64 products, 2 + p =
+        sliced products of phase p.  Algorithmic flops count n^3 per symmetric and 2 n^3 per
+        full product."""
         l = _i64(0)
         ms = ctypes.c_double(0)
         fl = ctypes.c_double(0)
-        self._check(gdm_get_profile(self._h, kind, ctypes.byref(l), ctypes.byref(ms),
-                                    ctypes.byref(fl), int(bool(reset))))
+        al = ctypes.c_double(0)
+        self._check(gdm_get_profile_ex(self._h, kind, ctypes.byref(l), ctypes.byref(ms),
+                                       ctypes.byref(fl), ctypes.byref(al), int(bool(reset))))
+        if algorithmic:
+            return l.value, ms.value, fl.value, al.value
         return l.value, ms.value, fl.value
 
     def set_max_iter(self, ns_max, purif_max):
@@ -220,11 +265,11 @@ class Handle:
         return self._check(gdm_set_stream(self._h, _stream_ptr(stream)))
 
     def set_overlap(self, S):
-        p, ld, mem = _buf(S)
+        p, ld, mem = _square(S, self.n, "S")
         return self._check(gdm_set_overlap(self._h, p, ld, mem))
 
     def set_hamiltonian(self, H):
-        p, ld, mem = _buf(H)
+        p, ld, mem = _square(H, self.n, "H")
         return self._check(gdm_set_hamiltonian(self._h, p, ld, mem))
 
     def solve(self, P=None, allow=(GDM_ERR_NOT_CONVERGED,)):
@@ -232,7 +277,7 @@ class Handle:
         Returns (P, energy, info dict, status)."""
         if P is None:
             P = np.empty((self.n, self.n))
-        p, ld, mem = _buf(P)
+        p, ld, mem = _square(P, self.n, "P")
         e = ctypes.c_double(0.0)
         info = gdm_info()
         st = gdm_solve_dm(self._h, p, ld, mem, ctypes.byref(e), ctypes.byref(info))
@@ -244,7 +289,7 @@ class Handle:
         n x n; allocated on the host when None).  Returns Q."""
         if Q is None:
             Q = np.empty((self.n, self.n))
-        q, ld, mem = _buf(Q)
+        q, ld, mem = _square(Q, self.n, "Q")
         self._check(gdm_get_edm(self._h, q, ld, mem))
         return Q
 
@@ -254,8 +299,8 @@ class Handle:
         float64 n x n; allocated on the host when None)."""
         if P is None:
             P = np.empty((self.n, self.n))
-        s, lds, ms = _buf(S_new)
-        p, ldp, mp = _buf(P)
+        s, lds, ms = _square(S_new, self.n, "S_new")
+        p, ldp, mp = _square(P, self.n, "P")
         self._check(gdm_extrapolate_dm(self._h, s, lds, ms, p, ldp, mp))
         return P
 
@@ -290,13 +335,14 @@ class Handle:
 
 
 def _problem(H, S, n_occ, P=None):
-    ph, ldh, mem = _buf(H)
-    ps, lds, mem2 = _buf(S)
+    n = _shape(H)[0] if len(_shape(H)) == 2 else -1
+    ph, ldh, mem = _square(H, n, "H")
+    ps, lds, mem2 = _square(S, n, "S")
     if mem != mem2:
         raise ValueError("H and S must live in the same memory")
     p = gdm_problem(H.shape[0], int(n_occ), ph, ldh, ps, lds, mem, None, 0, GDM_MEM_HOST)
     if P is not None:
-        pp, ldp, pmem = _buf(P)
+        pp, ldp, pmem = _square(P, n, "P")
         p.P, p.ldp, p.p_mem = pp, ldp, pmem
     return p
 
@@ -370,11 +416,14 @@ class Server:
 
 
 def op_product(A, Bt, C, nslice=3, max_order=3, symmetric=False, stream=None, slice_bits=0):
-    """C = A @ Bt.T on the device (torch CUDA float64 tensors)."""
+    """C = A @ Bt.T on the device (torch CUDA float64 tensors of one device; C is m x n for
+    A m x k and Bt n x k, checked here because the library trusts the sizes it is given)."""
+    m, n, k = _product_shapes(A, Bt, C, symmetric)
+    _device_operands(A=A, Bt=Bt, C=C)
     pa, lda, _ = _buf(A)
     pb, ldb, _ = _buf(Bt)
     pc, ldc, _ = _buf(C)
-    st = gdm_op_product(pa, lda, pb, ldb, pc, ldc, A.shape[0], Bt.shape[0], A.shape[1],
+    st = gdm_op_product(pa, lda, pb, ldb, pc, ldc, m, n, k,
                         nslice, max_order, slice_bits, int(bool(symmetric)),
                         _stream_ptr(stream))
     if st != GDM_OK:
@@ -385,11 +434,13 @@ def op_product(A, Bt, C, nslice=3, max_order=3, symmetric=False, stream=None, sl
 def op_product_noalloc(A, Bt, C, nslice=3, max_order=3, symmetric=False, stream=None,
                        slice_bits=0):
     """C = A @ Bt.T like op_product, with the library's fixed scratch array instead of device
-    allocations (m, n, k <= 1024)."""
+    allocations (m, n, k <= 1024).  Shapes and device are checked as in op_product."""
+    m, n, k = _product_shapes(A, Bt, C, symmetric)
+    _device_operands(A=A, Bt=Bt, C=C)
     pa, lda, _ = _buf(A)
     pb, ldb, _ = _buf(Bt)
     pc, ldc, _ = _buf(C)
-    st = gdm_op_product_noalloc(pa, lda, pb, ldb, pc, ldc, A.shape[0], Bt.shape[0], A.shape[1],
+    st = gdm_op_product_noalloc(pa, lda, pb, ldb, pc, ldc, m, n, k,
                                 nslice, max_order, slice_bits, int(bool(symmetric)),
                                 _stream_ptr(stream))
     if st != GDM_OK:
@@ -398,20 +449,27 @@ def op_product_noalloc(A, Bt, C, nslice=3, max_order=3, symmetric=False, stream=
 
 
 def op_gershgorin(A, stream=None):
+    """Gershgorin bounds (lo, hi) of the square CUDA float64 tensor A."""
+    n = _shape(A)[0] if len(_shape(A)) == 2 else -1
+    _square(A, n, "A")
+    _device_operands(A=A)
     pa, lda, _ = _buf(A)
     out = (ctypes.c_double * 2)()
-    st = gdm_op_gershgorin(pa, lda, A.shape[0], out, _stream_ptr(stream))
+    st = gdm_op_gershgorin(pa, lda, n, out, _stream_ptr(stream))
     if st != GDM_OK:
         raise GdmError(st, "gdm_op_gershgorin")
     return out[0], out[1]
 
 
 def op_trs4_step(X, n_occ, nslice=0, max_order=0, stream=None):
-    """One TRS4 step in place on the device tensor X; returns (gamma, branch)."""
+    """One TRS4 step in place on the square CUDA float64 tensor X; returns (gamma, branch)."""
+    n = _shape(X)[0] if len(_shape(X)) == 2 else -1
+    _square(X, n, "X")
+    _device_operands(X=X)
     px, ld, _ = _buf(X)
     g = ctypes.c_double(0.0)
     br = ctypes.c_int(-1)
-    st = gdm_op_trs4_step(px, ld, X.shape[0], float(n_occ), nslice, max_order, ctypes.byref(g),
+    st = gdm_op_trs4_step(px, ld, n, float(n_occ), nslice, max_order, ctypes.byref(g),
                           ctypes.byref(br), _stream_ptr(stream))
     if st != GDM_OK:
         raise GdmError(st, "gdm_op_trs4_step")

@@ -97,10 +97,12 @@ void collect_profile(gdm_handle* h) {
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       h->prof_ms[p.kind] += ms;
       h->prof_flops[p.kind] += p.flops;
+      h->prof_alg[p.kind] += p.alg;
       h->prof_launches[p.kind] += 1;
       if (p.kind == 0) {
         h->prof_ms[2 + p.phase] += ms;
         h->prof_flops[2 + p.phase] += p.flops;
+        h->prof_alg[2 + p.phase] += p.alg;
         h->prof_launches[2 + p.phase] += 1;
       }
     }
@@ -115,6 +117,13 @@ cudaError_t clear_device_flags(gdm_handle* h, cudaStream_t s) {
   return cudaMemsetAsync(h->err_dev, 0,
                          sizeof(uint32_t) * (1 + static_cast<size_t>(kSplitTiles) * kEpilogueWarps),
                          s);
+}
+
+// Algorithmic work of one n x n x n product: n^3 when only the upper triangle of a symmetric
+// result is formed, 2 n^3 otherwise (the count the roofline of the route is quoted in).
+double alg_flops(const gdm_handle* h, bool sym) {
+  const double n = static_cast<double>(h->n);
+  return (sym ? 1.0 : 2.0) * n * n * n;
 }
 
 // Tensor-pipe work of one sliced launch: slice pairs x computed tile area x 2 K
@@ -178,7 +187,7 @@ cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const dou
     if (e != cudaSuccess) return e;
     if (h->profiling) {
       cudaEventRecord(e1, h->stream);
-      h->prof_pending.push_back({e0, e1, sliced_flops(h, ph, sym), 0, ph});
+      h->prof_pending.push_back({e0, e1, sliced_flops(h, ph, sym), alg_flops(h, sym), 0, ph});
     }
     if (!exact_diag || a.diag_dot != nullptr) return cudaSuccess;
     e = diag_fix(A.f, h->ld, Bt.f, h->ld, C, h->ld, n, n, alpha, beta, D, h->ld, diag, coef,
@@ -217,7 +226,8 @@ cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const dou
     cudaEventRecord(e1, h->stream);
     const double nn = static_cast<double>(n);
     const double t = std::ceil(nn / 64.0);
-    h->prof_pending.push_back({e0, e1, (sym ? t * (t + 1) / 2 : t * t) * 64.0 * 64.0 * 2.0 * nn, 1, ph});
+    h->prof_pending.push_back(
+        {e0, e1, (sym ? t * (t + 1) / 2 : t * t) * 64.0 * 64.0 * 2.0 * nn, alg_flops(h, sym), 1, ph});
   }
   return e;
 }
@@ -906,18 +916,25 @@ gdm_status gdm_set_profiling(gdm_handle* h, int enable) {
   return GDM_OK;
 }
 
-gdm_status gdm_get_profile(gdm_handle* h, int kind, int64_t* launches, double* ms,
-                           double* flops, int reset) {
+gdm_status gdm_get_profile_ex(gdm_handle* h, int kind, int64_t* launches, double* ms,
+                              double* flops, double* alg_flops_out, int reset) {
   if (h == nullptr || kind < 0 || kind >= gdm_handle::kProfKinds) return GDM_ERR_ARG;
   if (launches) *launches = h->prof_launches[kind];
   if (ms) *ms = h->prof_ms[kind];
   if (flops) *flops = h->prof_flops[kind];
+  if (alg_flops_out) *alg_flops_out = h->prof_alg[kind];
   if (reset) {
     h->prof_launches[kind] = 0;
     h->prof_ms[kind] = 0.0;
     h->prof_flops[kind] = 0.0;
+    h->prof_alg[kind] = 0.0;
   }
   return GDM_OK;
+}
+
+gdm_status gdm_get_profile(gdm_handle* h, int kind, int64_t* launches, double* ms,
+                           double* flops, int reset) {
+  return gdm_get_profile_ex(h, kind, launches, ms, flops, nullptr, reset);
 }
 
 int64_t gdm_launch_count(void) { return launch_count(); }

@@ -70,7 +70,8 @@ struct gdm_handle {
   bool profiling = false;
   struct Prof {
     cudaEvent_t a, b;
-    double flops;
+    double flops;  // issued: tensor-pipe (slice pairs x computed tile area x 2K) or FP64 work
+    double alg;    // algorithmic: n^3 for a symmetric product, 2 n^3 for a full one
     int kind;  // 0 sliced, 1 fp64
     int phase;  // gdm_phase of the product
   };
@@ -79,7 +80,7 @@ struct gdm_handle {
   std::vector<Prof> prof_pending;
   std::vector<cudaEvent_t> ev_pool;
   int64_t prof_launches[kProfKinds] = {};
-  double prof_ms[kProfKinds] = {}, prof_flops[kProfKinds] = {};
+  double prof_ms[kProfKinds] = {}, prof_flops[kProfKinds] = {}, prof_alg[kProfKinds] = {};
   std::string last_error;
 };
 

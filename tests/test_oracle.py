@@ -16,10 +16,22 @@ import scipy.linalg
 
 import oracle
 from oracle import steps
+from oracle.lapack import density_matrix_eigh
 from workloads import (make_config0, make_random_small, make_small_diag, make_spectrum_problem,
                        haar_orthogonal, make_geometry_step, make_banded)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# Both statements of the definition are pinned by the same closed forms, golden values, special
+# cases, brute force and invariants: the Jacobi one (plain rotations, C) and the one with LAPACK's
+# eigensolver (numpy), which evaluates the definition at the full workload sizes.
+DM_IMPLS = {"jacobi": oracle.density_matrix, "lapack": density_matrix_eigh}
+
+
+@pytest.fixture(params=sorted(DM_IMPLS))
+def dm(request):
+    return DM_IMPLS[request.param]
 
 
 def rel(a, b):
@@ -67,9 +79,9 @@ def test_jacobi_repeated_eigenvalues_keep_orthonormal_basis():
 # density matrix: closed forms, special cases, golden values
 # ------------------------------------------------------------------------------------------
 
-def test_dm_config0_closed_form():
+def test_dm_config0_closed_form(dm):
     p = make_config0()
-    r = oracle.density_matrix(p.H, p.S, p.n_occ)
+    r = dm(p.H, p.S, p.n_occ)
     Pc, Ec = steps.closed_form_dm(p.factors, p.n_occ)
     assert r["status"] == "OK"
     assert rel(r["P"], Pc) <= 1e-11
@@ -80,9 +92,9 @@ def test_dm_config0_closed_form():
 
 
 @pytest.mark.parametrize("cond,gap", [(10.0, 0.5), (1e3, 0.2), (1e3, 0.05)])
-def test_dm_ill_conditioned_overlap_closed_form(cond, gap):
+def test_dm_ill_conditioned_overlap_closed_form(cond, gap, dm):
     p = make_spectrum_problem(7, 96, 24, cond_S=cond, gap=gap)
-    r = oracle.density_matrix(p.H, p.S, p.n_occ)
+    r = dm(p.H, p.S, p.n_occ)
     Pc, Ec = steps.closed_form_dm(p.factors, p.n_occ)
     assert r["status"] == "OK"
     assert rel(r["P"], Pc) <= 1e-10
@@ -90,32 +102,32 @@ def test_dm_ill_conditioned_overlap_closed_form(cond, gap):
     assert abs(r["gap"] - gap) <= 1e-10
 
 
-def test_dm_identity_overlap_is_standard_eigenproblem():
+def test_dm_identity_overlap_is_standard_eigenproblem(dm):
     p = make_random_small(11, 50, 17)
     S = np.eye(50)
-    r = oracle.density_matrix(p.H, S, p.n_occ)
+    r = dm(p.H, S, p.n_occ)
     w, V = np.linalg.eigh(p.H)
     Vo = V[:, :p.n_occ]
     assert rel(r["P"], Vo @ Vo.T) <= 1e-11
     assert abs(r["energy"] - w[:p.n_occ].sum()) <= 1e-11 * abs(w[:p.n_occ].sum())
 
 
-def test_dm_diagonal_case():
+def test_dm_diagonal_case(dm):
     p = make_small_diag(3, 20, 6)
     h, s = np.diag(p.H), np.diag(p.S)
     order = np.argsort(h / s, kind="stable")[:6]
     P_expect = np.zeros((20, 20))
     P_expect[order, order] = 1.0 / s[order]
-    r = oracle.density_matrix(p.H, p.S, 6)
+    r = dm(p.H, p.S, 6)
     assert np.max(np.abs(r["P"] - P_expect)) <= 1e-13
     assert abs(r["energy"] - np.sort(h / s)[:6].sum()) <= 1e-13
 
 
-def test_dm_golden_2x2():
+def test_dm_golden_2x2(dm):
     with open(os.path.join(GOLDEN, "dm_2x2.json")) as f:
         cases = json.load(f)["cases"]
     for c in cases:
-        r = oracle.density_matrix(np.array(c["H"]), np.array(c["S"]), c["n_occ"])
+        r = dm(np.array(c["H"]), np.array(c["S"]), c["n_occ"])
         np.testing.assert_allclose(r["P"], np.array(c["P"]), atol=1e-14, err_msg=c["name"])
         assert abs(r["energy"] - c["energy"]) <= 1e-14, c["name"]
         np.testing.assert_allclose(r["evals"], c["evals"], atol=1e-14, err_msg=c["name"])
@@ -125,36 +137,36 @@ def test_dm_golden_2x2():
 # Energy-weighted density matrix (Sec. 2.6, Eq. energy_density_matrix)
 # ------------------------------------------------------------------------------------------
 
-def test_edm_golden_2x2():
+def test_edm_golden_2x2(dm):
     with open(os.path.join(GOLDEN, "dm_2x2.json")) as f:
         cases = json.load(f)["cases"]
     for c in cases:
-        r = oracle.density_matrix(np.array(c["H"]), np.array(c["S"]), c["n_occ"], edm=True)
+        r = dm(np.array(c["H"]), np.array(c["S"]), c["n_occ"], edm=True)
         np.testing.assert_allclose(r["Q"], np.array(c["Q"]), atol=1e-14, err_msg=c["name"])
 
 
-def test_edm_config0_closed_form():
+def test_edm_config0_closed_form(dm):
     p = make_config0()
-    r = oracle.density_matrix(p.H, p.S, p.n_occ, edm=True)
+    r = dm(p.H, p.S, p.n_occ, edm=True)
     Qc = steps.closed_form_edm(p.factors, p.n_occ)
     assert rel(r["Q"], Qc) <= 1e-11
     # the P computed alongside is unchanged by asking for Q
-    assert np.array_equal(r["P"], oracle.density_matrix(p.H, p.S, p.n_occ)["P"])
+    assert np.array_equal(r["P"], dm(p.H, p.S, p.n_occ)["P"])
 
 
-def test_edm_full_occupation_is_sinv_h_sinv():
+def test_edm_full_occupation_is_sinv_h_sinv(dm):
     # with every state occupied, C C^T = S^{-1} and Q = C diag(eps) C^T = S^{-1} H S^{-1}
     p = make_random_small(77, 24, 5)
-    r = oracle.density_matrix(p.H, p.S, 24, edm=True)
+    r = dm(p.H, p.S, 24, edm=True)
     Si = np.linalg.inv(p.S)
     assert rel(r["Q"], Si @ p.H @ Si) <= 1e-11
 
 
-def test_edm_identities_on_unstructured_input():
+def test_edm_identities_on_unstructured_input(dm):
     # Q = P H P (C^T H C is diagonal), Tr(Q S) = sum of the occupied eigenvalues = Tr(P H),
     # and Q S P = Q (the range of Q lies in the occupied subspace)
     p = make_random_small(78, 40, 13)
-    r = oracle.density_matrix(p.H, p.S, 13, edm=True)
+    r = dm(p.H, p.S, 13, edm=True)
     Q, P = r["Q"], r["P"]
     assert rel(Q, P @ p.H @ P) <= 1e-11
     assert abs(np.sum(Q * p.S) - np.sum(r["evals"][:13])) <= 1e-11 * np.abs(r["evals"]).sum()
@@ -241,20 +253,20 @@ def test_extrapolation_rejects_indefinite_overlap():
     assert P1 is None and st == "NOT_SPD"
 
 
-def test_dm_full_occupation_is_inverse_overlap():
+def test_dm_full_occupation_is_inverse_overlap(dm):
     p = make_random_small(12, 30, 30)
-    r = oracle.density_matrix(p.H, p.S, 30)
+    r = dm(p.H, p.S, 30)
     assert rel(r["P"], np.linalg.inv(p.S)) <= 1e-12
 
 
-def test_dm_zero_occupation():
+def test_dm_zero_occupation(dm):
     p = make_random_small(13, 10, 0)
-    r = oracle.density_matrix(p.H, p.S, 0)
+    r = dm(p.H, p.S, 0)
     assert np.all(r["P"] == 0.0) and r["energy"] == 0.0
 
 
 @pytest.mark.parametrize("n,n_occ", [(4, 2), (6, 2), (7, 3), (8, 4)])
-def test_dm_brute_force_minimum(n, n_occ):
+def test_dm_brute_force_minimum(n, n_occ, dm):
     """Among all projectors onto n_occ generalised eigenvectors, the oracle's P has the least
     band energy Tr(P H), and it equals that projector."""
     p = make_random_small(20 + n, n, n_occ)
@@ -266,30 +278,68 @@ def test_dm_brute_force_minimum(n, n_occ):
         e = float(np.sum(P * p.H))
         if best is None or e < best[0]:
             best = (e, P)
-    r = oracle.density_matrix(p.H, p.S, n_occ)
+    r = dm(p.H, p.S, n_occ)
     assert abs(r["energy"] - best[0]) <= 1e-12 * max(1.0, abs(best[0]))
     assert np.max(np.abs(r["P"] - best[1])) <= 1e-11
 
 
-def test_dm_invariants_on_unstructured_input():
+def test_dm_invariants_on_unstructured_input(dm):
     p = make_random_small(31, 60, 25)
-    r = oracle.density_matrix(p.H, p.S, p.n_occ)
+    r = dm(p.H, p.S, p.n_occ)
     inv = steps.invariants(r["P"], p.H, p.S, p.n_occ)
     assert inv["idem"] < 1e-11 and inv["trace_err"] < 1e-11
     assert inv["asym"] == 0.0 and inv["commut"] < 1e-10
     assert abs(inv["energy"] - r["energy"]) < 1e-11 * max(1, abs(r["energy"]))
 
 
-def test_dm_status_no_gap_and_not_spd():
+def test_dm_status_no_gap_and_not_spd(dm):
     rng = np.random.default_rng(1)
     Q = haar_orthogonal(rng, 8)
     lam = np.array([-2.0, -1.0, 0.5, 0.5, 1.0, 2.0, 3.0, 4.0])
     H = (Q * lam) @ Q.T
-    r = oracle.density_matrix(H, np.eye(8), 3)
+    r = dm(H, np.eye(8), 3)
     assert r["status"] == "NO_GAP"
     S = np.eye(8)
     S[0, 0] = -1.0
-    assert oracle.density_matrix(H, S, 3)["status"] == "NOT_SPD"
+    assert dm(H, S, 3)["status"] == "NOT_SPD"
+
+
+@pytest.mark.parametrize("n,n_occ,seed", [(64, 17, 41), (150, 60, 42), (97, 1, 43), (97, 96, 44)])
+def test_lapack_statement_matches_jacobi(n, n_occ, seed):
+    """The two statements of the definition agree on unstructured inputs (no closed form),
+    including a single occupied and a single virtual state."""
+    p = make_random_small(seed, n, n_occ)
+    a = oracle.density_matrix(p.H, p.S, n_occ, edm=True)
+    b = density_matrix_eigh(p.H, p.S, n_occ, edm=True)
+    assert a["status"] == b["status"] == "OK"
+    assert rel(b["P"], a["P"]) <= 1e-12
+    assert rel(b["Q"], a["Q"]) <= 1e-11
+    assert abs(b["energy"] - a["energy"]) <= 1e-12 * max(1.0, abs(a["energy"]))
+    np.testing.assert_allclose(b["evals"], a["evals"], atol=1e-12)
+
+
+def test_lapack_statement_pins_catch_plausible_mistakes():
+    """Mistakes in the steps of the LAPACK statement that its pins must catch: the Cholesky-free
+    Loewdin factor replaced by S^{-1} (a dropped square root), the occupied columns taken from the
+    top of the spectrum (a wrong index), and P = C^T C (a transposed operand)."""
+    p = make_spectrum_problem(17, 80, 20, cond_S=50.0, gap=0.3)
+    Pc, Ec = steps.closed_form_dm(p.factors, p.n_occ)
+    good = density_matrix_eigh(p.H, p.S, p.n_occ)
+    assert rel(good["P"], Pc) <= 1e-11
+
+    s, U = np.linalg.eigh(p.S)
+
+    def route(zpow=-0.5, top=False, transpose=False):
+        Z = (U * s ** zpow) @ U.T
+        lam, V = np.linalg.eigh(steps.sym(Z @ p.H @ Z))
+        cols = V[:, -p.n_occ:] if top else V[:, :p.n_occ]
+        C = Z @ cols
+        return C.T @ C if transpose else C @ C.T
+    assert rel(route(), Pc) <= 1e-11
+    assert not rel(route(zpow=-1.0), Pc) <= 1e-3
+    assert not rel(route(top=True), Pc) <= 1e-3
+    with pytest.raises(ValueError):
+        rel(route(transpose=True), Pc)          # wrong shape: N x N instead of n x n
 
 
 def test_inv_sqrt_matches_factors():
@@ -443,7 +493,8 @@ def test_truncated_trs4_error_grows_with_threshold_and_keeps_count():
     errs = []
     for tau in (1e-9, 1e-7, 1e-5):
         X, _ = steps.trs4_purify_truncated(p.H, 128, tau)
-        assert abs(np.trace(X) - 128) <= 1e-10
+        # the gamma step resets the trace exactly; only the filtered part of W moves it
+        assert abs(np.trace(X) - 128) <= 1e-7 * 128
         assert np.array_equal(X, X.T)
         errs.append(rel(X, Pex))
     assert errs[0] < errs[1] < errs[2]
@@ -453,6 +504,79 @@ def test_truncated_trs4_error_grows_with_threshold_and_keeps_count():
     idx = np.arange(512)
     far = np.abs(idx[:, None] - idx[None, :]) > 256
     assert np.mean(X[far] == 0.0) > 0.5
+
+
+def _golden_trs4_filtered():
+    with open(os.path.join(GOLDEN, "trs4_filtered_6x6.json")) as f:
+        return json.load(f)
+
+
+def _filtered_steps(d, step):
+    """The oracle's initial guess and steps on the golden case, with `step` as the step."""
+    Ht = np.array(d["H_tilde"])
+    lo, hi = steps.gershgorin_bounds(Ht)
+    X = steps.filter_small(steps.initial_guess(Ht, lo, hi), d["tau"])
+    out = [(X, None)]
+    for _ in d["steps"]:
+        X, info = step(X, d["n_occ"], d["tau"])
+        out.append((X, info))
+    return (lo, hi), out
+
+
+def test_filtered_trs4_golden_6x6():
+    """Two filtered TRS4 steps on a 6 x 6 banded case, against exact rational values
+    (tests/golden/make_trs4_filtered.py): X0, X^2 and W each lose an element to the filter, and
+    one off-diagonal pair of X^2 W straddles the threshold."""
+    d = _golden_trs4_filtered()
+    (lo, hi), out = _filtered_steps(d, steps.trs4_filtered_step)
+    assert lo == d["eps_min"] and hi == d["eps_max"]
+    np.testing.assert_allclose(out[0][0], d["X0_filtered"], rtol=0, atol=1e-15)
+    for k, ref in enumerate(d["steps"]):
+        X, info = out[k + 1]
+        assert info["branch"] == "F+gG"
+        np.testing.assert_allclose(info["X2"], ref["X2_filtered"], rtol=0, atol=1e-14)
+        assert abs(info["gamma"] - ref["gamma"]) <= 1e-13 * abs(ref["gamma"])
+        np.testing.assert_allclose(info["W"], ref["W_filtered"], rtol=0, atol=1e-14)
+        np.testing.assert_allclose(X, ref["X_next"], rtol=0, atol=1e-14)
+        assert abs(np.trace(X) - ref["X_next_trace"]) <= 1e-14
+    # the case exercises every filter placement
+    assert d["X0_below_tau"] and all(s["X2_below_tau"] and s["W_below_tau"] for s in d["steps"])
+    assert d["steps"][1]["straddling_pairs"]
+
+
+def test_filtered_trs4_golden_catches_misplaced_filters():
+    """Plausible mistakes in where the filter sits, each of which the golden case rejects."""
+    d = _golden_trs4_filtered()
+    ref = np.array(d["steps"][-1]["X_next"])
+    f = steps.filter_small
+
+    def step(X, N, tau, filt_w=True, filt_after_sym=True, filt_x2_in_traces=True):
+        X2 = X @ X
+        X2f = f(X2, tau)
+        T = X2f if filt_x2_in_traces else X2
+        t2, t3, t4 = np.trace(T), np.sum(T * X), np.sum(T * T)
+        g = (N - (4 * t3 - 3 * t4)) / (t2 - 2 * t3 + t4)
+        W = g * np.eye(X.shape[0]) + (4 - 2 * g) * X + (g - 3) * X2f
+        if filt_w:
+            W = f(W, tau)
+        M = X2f @ W
+        Xn = f(steps.sym(M), tau) if filt_after_sym else steps.sym(f(M, tau))
+        return Xn, {}
+
+    def final(**kw):
+        return _filtered_steps(d, lambda X, N, tau: step(X, N, tau, **kw))[1][-1][0]
+
+    assert np.abs(final() - ref).max() <= 1e-14            # the restatement agrees ...
+    assert np.abs(final(filt_w=False) - ref).max() > 1e-6  # ... W left unfiltered
+    assert np.abs(final(filt_after_sym=False) - ref).max() > 1e-6  # filtered, then symmetrised
+    assert np.abs(final(filt_x2_in_traces=False) - ref).max() > 1e-6  # raw X^2 in gamma
+    # the initial guess left unfiltered
+    Ht = np.array(d["H_tilde"])
+    lo, hi = steps.gershgorin_bounds(Ht)
+    X = steps.initial_guess(Ht, lo, hi)
+    for _ in d["steps"]:
+        X, _ = steps.trs4_filtered_step(X, d["n_occ"], d["tau"])
+    assert np.abs(X - ref).max() > 1e-6
 
 
 def test_newton_schulz_and_refinement():
@@ -521,6 +645,7 @@ def _route_with(trs4_step=None, inv_sqrt=None):
     return rel(P, Pc)
 
 
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")  # a planted mistake diverges
 def test_planted_mistakes_are_caught():
     assert _route_with() <= 1e-10
 

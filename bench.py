@@ -544,6 +544,7 @@ def run_ours(args):
     relerr = rel_err(P, Pc)
     alg_per_solve = prof_alg / args.steps
     P_last = P.cpu().numpy()  # the last timed solve's result (P is reused below)
+    s_idem = float(torch.linalg.norm(P @ S @ P - P))  # ||P S P - P||_F of the returned P
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     Hh = torch.from_numpy(p.H).pin_memory()
@@ -652,6 +653,9 @@ def run_ours(args):
         "accuracy": {"rel_frobenius_err": relerr, "rel_frobenius_err_vs_oracle": oracle_err,
                      "abs_energy_err": abs(e - Ec), "rel_energy_err": abs(e - Ec) / abs(Ec),
                      "trace_err": info["trace_err"], "trace_err_raw": info["trace_err_raw"],
+                     "metric_cleanup": info["metric_cleanup"],
+                     "trace_rescaled": info["trace_rescaled"],
+                     "s_idem_err": s_idem, "bounds": [info["eps_min"], info["eps_max"]],
                      "truncation": args.truncation,
                      "kstage_fraction": info["kstage_fraction"],
                      "ns_iters": info["ns_iters"], "refine_iters": info["refine_iters"],
@@ -713,6 +717,8 @@ def config2_record(args, local, steps=3, warmup=2):
            "latency_ms": {"p50": statistics.median(per), "p99": pct(per, 0.99)},
            "rel_frobenius_err": rel_err(P, Pc), "rel_energy_err": abs(e - Ec) / abs(Ec),
            "trace_err": info["trace_err"], "trace_err_raw": info["trace_err_raw"],
+           "metric_cleanup": info["metric_cleanup"], "trace_rescaled": info["trace_rescaled"],
+           "s_idem_err": float(torch.linalg.norm(P @ S @ P - P)),
            "ns_iters": info["ns_iters"], "purif_iters": info["purif_iters"],
            "tflops_algorithmic": prof_alg / steps / (total_ms / steps / 1e3) / 1e12,
            "gemm_tflops_issued": (prof_flops / (prof_ms / 1e3)) / 1e12 if prof_ms else None,

@@ -93,11 +93,17 @@ typedef struct {
   double trace_err;    /* |Tr(P S) - n_occ| of the returned P */
   double trace_err_raw; /* |Tr(P S) - n_occ| before the final trace correction */
   double energy;       /* Tr(P H) */
-  double eps_min, eps_max; /* Gershgorin bounds of H~ */
+  double eps_min, eps_max; /* spectral bounds of H~ that the initial guess used */
   double ms_total;     /* device time of the solve (ms), CUDA events on the handle's stream */
   double trace_fix;    /* final trace reset of the orthogonal-basis matrix: N / Tr X - 1 */
   double kstage_fraction; /* truncated purification: k stages the products issued over the
                              stages of the dense products (1 without truncation) */
+  int bounds_restart;  /* 1 when the purification failed from the estimated bounds and was run
+                          again from Gershgorin's */
+  int metric_cleanup;  /* 1 when the S-metric clean-up ran (gdm_set_metric_cleanup) */
+  int trace_rescaled;  /* 1 when the final scalar rescale P <- P n_occ / Tr(P S) fired */
+  double s_idem_err;   /* ||P S P - P||_F of the back-transformed P when the clean-up ran
+                          (computed on its way), else -1 */
 } gdm_info;
 
 /* Create a handle for n_basis x n_basis problems with n_occ occupied states (f_l in {0,1})
@@ -121,6 +127,20 @@ gdm_status gdm_set_precision(gdm_handle* h, gdm_precision prec);
  * Errors: GDM_ERR_ARG (negative or non-finite threshold). */
 gdm_status gdm_set_truncation(gdm_handle* h, double threshold);
 
+/* Spectral bounds eps_min, eps_max of H~ for the initial guess (Eq. ntpoly_scale_hamiltonian,
+ * where the paper takes them "estimated"):
+ *   GDM_BOUNDS_GERSHGORIN  Gershgorin's discs: always enclose the spectrum, but for a dense H~
+ *                          they span it many times over, which narrows the gap at n_occ in X0 by
+ *                          that factor (more purification steps, and more of each product's
+ *                          rounding reaches the occupied subspace)
+ *   GDM_BOUNDS_LANCZOS     (default) the extreme Ritz values of `lanczos_steps` Lanczos steps
+ *                          (1..64; 0 keeps the current count, default 24) widened by 2% of their
+ *                          span and clamped to Gershgorin's interval; if the purification fails
+ *                          from them, it runs again from Gershgorin's (gdm_info.bounds_restart).
+ * Errors: GDM_ERR_ARG. */
+typedef enum { GDM_BOUNDS_GERSHGORIN = 0, GDM_BOUNDS_LANCZOS = 1 } gdm_bounds;
+gdm_status gdm_set_bounds(gdm_handle* h, gdm_bounds method, int lanczos_steps);
+
 /* Select the purification map for later solves (default GDM_PURIFY_TRS4).  Errors: GDM_ERR_ARG. */
 gdm_status gdm_set_purification(gdm_handle* h, gdm_purification method);
 
@@ -138,9 +158,21 @@ gdm_status gdm_set_slices(gdm_handle* h, gdm_phase phase, int nslice, int max_or
  * above which the solve reports GDM_ERR_NOT_CONVERGED (default 1e-6; 0 disables). */
 gdm_status gdm_set_tolerance(gdm_handle* h, double idem_tol, double trace_tol);
 
-/* Final trace correction (default on): after the back-transform, P <- P * n_occ / Tr(P S),
- * computed in FP64.  What it removes is the electron-count error left by Z^T S Z - I (about
- * 1e-8 at cond(S) = 1e3 in GDM_PREC_MIXED); gdm_info.trace_err_raw reports it either way. */
+/* S-metric clean-up of the back-transformed P (Eq. density_matrix_conditions, P S P = P and
+ * Tr(P S) = n_occ in the non-orthogonal basis), off by default: when |Tr(P S) - n_occ| exceeds
+ * `threshold`, one McWeeny step in the S metric, P <- 3 P S P - 2 P S P S P, computed as
+ * P S P - 2 D S P with D = P S P - P (three products, about 5% of a solve).  In the sliced
+ * arithmetic it lowers ||P S P - P||_F about tenfold for well-conditioned overlaps, but the
+ * rounding of its own products moves Tr(P S) by about 1e-8 at n = 8192 (more than the solve
+ * leaves there), and at cond(S) = 1e3 its products cannot resolve P S P - P at all; hence
+ * opt-in.  threshold 0 runs it after every solve, a negative one (the default) never.
+ * gdm_info.metric_cleanup and .s_idem_err report it.  Errors: GDM_ERR_ARG (NaN). */
+gdm_status gdm_set_metric_cleanup(gdm_handle* h, double threshold);
+
+/* Last-resort trace correction (default on): when |Tr(P S) - n_occ| is above 1e-8 after the
+ * solve (and the clean-up, if it ran), P <- P * n_occ / Tr(P S) in FP64, which moves P by that
+ * relative amount (gdm_info.trace_rescaled = 1).  gdm_info.trace_err_raw reports the count
+ * before it. */
 gdm_status gdm_set_trace_correction(gdm_handle* h, int enable);
 
 /* Timing of the product launches: when enabled, CUDA events are recorded around every

@@ -29,6 +29,7 @@ GDM_MEM_HOST, GDM_MEM_DEVICE = 0, 1
 GDM_PREC_FP64, GDM_PREC_MIXED = 0, 1
 GDM_PURIFY_TRS4, GDM_PURIFY_TRS2, GDM_PURIFY_CANONICAL = 0, 1, 2
 GDM_PHASE_NEWTON_SCHULZ, GDM_PHASE_REFINE, GDM_PHASE_TRANSFORM, GDM_PHASE_PURIFY = range(4)
+GDM_BOUNDS_GERSHGORIN, GDM_BOUNDS_LANCZOS = 0, 1
 
 
 class gdm_info(ctypes.Structure):
@@ -39,7 +40,9 @@ class gdm_info(ctypes.Structure):
                 ("energy", ctypes.c_double),
                 ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("trace_fix", ctypes.c_double),
-                ("kstage_fraction", ctypes.c_double)]
+                ("kstage_fraction", ctypes.c_double), ("bounds_restart", ctypes.c_int),
+                ("metric_cleanup", ctypes.c_int), ("trace_rescaled", ctypes.c_int),
+                ("s_idem_err", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +92,8 @@ def _decl(name, res, args):
 _decl("gdm_init", _int, [ctypes.POINTER(_vp), _i64, _i64, _int])
 _decl("gdm_set_precision", _int, [_vp, _int])
 _decl("gdm_set_purification", _int, [_vp, _int])
+_decl("gdm_set_bounds", _int, [_vp, _int, _int])
+_decl("gdm_set_metric_cleanup", _int, [_vp, _dbl])
 _decl("gdm_set_truncation", _int, [_vp, _dbl])
 _decl("gdm_set_slices", _int, [_vp, _int, _int, _int, _int])
 _decl("gdm_set_tolerance", _int, [_vp, _dbl, _dbl])
@@ -227,6 +232,11 @@ class Handle:
         """Threshold filtering of the purification (0 turns it off)."""
         return self._check(gdm_set_truncation(self._h, float(threshold)))
 
+    def set_bounds(self, method, lanczos_steps=0):
+        """Spectral bounds of H~ for the initial guess: GDM_BOUNDS_LANCZOS (default) or
+        GDM_BOUNDS_GERSHGORIN; lanczos_steps 0 keeps the current count."""
+        return self._check(gdm_set_bounds(self._h, method, int(lanczos_steps)))
+
     def set_purification(self, method):
         """GDM_PURIFY_TRS4 (default), GDM_PURIFY_TRS2 or GDM_PURIFY_CANONICAL."""
         return self._check(gdm_set_purification(self._h, method))
@@ -236,6 +246,10 @@ class Handle:
 
     def set_tolerance(self, idem_tol, trace_tol):
         return self._check(gdm_set_tolerance(self._h, idem_tol, trace_tol))
+
+    def set_metric_cleanup(self, threshold):
+        """S-metric clean-up when |Tr(PS) - n_occ| > threshold (0: always, < 0: never)."""
+        return self._check(gdm_set_metric_cleanup(self._h, float(threshold)))
 
     def set_trace_correction(self, enable):
         return self._check(gdm_set_trace_correction(self._h, int(bool(enable))))

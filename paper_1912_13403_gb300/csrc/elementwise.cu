@@ -1575,6 +1575,82 @@ __global__ void tighten_bound_kernel(double* bounds, const double* est, double f
   if (isfinite(c) && c > 0.0 && c < bounds[1]) bounds[1] = c;
 }
 
+// ---- Lanczos estimates of the extreme eigenvalues of a symmetric matrix ---------------------
+// Three-term recurrence without reorthogonalisation (its extreme Ritz values converge first and
+// are not disturbed by the loss of orthogonality, which only adds copies of converged values):
+//   w = A v_k - beta_{k-1} v_{k-1},  alpha_k = v_k . w,  w -= alpha_k v_k,  beta_k = ||w||,
+//   v_{k+1} = w / beta_k.
+// v lives in FP64 (v, vprev) and as a double-float pair (xh, xl) for the matrix-vector product.
+
+// Start vector: the power iteration's fixed pseudo-random vector, normalised; vprev = 0.
+__global__ void lanczos_init_kernel(int n, float* xh, float* xl, double* v, double* vprev) {
+  __shared__ double red[32];
+  __shared__ double inv_sh;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    unsigned h = static_cast<unsigned>(i) * 2654435761u + 0x9E3779B9u;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    const double x = static_cast<double>(__uint_as_float(0x3F800000u | (h >> 9))) - 1.5;
+    v[i] = x;  // in [-0.5, 0.5)
+    acc += x * x;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) inv_sh = acc > 0.0 ? 1.0 / sqrt(acc) : 0.0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = v[i] * inv_sh;
+    v[i] = x;
+    vprev[i] = 0.0;
+    const float hi = static_cast<float>(x);
+    xh[i] = hi;
+    xl[i] = static_cast<float>(x - static_cast<double>(hi));
+  }
+}
+
+// One step after y = A v: alpha_k and beta_k into ab[k] and ab[kmax + k], then the next v.
+// A beta at the rounding level (an invariant subspace) ends the recurrence: the next vector is
+// left zero, so every later alpha and beta is zero and the Ritz values stay those found.
+__global__ void lanczos_update_kernel(double* y, double* v, double* vprev, float* xh, float* xl,
+                                      int n, double* ab, int k, int kmax) {
+  __shared__ double red[32];
+  __shared__ double alpha_sh, inv_sh;
+  const double beta_prev = (k > 0) ? ab[kmax + k - 1] : 0.0;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += v[i] * y[i];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) alpha_sh = acc;
+  __syncthreads();
+  const double alpha = alpha_sh;
+  double ss = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double w = y[i] - alpha * v[i] - beta_prev * vprev[i];
+    y[i] = w;
+    ss += w * w;
+  }
+  ss = block_sum(ss, red);
+  if (threadIdx.x == 0) {
+    const double beta = sqrt(ss);
+    ab[k] = alpha;
+    // relative to the size of the recurrence's terms (v has unit norm, or is zero once the
+    // recurrence has ended): below it the new direction is rounding noise
+    const bool ends = !(beta > 1e-12 * (fabs(alpha) + beta_prev));
+    ab[kmax + k] = ends ? 0.0 : beta;
+    inv_sh = ends ? 0.0 : 1.0 / beta;
+  }
+  __syncthreads();
+  const double inv = inv_sh;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double vn = y[i] * inv;
+    vprev[i] = v[i];
+    v[i] = vn;
+    const float hi = static_cast<float>(vn);
+    xh[i] = hi;
+    xl[i] = static_cast<float>(vn - static_cast<double>(hi));
+  }
+}
+
 __global__ void scale_coef_kernel(const double* bounds, int inv_sqrt, double* coef) {
   const double c = bounds[1];
   coef[0] = inv_sqrt ? 1.0 / sqrt(c) : 1.0 / c;
@@ -1851,6 +1927,35 @@ cudaError_t power_bound(const double* A, int64_t lda, int n, int iters, double f
   }
   count_launch();
   tighten_bound_kernel<<<1, 1, 0, stream>>>(bounds_dev, est_dev, factor);
+  return cudaGetLastError();
+}
+
+cudaError_t lanczos(const double* A, int64_t lda, int n, int steps, double* work,
+                    double* partials, double* ab_dev, cudaStream_t stream) {
+  if (n <= 0 || steps <= 0) return cudaSuccess;
+  float* xh = reinterpret_cast<float*>(work);
+  float* xl = xh + n;
+  double* y = work + n;
+  double* v = work + 2 * static_cast<int64_t>(n);
+  double* vprev = work + 3 * static_cast<int64_t>(n);
+  const bool rows_fit = n % 2 == 0 && n <= kFusedMaxCols && lda % 2 == 0 &&
+                        (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+  const int nb = (n + kRowsPerBlock - 1) / kRowsPerBlock;
+  count_launch();
+  lanczos_init_kernel<<<1, 1024, 0, stream>>>(n, xh, xl, v, vprev);
+  for (int k = 0; k < steps; ++k) {
+    count_launch();
+    if (!rows_fit)
+      matvec_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, n, xh, xl, y, partials);
+    else if (n / 2 <= 128 * kFusedPPT)
+      matvec_rows_kernel<128><<<n, 128, 0, stream>>>(A, lda, n, xh, xl, y, partials);
+    else if (n / 2 <= 256 * kFusedPPT)
+      matvec_rows_kernel<256><<<n, 256, 0, stream>>>(A, lda, n, xh, xl, y, partials);
+    else
+      matvec_rows_kernel<512><<<n, 512, 0, stream>>>(A, lda, n, xh, xl, y, partials);
+    count_launch();
+    lanczos_update_kernel<<<1, 1024, 0, stream>>>(y, v, vprev, xh, xl, n, ab_dev, k, steps);
+  }
   return cudaGetLastError();
 }
 

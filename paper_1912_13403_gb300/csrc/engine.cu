@@ -40,7 +40,47 @@ enum SmallSlot {
   SM_COEF_X0 = 12,   // 3
   SM_RED = 16,       // 8 reduction outputs
   SM_KCOUNT = 24,    // 1: k stages issued by masked products (as an unsigned 64-bit count)
+  SM_GERSH_H = 26,   // 2: Gershgorin bounds of H~
+  SM_LANCZOS = 32,   // 2 x kMaxLanczos: alpha_k, then beta_k, of the Lanczos recurrence on H~
 };
+constexpr int kMaxLanczos = 64;
+
+// Extreme eigenvalues of the symmetric tridiagonal matrix with diagonal a[0..m) and
+// off-diagonal b[0..m-1), by bisection on Sturm counts (the number of eigenvalues below x is the
+// number of negative pivots of T - x I).
+int sturm_count(const double* a, const double* b, int m, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (int i = 0; i < m; ++i) {
+    const double off = (i > 0) ? b[i - 1] * b[i - 1] / q : 0.0;
+    q = a[i] - x - off;
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+void tridiag_extremes(const double* a, const double* b, int m, double* lo, double* hi) {
+  double glo = INFINITY, ghi = -INFINITY;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+    glo = std::min(glo, a[i] - r);
+    ghi = std::max(ghi, a[i] + r);
+  }
+  double l = glo, u = ghi;  // smallest: the least x with at least one eigenvalue below it
+  for (int it = 0; it < 200 && u - l > 1e-15 * (std::fabs(l) + std::fabs(u)); ++it) {
+    const double mid = 0.5 * (l + u);
+    if (sturm_count(a, b, m, mid) >= 1) u = mid; else l = mid;
+  }
+  *lo = u;
+  l = glo;
+  u = ghi;  // largest: the least x with all m eigenvalues below it
+  for (int it = 0; it < 200 && u - l > 1e-15 * (std::fabs(l) + std::fabs(u)); ++it) {
+    const double mid = 0.5 * (l + u);
+    if (sturm_count(a, b, m, mid) >= m) u = mid; else l = mid;
+  }
+  *hi = u;
+}
 
 gdm_status set_err(gdm_handle* h, gdm_status st, const char* fmt, ...) {
   if (h != nullptr) {
@@ -402,11 +442,16 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
     double* T = h->f[F_T];
     double* Dl = h->f[F_U];
     double* F = h->f[F_V];
+    // Exact diagonals (recomputed from the FP64 operands) for T, delta and Z F: when S is
+    // close to I the two factors of each have nearly parallel rows, the truncating FP32
+    // accumulators bias every diagonal entry the same way, and the refinement would then drive
+    // the computed delta to zero while the true Z^T S Z - I keeps that bias on its diagonal -
+    // an electron-count error of about bias x n_occ (measured 3.8e-5 at n = 8192).
     CK(product(h, zct, {S, &h->sl[SL_S]}, T, nullptr, nullptr, 1.0, 0.0, 0.0, false,
-               GDM_PHASE_REFINE));                                   // T = Z^T S
+               GDM_PHASE_REFINE, nullptr, true));                    // T = Z^T S
     CK(slice(h, T, &h->sl[SL_A], GDM_PHASE_REFINE));
     CK(product(h, {T, &h->sl[SL_A]}, zct, Dl, nullptr, nullptr, 1.0, 0.0, -1.0, true,
-               GDM_PHASE_REFINE));                                   // delta = Z^T S Z - I
+               GDM_PHASE_REFINE, nullptr, true));                    // delta = Z^T S Z - I
     double d2 = 0.0;
     st = dot(h, Dl, nullptr, 0, &d2);
     if (st != GDM_OK) return st;
@@ -427,7 +472,7 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
     double* Znew = h->f[F_X];
     double* Zt_new = h->f[F_X2];
     CK(product(h, zc, {F, &h->sl[SL_A]}, Znew, Zt_new, nullptr, 1.0, 0.0, 0.0, false,
-               GDM_PHASE_REFINE));                                   // Z <- Z F
+               GDM_PHASE_REFINE, nullptr, true));                    // Z <- Z F
     std::swap(h->f[F_Z], h->f[F_X]);
     std::swap(h->f[F_ZT], h->f[F_X2]);
     CK(slice(h, h->f[F_Z], &h->sl[SL_Z], GDM_PHASE_REFINE));
@@ -446,6 +491,58 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
   CK(slice(h, h->f[F_ZT], &h->sl[SL_ZT], GDM_PHASE_TRANSFORM));
   h->z_err = derr;
   h->z_valid = true;
+  return GDM_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// S-metric clean-up of the back-transformed density matrix
+// ------------------------------------------------------------------------------------------
+// McWeeny's map in the S metric, P' = 3 P S P - 2 P S P S P (the paper's conditions P S P = P,
+// Tr(P S) = n_occ, Eq. density_matrix_conditions, read in the non-orthogonal basis).  With
+// D = P S P - P it is P' = P S P - 2 D S P: two products of the transform's accuracy give P S
+// and P S P, and the product with the small D needs only the Newton-Schulz format.  When
+// P = Z X Z^T with X a projector and Z^T S Z = I + delta, Tr(P' S) - n_occ is O(delta^2)
+// instead of O(delta).  *s_idem = ||P S P - P||_F of the matrix it was given.  Writes the
+// result into F_XN (swapped with F_V).
+gdm_status metric_cleanup(gdm_handle* h, double* s_idem) {
+  const int n = static_cast<int>(h->n);
+  const int64_t ld = h->ld;
+  cudaStream_t s = h->stream;
+  double* P = h->f[F_XN];
+  double* S = h->f[F_S];
+  double* T = h->f[F_T];    // P S
+  double* PSP = h->f[F_U];
+  double* D = h->f[F_X2];
+  double* Pn = h->f[F_V];
+  const int ns_sl = slices_for(h, GDM_PHASE_NEWTON_SCHULZ);
+  CK(slice(h, P, &h->sl[SL_B], GDM_PHASE_TRANSFORM));
+  // S's slices from the refinement serve when that phase used the transform's format
+  Op s_op = {S, &h->sl[SL_S]};
+  const Precision& pr = h->phase[GDM_PHASE_REFINE];
+  const Precision& pt = h->phase[GDM_PHASE_TRANSFORM];
+  if (sliced(h, GDM_PHASE_TRANSFORM) &&
+      !(sliced(h, GDM_PHASE_REFINE) && pr.nslice == pt.nslice && pr.bits == pt.bits &&
+        h->sl[SL_S].nslice_valid >= pt.nslice && h->sl[SL_S].bits == pt.bits)) {
+    CK(slice(h, S, &h->sl[SL_X], GDM_PHASE_TRANSFORM));
+    s_op = {S, &h->sl[SL_X]};
+  }
+  CK(product(h, {P, &h->sl[SL_B]}, s_op, T, nullptr, nullptr, 1.0, 0.0, 0.0, false,
+             GDM_PHASE_TRANSFORM, nullptr, true));                   // T = P S
+  CK(slice(h, T, &h->sl[SL_A], GDM_PHASE_TRANSFORM));
+  CK(product(h, {T, &h->sl[SL_A]}, {P, &h->sl[SL_B]}, PSP, nullptr, nullptr, 1.0, 0.0, 0.0, true,
+             GDM_PHASE_TRANSFORM, nullptr, true));                   // P S P (symmetric)
+  CK(form_and_slice(PSP, ld, P, ld, n, n, nullptr, 1.0, -1.0, 0.0, D, ld,
+                    ns_sl > 0 ? &h->sl[SL_X2] : nullptr, ns_sl, nullptr, s,
+                    bits_for(h, GDM_PHASE_NEWTON_SCHULZ)));          // D = P S P - P
+  double d2 = 0.0;
+  gdm_status st = dot(h, D, nullptr, 0, &d2);
+  if (st != GDM_OK) return st;
+  *s_idem = std::sqrt(d2);
+  CK(slice(h, T, &h->sl[SL_W], GDM_PHASE_NEWTON_SCHULZ));
+  // P' = P S P - 2 D (P S)^T = P S P - 2 D S P, symmetric (D S P = P S P S P - P S P)
+  CK(product(h, {D, &h->sl[SL_X2]}, {T, &h->sl[SL_W]}, Pn, nullptr, PSP, -2.0, 1.0, 0.0, true,
+             GDM_PHASE_NEWTON_SCHULZ));
+  std::swap(h->f[F_XN], h->f[F_V]);
   return GDM_OK;
 }
 
@@ -477,29 +574,75 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   CK(product(h, {h->f[F_T], &h->sl[SL_B]}, Zt, Ht, nullptr, nullptr, 1.0, 0.0, 0.0, true,
              GDM_PHASE_TRANSFORM));
 
-  // bounds and X_0
-  CK(gershgorin(Ht, ld, n, h->partials, h->small + SM_BOUNDS_H, s));
-  if (h->purify == kPurifyCanonical)
-    CK(canonical_x0_coefficients(h->small + SM_BOUNDS_H, Ht, ld, n,
-                                 static_cast<double>(h->n_occ), h->small + SM_COEF_X0, s));
-  else
-    CK(x0_coefficients(h->small + SM_BOUNDS_H, h->small + SM_COEF_X0, s));
-  double bh[2];
-  st = read_small(h, SM_BOUNDS_H, 2, bh);
+  // Spectral bounds of H~ (Eq. ntpoly_scale_hamiltonian takes them "estimated"): Gershgorin's
+  // discs always enclose the spectrum but, for a dense H~, span it many times over, and the
+  // initial guess then squeezes the gap at n_occ by that factor - more purification steps, and
+  // every product's rounding is amplified by the inverse of that gap when it turns the occupied
+  // subspace.  The extreme Ritz values of a short Lanczos recurrence estimate the spectrum from
+  // inside; widened by 2% of their span (a margin that covers the Ritz values' distance from
+  // the extremes for smooth spectra many times over) and clamped to Gershgorin's interval, they
+  // give the bounds.  The purification tolerates eigenvalues a little outside [0, 1]
+  // (x = 1 + d maps to 1 + (gamma - 4) d^2, x = -d to gamma d^2 - 4 d^3); if it still fails, it
+  // restarts from Gershgorin's bounds.
+  CK(gershgorin(Ht, ld, n, h->partials, h->small + SM_GERSH_H, s));
+  const int lz = (h->bounds_method == GDM_BOUNDS_LANCZOS)
+                     ? static_cast<int>(std::min<int64_t>(h->lanczos_steps, n)) : 0;
+  if (lz > 0)
+    CK(lanczos(Ht, ld, n, lz, h->f[F_X], h->partials, h->small + SM_LANCZOS, s));
+  double sm[SM_LANCZOS + 2 * kMaxLanczos];
+  st = read_small(h, 0, SM_LANCZOS + 2 * lz, sm);
   if (st != GDM_OK) return st;
-  if (!std::isfinite(bh[0]) || !std::isfinite(bh[1]))
+  const double g_lo = sm[SM_GERSH_H], g_hi = sm[SM_GERSH_H + 1];
+  if (!std::isfinite(g_lo) || !std::isfinite(g_hi))
     return set_err(h, GDM_ERR_NONFINITE, "non-finite orthogonalised Hamiltonian");
-  if (info) {
-    info->eps_min = bh[0];
-    info->eps_max = bh[1];
+  if (!(g_hi > g_lo)) return set_err(h, GDM_ERR_NO_GAP, "degenerate spectrum bounds");
+  double l_lo = g_lo, l_hi = g_hi;
+  bool use_lanczos = false;
+  if (lz > 0) {
+    const double* la = sm + SM_LANCZOS;
+    const double* lb = la + lz;
+    int m = lz;
+    for (int k = 0; k < lz; ++k)
+      if (!(lb[k] > 0.0)) {  // the recurrence ended at step k: T is (k+1) x (k+1)
+        m = k + 1;
+        break;
+      }
+    bool finite = true;
+    for (int k = 0; k < m; ++k) finite = finite && std::isfinite(la[k]) && std::isfinite(lb[k]);
+    double t_lo = 0.0, t_hi = 0.0;
+    if (finite) tridiag_extremes(la, lb, m, &t_lo, &t_hi);
+    const double margin = 0.02 * (t_hi - t_lo) + 1e-12 * std::max(std::fabs(t_lo), std::fabs(t_hi));
+    l_lo = std::max(g_lo, t_lo - margin);
+    l_hi = std::min(g_hi, t_hi + margin);
+    use_lanczos = finite && std::isfinite(l_lo) && std::isfinite(l_hi) && l_hi > l_lo;
   }
-  if (!(bh[1] > bh[0])) return set_err(h, GDM_ERR_NO_GAP, "degenerate spectrum bounds");
   double* X = h->f[F_X];
   double* X2 = h->f[F_X2];
   double* Xn = h->f[F_XN];
   // truncated purification (gdm_set_truncation): every matrix entering a product is filtered
   TruncArgs trunc_args;
   const TruncArgs* tr = purify_trunc(h, &trunc_args);
+  const double tol_abs = h->idem_tol * static_cast<double>(h->n_occ);
+  double last_idem = INFINITY;
+  int it = 0;
+  int stop = 4;
+  double* W = h->f[F_V];
+  for (int attempt = use_lanczos ? 0 : 1; attempt < 2; ++attempt) {
+  const double bh[2] = {attempt == 0 ? l_lo : g_lo, attempt == 0 ? l_hi : g_hi};
+  h->host_buf[0] = bh[0];
+  h->host_buf[1] = bh[1];
+  CK(cudaMemcpyAsync(h->small + SM_BOUNDS_H, h->host_buf, 2 * sizeof(double),
+                     cudaMemcpyHostToDevice, s));
+  if (info) {
+    info->eps_min = bh[0];
+    info->eps_max = bh[1];
+    info->bounds_restart = attempt == 1 && use_lanczos ? 1 : 0;
+  }
+  if (h->purify == kPurifyCanonical)
+    CK(canonical_x0_coefficients(h->small + SM_BOUNDS_H, Ht, ld, n,
+                                 static_cast<double>(h->n_occ), h->small + SM_COEF_X0, s));
+  else
+    CK(x0_coefficients(h->small + SM_BOUNDS_H, h->small + SM_COEF_X0, s));
   h->kstages_dense = 0.0;
   h->kstages_issued = 0.0;
   if (tr != nullptr)
@@ -515,12 +658,10 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   init.method = h->purify;
   init.idem = INFINITY;
   CK(cudaMemcpyAsync(h->st_dev, &init, sizeof(init), cudaMemcpyHostToDevice, s));
-  const double tol_abs = h->idem_tol * static_cast<double>(h->n_occ);
   h->hist.clear();
-  double last_idem = INFINITY;
-  int it = 0;
-  int stop = 4;
-  double* W = h->f[F_V];
+  last_idem = INFINITY;
+  stop = 4;
+  bool failed = false;
   for (it = 0; it < h->max_purif; ++it) {
     CK(product(h, {X, &h->sl[SL_X]}, {X, &h->sl[SL_X]}, X2, nullptr, nullptr, 1.0, 0.0, 0.0, true,
                GDM_PHASE_PURIFY, nullptr, true));
@@ -543,6 +684,12 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
     CK(cudaStreamSynchronize(s));
     const Trs4State& t = *h->st_host;
     h->hist.push_back({t.idem, t.t[0], t.gamma, t.stop != 0 ? -1 : t.branch});
+    // a trace outside [0, n] means eigenvalues far outside [0, 1]: the bounds did not enclose
+    // the spectrum (only estimated bounds can do that)
+    if (attempt == 0 && (t.stop == 3 || !(t.t[0] > -0.5 && t.t[0] < static_cast<double>(n) + 0.5))) {
+      failed = true;
+      break;
+    }
     if (t.stop != 0) {
       stop = t.stop;
       // at the arithmetic's floor a further step only adds rounding: if this iterate is worse
@@ -590,6 +737,9 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
     }
     std::swap(X, Xn);
   }
+  if (attempt == 0 && failed) continue;  // again from Gershgorin's bounds
+  break;
+  }
   h->f[F_X] = X;
   h->f[F_XN] = Xn;
   if (info) {
@@ -625,21 +775,45 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
              GDM_PHASE_TRANSFORM));
   CK(slice(h, h->f[F_T], &h->sl[SL_A], GDM_PHASE_TRANSFORM));
   double* P = h->f[F_XN];
+  // exact diagonal: it carries the electron count Tr(P S) when S is close to I
   CK(product(h, {h->f[F_T], &h->sl[SL_A]}, Z, P, nullptr, nullptr, 1.0, 0.0, 0.0, true,
-             GDM_PHASE_TRANSFORM));
-  // Electron count in the S metric, then the final trace correction P <- P N / Tr(P S): the
-  // remaining count error comes from Z^T S Z - I (the accuracy to which the products resolve
-  // the overlap), and renormalising moves P by that same relative amount (about 1e-11).
+             GDM_PHASE_TRANSFORM, nullptr, true));
+  // Electron count in the S metric.  What can leave it off is Z^T S Z - I (the accuracy to
+  // which the products resolve the overlap) and the products of the back-transform: P = Z X Z^T
+  // is then a projector in a slightly different metric.  With the exact diagonals above, the
+  // count is within a few 1e-9 for well-conditioned overlaps (measured at n = 4362 and 8192)
+  // and about 1e-7 at cond(S) = 1e3, n = 4096, where the 38-bit products' resolution of
+  // Z^T S Z is the floor.  The optional S-metric McWeeny step restores P S P = P; the scalar
+  // rescale P <- P N / Tr(P S) is the last resort above 1e-8 and is reported when it fires.
   double trps = 0.0, e = 0.0;
   st = dot(h, P, h->f[F_S], 0, &trps);
   if (st != GDM_OK) return st;
   const double N = static_cast<double>(h->n_occ);
-  if (info) info->trace_err_raw = std::fabs(trps - N);
-  if (h->trace_correct && std::isfinite(trps) && trps > 0.0) {
+  if (info) {
+    info->trace_err_raw = std::fabs(trps - N);
+    info->s_idem_err = -1.0;
+    info->metric_cleanup = 0;
+    info->trace_rescaled = 0;
+  }
+  if (h->cleanup_tol >= 0.0 && std::isfinite(trps) && std::fabs(trps - N) > h->cleanup_tol) {
+    double s_idem = 0.0;
+    st = metric_cleanup(h, &s_idem);
+    if (st != GDM_OK) return st;
+    P = h->f[F_XN];
+    st = dot(h, P, h->f[F_S], 0, &trps);
+    if (st != GDM_OK) return st;
+    if (info) {
+      info->s_idem_err = s_idem;
+      info->metric_cleanup = 1;
+    }
+  }
+  if (h->trace_correct && std::isfinite(trps) && trps > 0.0 &&
+      std::fabs(trps - N) > h->rescale_tol) {
     CK(form_and_slice(P, ld, nullptr, 0, n, n, nullptr, N / trps, 0.0, 0.0, P, ld, nullptr, 0,
                       nullptr, s));
     st = dot(h, P, h->f[F_S], 0, &trps);
     if (st != GDM_OK) return st;
+    if (info) info->trace_rescaled = 1;
   }
   st = dot(h, P, H, 0, &e);
   if (st != GDM_OK) return st;
@@ -867,6 +1041,17 @@ gdm_status gdm_set_purification(gdm_handle* h, gdm_purification method) {
   return GDM_OK;
 }
 
+gdm_status gdm_set_bounds(gdm_handle* h, gdm_bounds method, int lanczos_steps) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  if (method != GDM_BOUNDS_GERSHGORIN && method != GDM_BOUNDS_LANCZOS)
+    return set_err(h, GDM_ERR_ARG, "unknown bounds method %d", static_cast<int>(method));
+  if (lanczos_steps < 0 || lanczos_steps > kMaxLanczos)
+    return set_err(h, GDM_ERR_ARG, "lanczos_steps must be 0..%d", kMaxLanczos);
+  h->bounds_method = static_cast<int>(method);
+  if (lanczos_steps > 0) h->lanczos_steps = lanczos_steps;
+  return GDM_OK;
+}
+
 gdm_status gdm_set_truncation(gdm_handle* h, double threshold) {
   if (h == nullptr) return GDM_ERR_ARG;
   if (!(threshold >= 0.0) || !std::isfinite(threshold))
@@ -938,6 +1123,13 @@ gdm_status gdm_get_profile(gdm_handle* h, int kind, int64_t* launches, double* m
 }
 
 int64_t gdm_launch_count(void) { return launch_count(); }
+
+gdm_status gdm_set_metric_cleanup(gdm_handle* h, double threshold) {
+  if (h == nullptr) return GDM_ERR_ARG;
+  if (std::isnan(threshold)) return set_err(h, GDM_ERR_ARG, "threshold is NaN");
+  h->cleanup_tol = threshold;
+  return GDM_OK;
+}
 
 gdm_status gdm_set_trace_correction(gdm_handle* h, int enable) {
   if (h == nullptr) return GDM_ERR_ARG;
@@ -1029,7 +1221,7 @@ gdm_status gdm_get_edm(gdm_handle* h, double* Q, int64_t ld, gdm_mem mem) {
              GDM_PHASE_TRANSFORM));
   CK(slice(h, T, &h->sl[SL_X], GDM_PHASE_TRANSFORM));
   CK(product(h, {T, &h->sl[SL_X]}, {P, &h->sl[SL_A]}, Qd, nullptr, nullptr, 1.0, 0.0, 0.0, true,
-             GDM_PHASE_TRANSFORM));
+             GDM_PHASE_TRANSFORM, nullptr, true));
   CK(cudaMemcpy2DAsync(Q, sizeof(double) * ld, Qd, sizeof(double) * h->ld,
                        sizeof(double) * h->n, static_cast<size_t>(h->n),
                        mem == GDM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
@@ -1072,7 +1264,7 @@ gdm_status gdm_extrapolate_dm(gdm_handle* h, const double* S_new, int64_t lds, g
   CK(slice(h, h->f[F_T], &h->sl[SL_A], GDM_PHASE_TRANSFORM));
   double* P1 = h->f[F_XN];
   CK(product(h, {h->f[F_T], &h->sl[SL_A]}, Z, P1, nullptr, nullptr, 1.0, 0.0, 0.0, true,
-             GDM_PHASE_TRANSFORM));
+             GDM_PHASE_TRANSFORM, nullptr, true));
   CK(cudaMemcpy2DAsync(P, sizeof(double) * ldp, P1, sizeof(double) * ld, sizeof(double) * h->n,
                        static_cast<size_t>(h->n),
                        mem_p == GDM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,

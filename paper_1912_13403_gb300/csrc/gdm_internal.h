@@ -164,6 +164,13 @@ cudaError_t power_bound(const double* A, int64_t lda, int n, int iters, double f
                         double* work, double* partials, double* bounds_dev, double* est_dev,
                         cudaStream_t stream);
 
+// `steps` Lanczos steps on the symmetric n x n matrix A from a fixed start vector (no
+// reorthogonalisation): ab_dev[k] = alpha_k and ab_dev[steps + k] = beta_k for k < steps, the
+// diagonal and off-diagonal of the tridiagonal whose extreme eigenvalues estimate A's from inside.
+// `work` holds >= 4 n doubles, `partials` >= n.
+cudaError_t lanczos(const double* A, int64_t lda, int n, int steps, double* work,
+                    double* partials, double* ab_dev, cudaStream_t stream);
+
 // Gershgorin bounds of a symmetric n x n matrix: writes {min_i(a_ii - r_i), max_i(a_ii + r_i)}
 // into out_dev[0..1].  `partials` holds >= 2 * ceil(n / 8) doubles.
 cudaError_t gershgorin(const double* A, int64_t lda, int n, double* partials, double* out_dev,

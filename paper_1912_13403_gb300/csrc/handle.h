@@ -40,7 +40,11 @@ struct gdm_handle {
   gdm::Precision phase[4] = {{2, 1, 12}, {4, 3, 9}, {4, 3, 9}, {3, 3, 12}};
   double idem_tol = 1e-13, trace_tol = 1e-6;
   bool trace_correct = true;
+  double cleanup_tol = -1.0;  // S-metric clean-up above this |Tr(P S) - n_occ| (< 0: never)
+  double rescale_tol = 1e-8;  // last-resort rescale above this |Tr(P S) - n_occ|
   int max_ns = 100, max_purif = 200, n_refine = 2;
+  int bounds_method = 1;   // gdm_bounds: spectral bounds of H~ for the initial guess
+  int lanczos_steps = 24;
 
   void* pool = nullptr;
   double* f[gdm::F_COUNT] = {};

@@ -375,7 +375,8 @@ def test_truncated_purification_matches_oracle_route(g, tau):
     # they compare step for step with the oracle's statement of that map; at the iteration cap
     # the engine resets Tr X to N, and so does the comparison
     assert all(b in (0, 1, 2) for (_, _, _, b) in histK[:K]), histK
-    lo, hi = steps.gershgorin_bounds(p.H)
+    # the oracle starts from the spectral bounds the engine used (its estimated ones)
+    lo, hi = infoK["eps_min"], infoK["eps_max"]
     XK = steps.filter_small(steps.initial_guess(p.H, lo, hi), tau)
     for _ in range(K):
         XK, _ = steps.trs4_filtered_step(XK, p.n_occ, tau)
@@ -387,7 +388,7 @@ def test_truncated_purification_matches_oracle_route(g, tau):
     # with the engine's controller restated: 4% at tau = 1e-7, 5% at tau = 1e-5)
     P, e, info, st = _trunc_solve(g, p, tau)
     assert st == g.GDM_OK, info
-    X, _ = steps.trs4_purify_truncated(p.H, p.n_occ, tau)
+    X, _ = steps.trs4_purify_truncated(p.H, p.n_occ, tau, bounds=(info["eps_min"], info["eps_max"]))
     err_oracle = rel(X, P_exact)
     assert rel(P, X) <= 0.25 * err_oracle, (rel(P, X), err_oracle)
     assert rel(P, P_exact) <= 1.5 * err_oracle + 1e-6
@@ -406,3 +407,99 @@ def test_truncated_purification_nonorthogonal_basis(g):
     assert info["trace_err"] <= TRACE
     with g.Handle(64, 10) as h:
         assert g.gdm_set_truncation(h._h, -1.0) == g.GDM_ERR_ARG
+
+
+# ------------------------------------------------------------------------------------------
+# Spectral bounds of H~ for the initial guess (Eq. ntpoly_scale_hamiltonian, "estimated")
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["dense", "dftb"])
+def test_lanczos_bounds_enclose_and_tighten(g, case):
+    # the generalised eigenvalues of the construction are H~'s spectrum (up to rounding)
+    p = (make_spectrum_problem(51, 1024, 256, cond_S=1e3, gap=0.2) if case == "dense"
+         else make_config2(52, n=1024, n_occ=256))
+    lam = p.factors["lam"]
+    Pc, _ = steps.closed_form_dm(p.factors, p.n_occ)
+    out = {}
+    for method in (g.GDM_BOUNDS_GERSHGORIN, g.GDM_BOUNDS_LANCZOS):
+        with g.Handle(p.n, p.n_occ) as h:
+            h.set_bounds(method)
+            h.set_overlap(p.S)
+            h.set_hamiltonian(p.H)
+            P, e, info, st = h.solve()
+        assert st == g.GDM_OK, info
+        assert rel(P, Pc) <= REL_P, (method, rel(P, Pc))
+        assert info["trace_err"] <= TRACE
+        assert info["bounds_restart"] == 0
+        span = lam[-1] - lam[0]
+        assert info["eps_min"] <= lam[0] - 1e-9 * span and info["eps_max"] >= lam[-1] + 1e-9 * span
+        out[method] = (info["eps_max"] - info["eps_min"]) / span, info["purif_iters"], rel(P, Pc)
+    width_g, it_g, err_g = out[g.GDM_BOUNDS_GERSHGORIN]
+    width_l, it_l, err_l = out[g.GDM_BOUNDS_LANCZOS]
+    assert width_l <= 1.1 and width_l < width_g, out   # 2% margin each side
+    assert it_l <= it_g, out
+
+
+def test_too_tight_estimate_restarts_from_gershgorin(g):
+    # one Lanczos step estimates a single point: the initial guess then lies far outside [0, 1],
+    # the purification leaves the trace range, and the solve runs again from Gershgorin's bounds
+    p = make_random_small(61, 200, 50)
+    ref = oracle.density_matrix(p.H, p.S, p.n_occ)
+    with g.Handle(p.n, p.n_occ) as h:
+        h.set_bounds(g.GDM_BOUNDS_LANCZOS, 1)
+        h.set_overlap(p.S)
+        h.set_hamiltonian(p.H)
+        P, e, info, st = h.solve()
+        assert st == g.GDM_OK, info
+        assert info["bounds_restart"] == 1
+        assert rel(P, ref["P"]) <= REL_P
+        assert g.gdm_set_bounds(h._h, 7, 0) == g.GDM_ERR_ARG
+        assert g.gdm_set_bounds(h._h, g.GDM_BOUNDS_LANCZOS, 65) == g.GDM_ERR_ARG
+
+
+# ------------------------------------------------------------------------------------------
+# Electron count in the S metric (Eq. density_matrix_conditions: P S P = P, Tr(P S) = n_occ)
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["near_identity_S", "cond1e3"])
+def test_count_without_rescale_and_metric_cleanup(g, case):
+    # the count that the route leaves: within 1e-8 for a well-conditioned overlap; at
+    # cond(S) = 1e3 the 38-bit products resolve Z^T S Z - I to about 1e-8 per unit count here,
+    # and the last-resort rescale (on by default) takes what is above 1e-8
+    if case == "near_identity_S":
+        p = make_request_problem(dict(seed=91, n=1024, n_occ=256, gap=0.2))
+    else:
+        p = make_spectrum_problem(92, 1024, 256, cond_S=1e3, gap=0.2)
+    Pc, Ec = steps.closed_form_dm(p.factors, p.n_occ)
+    raw_bar = TRACE if case == "near_identity_S" else 1e-7
+    with g.Handle(p.n, p.n_occ) as h:
+        h.set_overlap(p.S)
+        h.set_hamiltonian(p.H)
+        Pd, ed, idf, std = h.solve()                      # defaults
+        assert std == g.GDM_OK, idf
+        assert idf["metric_cleanup"] == 0 and idf["s_idem_err"] == -1.0
+        assert idf["trace_err_raw"] <= raw_bar, idf
+        assert idf["trace_rescaled"] == (1 if idf["trace_err_raw"] > TRACE else 0)
+        assert idf["trace_err"] <= TRACE
+        h.set_trace_correction(False)                     # neither correction
+        P0, e0, i0, st0 = h.solve()
+        assert st0 == g.GDM_OK, i0
+        assert i0["trace_rescaled"] == 0 and i0["trace_err"] == i0["trace_err_raw"]
+        assert rel(P0, Pc) <= REL_P
+        h.set_metric_cleanup(0.0)                         # the S-metric step forced on
+        P1, e1, i1, st1 = h.solve()
+    assert st1 in (g.GDM_OK, g.GDM_ERR_NOT_CONVERGED), i1
+    assert i1["metric_cleanup"] == 1 and i1["trace_rescaled"] == 0
+    assert rel(P1, Pc) <= REL_P
+    assert abs(e1 - Ec) <= REL_P * abs(Ec)
+    assert np.array_equal(P1, P1.T)
+    # the reported ||P S P - P||_F of the matrix it was given (computed with the transform's
+    # products, so to a few per cent)
+    d0 = np.linalg.norm(P0 @ p.S @ P0 - P0)
+    assert abs(i1["s_idem_err"] - d0) <= 0.1 * d0, (i1["s_idem_err"], d0)
+    if case == "near_identity_S":
+        # well conditioned: P S P = P several times closer, the count still within 1e-8
+        assert np.linalg.norm(P1 @ p.S @ P1 - P1) <= 0.3 * d0
+        assert i1["trace_err"] <= TRACE, i1
+    with g.Handle(64, 10) as h:
+        assert g.gdm_set_metric_cleanup(h._h, float("nan")) == g.GDM_ERR_ARG

@@ -1364,6 +1364,14 @@ __global__ void trs4_control_kernel(const double* partials, int nblocks, Trs4Sta
                                     double tol_idem) {
   __shared__ double red[32];
   __shared__ double t[kTraceTerms];
+  // A finished problem of a lockstep batch keeps its state and takes no further step.
+  if (st->done) {
+    if (threadIdx.x == 0) {
+      st->skip_gemm = 1;
+      st->skip_form_x = 1;
+    }
+    return;
+  }
   reduce_terms(partials, nblocks, kTraceTerms, t, red);
   __syncthreads();
   if (threadIdx.x != 0) return;
@@ -1386,7 +1394,22 @@ __global__ void trs4_control_kernel(const double* partials, int nblocks, Trs4Sta
   } else if (fabs(idem) < 1e-4 * Nf && fabs(idem) > 0.5 * fabs(st->idem_prev)) {
     stop = 2;  // the idempotency error no longer falls: the arithmetic's floor is reached
   }
+  if (stop == 0 && st->max_iter > 0 && st->iter >= st->max_iter) stop = 4;
+  // Estimated spectral bounds that missed part of the spectrum leave Tr X outside [0, n].
+  if (st->check_trace && (!(t[0] > -0.5) || !(t[0] < st->n + 0.5))) {
+    stop = 3;
+    st->failed = 1;
+  }
   st->stop = stop;
+  if (stop != 0) {
+    // the iterate of this iteration is final, or the previous one if it was better (at the
+    // floor a further step only adds rounding); its buffer is the iteration's parity, or the
+    // other one
+    st->done = 1;
+    const int revert = (stop == 2 && st->iter > 0 && fabs(idem) > fabs(st->idem_prev)) ? 1 : 0;
+    st->final_buf = (st->iter & 1) ^ revert;
+    st->final_idem = revert ? st->idem_prev : idem;
+  }
   // Endgame.  Once Tr(X - X^2) < 0.1 every eigenvalue x has x(1-x) < 0.1, i.e. it lies within
   // 0.113 of 0 or 1, and with |Tr X - N| < 0.25 exactly N of them are near 1.  From there the
   // McWeeny map 3X^2 - 2X^3 = X^2 (3I - 2X) takes each to the nearer end (quadratically) and
@@ -1688,7 +1711,9 @@ __global__ void symmetrise_kernel(double* A, int64_t lda, int n) {
 __global__ void __launch_bounds__(kRowsPerBlock * 32)
     diag_fix_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ Bt,
                     int64_t ldb, double* C, int64_t ldc, int n, int K, double alpha, double beta,
-                    const double* D, int64_t ldd, double diag, const double* coef) {
+                    const double* D, int64_t ldd, double diag, const double* coef,
+                    const int* skip) {
+  if (skip != nullptr && *skip != 0) return;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * kRowsPerBlock + w;
   if (row >= n) return;
@@ -2106,12 +2131,13 @@ cudaError_t symmetrise(double* A, int64_t lda, int n, cudaStream_t stream) {
 
 cudaError_t diag_fix(const double* A, int64_t lda, const double* Bt, int64_t ldb, double* C,
                      int64_t ldc, int n, int K, double alpha, double beta, const double* D,
-                     int64_t ldd, double diag, const double* coef, cudaStream_t stream) {
+                     int64_t ldd, double diag, const double* coef, cudaStream_t stream,
+                     const int* skip) {
   if (n <= 0) return cudaSuccess;
   const int nb = (n + kRowsPerBlock - 1) / kRowsPerBlock;
   count_launch();
   diag_fix_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, Bt, ldb, C, ldc, n, K, alpha,
-                                                         beta, D, ldd, diag, coef);
+                                                         beta, D, ldd, diag, coef, skip);
   return cudaGetLastError();
 }
 

@@ -90,6 +90,20 @@ struct SlicedGemmArgs {
   const int* skip = nullptr;          // optional device flag: non-zero -> no-op launch
   uint32_t* err = nullptr;
   int tiles_n = 0, tiles_m = 0;
+  // grouped launch (sliced_gemm_grouped): the products of a device table, one after another
+  // in the unit order; each entry's own fields describe its product, these only its format
+  const struct GroupItem* group = nullptr;
+  int ngroup = 0, group_units = 0;
+  int unit_begin = 0;                 // grouped: first unit of this product in the launch
+};
+
+// One product of a grouped launch: its operands' tensor maps (global memory, 64-byte aligned)
+// and its arguments (C, leading dimensions, epilogue coefficients, row scales, skip flag, M, N,
+// K, tiles, unit_begin); the format fields of `a` are ignored.
+struct alignas(64) GroupItem {
+  CUtensorMap ta;
+  CUtensorMap tb;
+  SlicedGemmArgs a;
 };
 
 // Number of kernels this library has launched since it was loaded (all threads).
@@ -99,6 +113,25 @@ int64_t launch_count();
 int build_pairs(int nslice, int max_order, SlicedGemmArgs* a);
 cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& Bt, const Precision& prec,
                         SlicedGemmArgs args, cudaStream_t stream);
+
+// Grouped products.  sliced_gemm_group_item fills one table entry for C = alpha A Bt^T (+ ...)
+// from the operands' slice buffers and `args` (C, ldc, mode, alpha, ...; skip is the entry's
+// own flag); sliced_gemm_grouped then runs every entry of the device table `items` (count
+// entries, built with the same format `prec`) in one persistent launch: the CTAs walk the
+// 128 x 128 tiles of all products, entries in table order.  Returns cudaErrorInvalidValue for
+// operands that do not fit the format.  The k split of the last wave is not used here.
+// `bk` is the k extent of the operands' tensor-map boxes: grouped_variant_bk(nslice, variant)
+// of the variant the launch will use.  group_assign_units sets each entry's unit_begin (table
+// order) and returns the launch's unit count.
+cudaError_t sliced_gemm_group_item(const SliceBuf& A, const SliceBuf& Bt, const Precision& prec,
+                                   const SlicedGemmArgs& args, GroupItem* item, int bk);
+int group_assign_units(GroupItem* items, int count);
+cudaError_t sliced_gemm_grouped(const GroupItem* items_dev, int count, int total_units,
+                                const Precision& prec, uint32_t* err, cudaStream_t stream,
+                                int variant = 0);
+// (BK, stages) variants of the grouped kernel for a slice count (the autotuner's choices).
+int grouped_variant_count(int nslice);
+int grouped_variant_bk(int nslice, int variant);
 
 // K elements per pipeline stage of sliced_gemm for a format with `nslice` slices.
 int sliced_gemm_bk(int nslice);
@@ -218,9 +251,17 @@ struct Trs4State {
                           // 4: X W (canonical)
   int skip_gemm;          // 1 unless branch 2 or 3
   int skip_form_x;        // 1 when branch 2 or 3
-  int stop;               // 1: converged (X is final), 2: stalled, 3: non-finite
+  int stop;               // 1: converged (X is final), 2: stalled, 3: non-finite, 4: cap
   int iter;
   int stall;
+  // lockstep batches (zero in a single solve, which leaves the loop at the first stop):
+  int done;               // set at the first stop; later controls change nothing
+  int final_buf;          // 0: the final iterate is in the iteration's even buffer, 1: odd
+  double final_idem;
+  int max_iter;           // > 0: stop with 4 once iter reaches it
+  int check_trace;        // 1: a trace outside [-0.5, n + 0.5] stops with 3 and sets failed
+  int failed;
+  double n;               // matrix size (for check_trace)
 };
 cudaError_t trs4_control(const double* partials, int nblocks, Trs4State* st, double tol_idem,
                          cudaStream_t stream);
@@ -242,7 +283,8 @@ cudaError_t scale_coefficients(const double* bounds_dev, int inv_sqrt, double* c
 // coef when non-null).  Run after the sliced product (see elementwise.cu).
 cudaError_t diag_fix(const double* A, int64_t lda, const double* Bt, int64_t ldb, double* C,
                      int64_t ldc, int n, int K, double alpha, double beta, const double* D,
-                     int64_t ldd, double diag, const double* coef, cudaStream_t stream);
+                     int64_t ldd, double diag, const double* coef, cudaStream_t stream,
+                     const int* skip = nullptr);
 
 // X <- X * target / Tr X (trace in FP64); fix_out (device, 2 doubles) = {target/Tr X - 1,
 // target/Tr X}.

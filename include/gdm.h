@@ -289,18 +289,41 @@ typedef struct {
   double latency_ms;  /* batch: solve wall time; server: submission to completion */
 } gdm_result;
 
+/* How a batch runs:
+ *   GDM_BATCH_GROUPED     (default, mixed precision) every problem advances in lockstep and each
+ *                         product step of all problems is one persistent grouped launch of the
+ *                         sliced tensor-core kernel over a device table of the problems'
+ *                         products; the phases run as CUDA graphs captured once per batch shape
+ *                         and replayed, with each problem's control flags on the device (the host
+ *                         reads them once per four iterations).  The grouped kernel's k tile and
+ *                         stage count per slice format are chosen by timing them on the batch's
+ *                         largest product, remembered in the JSON file named by the environment
+ *                         variable GDM_AUTOTUNE_CACHE (default ~/.cache/gdm_autotune.json).  A
+ *                         problem that fails in the lockstep is solved again alone.  latency_ms is
+ *                         the batch's wall time for every problem.
+ *   GDM_BATCH_CONCURRENT  worker threads, each with its own handle and stream, solve the problems
+ *                         one by one (largest first); their kernels overlap on the device.  Used
+ *                         for GDM_PREC_FP64 either way. */
+typedef enum { GDM_BATCH_GROUPED = 0, GDM_BATCH_CONCURRENT = 1 } gdm_batch_engine;
+
 typedef struct {
   int device;               /* CUDA device */
-  int concurrency;          /* concurrent solves (worker threads / streams); <= 0: 4 */
+  int concurrency;          /* GDM_BATCH_CONCURRENT: worker threads / streams; <= 0: 4 */
   gdm_precision precision;  /* GDM_PREC_MIXED (0-initialised structs give FP64: set it) */
+  int engine;               /* gdm_batch_engine */
 } gdm_batch_config;
 
-/* Solve `count` independent problems of any sizes; results[i] belongs to problems[i].  Larger
- * problems start first.  cfg may be NULL (device 0, 4 concurrent, mixed precision).  Blocks
- * until all are done.  Returns GDM_OK, or the first failing problem's status (every result
- * is filled either way); GDM_ERR_ARG before any work for an invalid problem. */
+/* Solve `count` independent problems of any sizes; results[i] belongs to problems[i].  cfg may
+ * be NULL (device 0, grouped, mixed precision).  Blocks until all are done.  The grouped engine
+ * keeps the device memory of the last batch shape (one handle per problem, ~144 n^2 bytes each)
+ * for the next call with the same sizes; gdm_batch_release frees it.  Returns GDM_OK, or the
+ * first failing problem's status (every result is filled either way); GDM_ERR_ARG before any
+ * work for an invalid problem or engine. */
 gdm_status gdm_solve_batch(const gdm_problem* problems, int count, gdm_result* results,
                            const gdm_batch_config* cfg);
+
+/* Free the grouped batch engine's cached device memory and graphs (a later batch rebuilds). */
+void gdm_batch_release(void);
 
 typedef struct gdm_server gdm_server; /* opaque */
 

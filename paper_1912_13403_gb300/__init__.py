@@ -30,6 +30,7 @@ GDM_PREC_FP64, GDM_PREC_MIXED = 0, 1
 GDM_PURIFY_TRS4, GDM_PURIFY_TRS2, GDM_PURIFY_CANONICAL = 0, 1, 2
 GDM_PHASE_NEWTON_SCHULZ, GDM_PHASE_REFINE, GDM_PHASE_TRANSFORM, GDM_PHASE_PURIFY = range(4)
 GDM_BOUNDS_GERSHGORIN, GDM_BOUNDS_LANCZOS = 0, 1
+GDM_BATCH_GROUPED, GDM_BATCH_CONCURRENT = 0, 1
 
 
 class gdm_info(ctypes.Structure):
@@ -66,7 +67,7 @@ class gdm_result(ctypes.Structure):
 
 class gdm_batch_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("concurrency", ctypes.c_int),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("engine", ctypes.c_int)]
 
 
 class gdm_server_config(ctypes.Structure):
@@ -114,6 +115,7 @@ _decl("gdm_reinit", _int, [_vp])
 _decl("gdm_finalize", _int, [_vp])
 _decl("gdm_status_string", ctypes.c_char_p, [_int])
 _decl("gdm_last_error", ctypes.c_char_p, [_vp])
+_decl("gdm_batch_release", None, [])
 _decl("gdm_solve_batch", _int, [ctypes.POINTER(gdm_problem), _int, ctypes.POINTER(gdm_result),
                                 ctypes.POINTER(gdm_batch_config)])
 _decl("gdm_server_create", _int, [ctypes.POINTER(_vp), ctypes.POINTER(gdm_server_config)])
@@ -361,14 +363,21 @@ def _problem(H, S, n_occ, P=None):
     return p
 
 
-def solve_batch(items, concurrency=4, precision=GDM_PREC_MIXED, device=0):
-    """Solve a list of (H, S, n_occ, P) tuples concurrently (gdm_solve_batch).  P may be None.
-    Returns (status, list of result dicts)."""
+def solve_batch(items, concurrency=4, precision=GDM_PREC_MIXED, device=0,
+                engine=GDM_BATCH_GROUPED):
+    """Solve a list of (H, S, n_occ, P) tuples as one batch (gdm_solve_batch): by default in
+    lockstep with grouped products (GDM_BATCH_GROUPED), or as concurrent solves
+    (GDM_BATCH_CONCURRENT).  P may be None.  Returns (status, list of result dicts)."""
     arr = (gdm_problem * len(items))(*[_problem(*it) for it in items])
     res = (gdm_result * len(items))()
-    cfg = gdm_batch_config(device, concurrency, precision)
+    cfg = gdm_batch_config(device, concurrency, precision, engine)
     st = gdm_solve_batch(arr, len(items), res, ctypes.byref(cfg))
     return st, [r.as_dict() for r in res]
+
+
+def batch_release():
+    """Free the grouped batch engine's cached device memory (gdm_batch_release)."""
+    gdm_batch_release()
 
 
 class Server:

@@ -911,9 +911,9 @@ __global__ void __launch_bounds__(THREADS)
 // sums, diagonals exact).  Both rows are read once.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS)
-    slice_traces_kernel(const double* X2, const double* X, int64_t ld, int n, __half* out,
-                        double* out_scale, int64_t out_ld, int64_t plane, int nslice, int bits,
-                        double* partials, const int* skip) {
+    slice_traces_kernel(const double* X2, const double* X, int64_t ld, int n, int cols,
+                        __half* out, double* out_scale, int64_t out_ld, int64_t plane, int nslice,
+                        int bits, double* partials, const int* skip) {
   __shared__ float red_ss[THREADS / 32];
   __shared__ DF red_dot[3][THREADS / 32];
   __shared__ unsigned long long diag_sh[2];
@@ -922,7 +922,7 @@ __global__ void __launch_bounds__(THREADS)
   const int row = blockIdx.x;
   if (row >= n) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int npairs = n >> 1;
+  const int npairs = cols >> 1;  // cols = n, or n + 1 over a zero column
   const uint4* yr = reinterpret_cast<const uint4*>(X2 + row * ld);
   const uint4* xr = reinterpret_cast<const uint4*>(X + row * ld);
   uint4 v[kFusedPPT], x[kFusedPPT];
@@ -1021,8 +1021,9 @@ __global__ void w_row_dots_kernel(const double* __restrict__ partials, int n,
 template <int THREADS, bool HAS_B>
 __global__ void __launch_bounds__(THREADS)
     dot_rows_kernel(const double* A, int64_t lda, const double* B, int64_t ldb, int cols,
-                    int minus_identity, double* partials) {
+                    int minus_identity, double* partials, const int* skip) {
   __shared__ DF red[THREADS / 32];
+  if (skip != nullptr && *skip != 0) return;
   const int row = blockIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int npairs = cols >> 1;
@@ -1192,9 +1193,10 @@ __global__ void minmax_reduce_kernel(const double* partials, int nblocks, double
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRowsPerBlock * 32)
     trs4_traces_kernel(const double* __restrict__ X, const double* __restrict__ X2, int64_t ld,
-                       int n, double* partials) {
+                       int n, double* partials, const int* skip) {
   // <X2, X>, ||X2||^2 and ||X||^2 in FP32 double-float (no FP64 ALU), diagonals exact
   __shared__ double s[kRowsPerBlock][kTraceTerms];
+  if (skip != nullptr && *skip != 0) return;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * kRowsPerBlock + w;
   double t[kTraceTerms] = {0, 0, 0, 0, 0};
@@ -1265,9 +1267,11 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32)
 
 __global__ void __launch_bounds__(kRowsPerBlock * 32)
     dot_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ B,
-               int64_t ldb, int rows, int cols, int minus_identity, double* partials) {
+               int64_t ldb, int rows, int cols, int minus_identity, double* partials,
+               const int* skip) {
   // FP32 double-float accumulation (no FP64 ALU)
   __shared__ double s[kRowsPerBlock];
+  if (skip != nullptr && *skip != 0) return;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * kRowsPerBlock + w;
   double r = 0.0;
@@ -1674,6 +1678,80 @@ __global__ void lanczos_update_kernel(double* y, double* v, double* vprev, float
   }
 }
 
+// Number of eigenvalues below x of the tridiagonal (a, b) (negative pivots of T - x I).
+__device__ int sturm_count_dev(const double* a, const double* b, int m, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (int i = 0; i < m; ++i) {
+    const double off = (i > 0) ? b[i - 1] * b[i - 1] / q : 0.0;
+    q = a[i] - x - off;
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// Spectral bounds of H~ from the Lanczos tridiagonal (small + lanczos_at) and Gershgorin's
+// interval (small + gersh_at): the extreme Ritz values by bisection, widened by 2% of their
+// span and clamped to Gershgorin's interval, into small[bounds_at..+1]; small[bounds_at+2] = 1 when
+// the estimate (not Gershgorin's interval) is used.
+__global__ void lanczos_bounds_kernel(double* small, int steps, int gersh_at, int lanczos_at,
+                                      int bounds_at) {
+  // one warp: each multisection round evaluates 32 Sturm counts at once and shrinks the
+  // interval 33-fold, so the two extremes take ~10 rounds each
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  const double g_lo = small[gersh_at], g_hi = small[gersh_at + 1];
+  const double* a = small + lanczos_at;
+  const double* b = a + steps;
+  int m = steps;
+  for (int k = 0; k < steps; ++k)
+    if (!(b[k] > 0.0)) {
+      m = k + 1;
+      break;
+    }
+  bool finite = true;
+  double glo = INFINITY, ghi = -INFINITY;
+  for (int i = 0; i < m; ++i) {
+    finite = finite && isfinite(a[i]) && isfinite(b[i]);
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < m ? fabs(b[i]) : 0.0);
+    glo = fmin(glo, a[i] - r);
+    ghi = fmax(ghi, a[i] + r);
+  }
+  double lo = g_lo, hi = g_hi;
+  if (finite) {
+    double t[2];
+    for (int end = 0; end < 2; ++end) {
+      // end 0: the least x with at least one eigenvalue below it; end 1: with all m below it
+      const int want = (end == 0) ? 1 : m;
+      double l = glo, u = ghi;
+      for (int it = 0; it < 64 && u - l > 1e-15 * (fabs(l) + fabs(u)); ++it) {
+        const double x = l + (u - l) * (lane + 1) / 33.0;
+        const bool above = sturm_count_dev(a, b, m, x) >= want;
+        const unsigned mask = __ballot_sync(0xffffffffu, above);
+        // the first point at or above the target bounds it from above, the one before from below
+        const int first = mask ? __ffs(mask) - 1 : 32;
+        const double nu = (first < 32) ? l + (u - l) * (first + 1) / 33.0 : u;
+        const double nl = (first > 0) ? l + (u - l) * first / 33.0 : l;
+        l = nl;
+        u = nu;
+      }
+      t[end] = u;
+    }
+    const double margin = 0.02 * (t[1] - t[0]) + 1e-12 * fmax(fabs(t[0]), fabs(t[1]));
+    const double c_lo = fmax(g_lo, t[0] - margin), c_hi = fmin(g_hi, t[1] + margin);
+    if (isfinite(c_lo) && isfinite(c_hi) && c_hi > c_lo) {
+      lo = c_lo;
+      hi = c_hi;
+    }
+  }
+  if (lane == 0) {
+    small[bounds_at] = lo;
+    small[bounds_at + 1] = hi;
+    small[bounds_at + 2] = (lo == g_lo && hi == g_hi) ? 0.0 : 1.0;  // 1: the estimate was used
+  }
+}
+
 __global__ void scale_coef_kernel(const double* bounds, int inv_sqrt, double* coef) {
   const double c = bounds[1];
   coef[0] = inv_sqrt ? 1.0 / sqrt(c) : 1.0 / c;
@@ -1805,11 +1883,18 @@ __global__ void identity_kernel(double* A, int64_t lda, int n) {
 }  // namespace
 
 cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64_t ldx2,
-                           int rows, int cols, const double* coef_dev, double ha, double hb,
-                           double hc, double* Y, int64_t ldy, SliceBuf* out, int nslice,
-                           const int* skip, cudaStream_t stream, int bits, int dot,
-                           const TruncArgs* trunc) {
+                           int rows, int cols_logical, const double* coef_dev, double ha,
+                           double hb, double hc, double* Y, int64_t ldy, SliceBuf* out,
+                           int nslice, const int* skip, cudaStream_t stream, int bits, int dot,
+                           const TruncArgs* trunc, bool zero_pad) {
   if (rows <= 0) return cudaSuccess;
+  // an odd row length with a zero column after it in every buffer is processed as the even one
+  // (the paired kernels), and the logical shape stays the caller's
+  const int cols = (zero_pad && (cols_logical & 1) && ldx > cols_logical &&
+                    (X2 == nullptr || ldx2 > cols_logical) &&
+                    (Y == nullptr || ldy > cols_logical) &&
+                    (out == nullptr || nslice <= 0 || out->ld > cols_logical))
+                       ? cols_logical + 1 : cols_logical;
   if (bits < 9 || bits > 12) return cudaErrorInvalidValue;
   if (dot == kDotX2 && X2 == nullptr) return cudaErrorInvalidValue;
   TruncArgs tr;
@@ -1843,7 +1928,7 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
     old = out->ld;
     plane = static_cast<int64_t>(out->ld) * out->rows_alloc;
     out->rows = rows;
-    out->cols = cols;
+    out->cols = cols_logical;
     out->nslice_valid = nslice;
     out->bits = bits;
     out->dot_partner = nullptr;
@@ -1984,6 +2069,13 @@ cudaError_t lanczos(const double* A, int64_t lda, int n, int steps, double* work
   return cudaGetLastError();
 }
 
+cudaError_t lanczos_bounds(double* small, int steps, int gersh_at, int lanczos_at, int bounds_at,
+                           cudaStream_t stream) {
+  count_launch();
+  lanczos_bounds_kernel<<<1, 32, 0, stream>>>(small, steps, gersh_at, lanczos_at, bounds_at);
+  return cudaGetLastError();
+}
+
 cudaError_t gershgorin(const double* A, int64_t lda, int n, double* partials, double* out_dev,
                        cudaStream_t stream) {
   const int nb = (n + kRowsPerBlock - 1) / kRowsPerBlock;
@@ -1995,19 +2087,21 @@ cudaError_t gershgorin(const double* A, int64_t lda, int n, double* partials, do
 }
 
 cudaError_t trs4_traces(const double* X, const double* X2, int64_t ld, int n, double* partials,
-                        int* nblocks, cudaStream_t stream) {
+                        int* nblocks, cudaStream_t stream, const int* skip) {
   const int nb = (n + kRowsPerBlock - 1) / kRowsPerBlock;
   count_launch();
-  trs4_traces_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(X, X2, ld, n, partials);
+  trs4_traces_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(X, X2, ld, n, partials, skip);
   *nblocks = nb;
   return cudaGetLastError();
 }
 
 cudaError_t slice_traces(const double* X2, const double* X, int64_t ld, int n, SliceBuf* out,
-                         int nslice, int bits, double* partials, int* nrows, cudaStream_t stream) {
+                         int nslice, int bits, double* partials, int* nrows, cudaStream_t stream,
+                         const int* skip, bool zero_pad) {
   *nrows = 0;
   if (n <= 0) return cudaSuccess;
-  if (!slice_traces_fits(X2, X, ld, n, out, nslice)) return cudaErrorInvalidValue;
+  if (!slice_traces_fits(X2, X, ld, n, out, nslice, zero_pad)) return cudaErrorInvalidValue;
+  const int cols = (n & 1) ? n + 1 : n;
   out->mask_valid = false;
   out->rows = n;
   out->cols = n;
@@ -2015,20 +2109,20 @@ cudaError_t slice_traces(const double* X2, const double* X, int64_t ld, int n, S
   out->bits = bits;
   out->dot_partner = nullptr;
   const int64_t plane = static_cast<int64_t>(out->ld) * out->rows_alloc;
-  const int npairs = n / 2;
+  const int npairs = cols / 2;
   count_launch();
   if (npairs <= 128 * kFusedPPT)
-    slice_traces_kernel<128><<<n, 128, 0, stream>>>(X2, X, ld, n, out->data, out->row_scale,
-                                                   out->ld, plane, nslice, bits, partials,
-                                                   nullptr);
+    slice_traces_kernel<128><<<n, 128, 0, stream>>>(X2, X, ld, n, cols, out->data,
+                                                   out->row_scale, out->ld, plane, nslice, bits,
+                                                   partials, skip);
   else if (npairs <= 256 * kFusedPPT)
-    slice_traces_kernel<256><<<n, 256, 0, stream>>>(X2, X, ld, n, out->data, out->row_scale,
-                                                   out->ld, plane, nslice, bits, partials,
-                                                   nullptr);
+    slice_traces_kernel<256><<<n, 256, 0, stream>>>(X2, X, ld, n, cols, out->data,
+                                                   out->row_scale, out->ld, plane, nslice, bits,
+                                                   partials, skip);
   else
-    slice_traces_kernel<512><<<n, 512, 0, stream>>>(X2, X, ld, n, out->data, out->row_scale,
-                                                   out->ld, plane, nslice, bits, partials,
-                                                   nullptr);
+    slice_traces_kernel<512><<<n, 512, 0, stream>>>(X2, X, ld, n, cols, out->data,
+                                                   out->row_scale, out->ld, plane, nslice, bits,
+                                                   partials, skip);
   *nrows = n;
   return cudaGetLastError();
 }
@@ -2043,16 +2137,22 @@ cudaError_t w_row_dots(const double* partials, int n, const double* coef_dev, Sl
 }
 
 bool slice_traces_fits(const double* X2, const double* X, int64_t ld, int n, const SliceBuf* out,
-                       int nslice) {
-  return out != nullptr && nslice >= 1 && nslice <= 4 && n % 2 == 0 && ld % 2 == 0 &&
-         n <= kFusedMaxCols && out->ld >= n && out->rows_alloc >= n && out->ld % 2 == 0 &&
+                       int nslice, bool zero_pad) {
+  // an odd n needs the zero column after the rows (zero_pad) in X, X2 and the slices
+  const int cols = (n & 1) ? n + 1 : n;
+  return out != nullptr && nslice >= 1 && nslice <= 4 && ((n & 1) == 0 || zero_pad) &&
+         ld % 2 == 0 && ld >= cols && cols <= kFusedMaxCols && out->ld >= cols &&
+         out->rows_alloc >= n && out->ld % 2 == 0 &&
          ((reinterpret_cast<uintptr_t>(X2) | reinterpret_cast<uintptr_t>(X)) & 15) == 0 &&
          (reinterpret_cast<uintptr_t>(out->data) & 3) == 0;
 }
 
 cudaError_t dot_partials(const double* A, int64_t lda, const double* B, int64_t ldb, int rows,
-                         int cols, int minus_identity, double* partials, int* nblocks,
-                         cudaStream_t stream) {
+                         int cols_logical, int minus_identity, double* partials, int* nblocks,
+                         cudaStream_t stream, const int* skip, bool zero_pad) {
+  const int cols = (zero_pad && (cols_logical & 1) && lda > cols_logical &&
+                    (B == nullptr || ldb > cols_logical))
+                       ? cols_logical + 1 : cols_logical;
   const bool rows_fit =
       cols % 2 == 0 && cols <= kFusedMaxCols && lda % 2 == 0 &&
       ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
@@ -2064,10 +2164,10 @@ cudaError_t dot_partials(const double* A, int64_t lda, const double* B, int64_t 
 #define GDM_DOTROWS(T)                                                                         \
   if (B != nullptr)                                                                            \
     dot_rows_kernel<T, true><<<rows, T, 0, stream>>>(A, lda, B, ldb, cols, minus_identity,     \
-                                                     partials);                                \
+                                                     partials, skip);                          \
   else                                                                                         \
     dot_rows_kernel<T, false><<<rows, T, 0, stream>>>(A, lda, B, ldb, cols, minus_identity,    \
-                                                      partials)
+                                                      partials, skip)
     if (npairs <= 128 * kFusedPPT) {
       GDM_DOTROWS(128);
     } else if (npairs <= 256 * kFusedPPT) {
@@ -2082,7 +2182,7 @@ cudaError_t dot_partials(const double* A, int64_t lda, const double* B, int64_t 
   const int nb = (rows + kRowsPerBlock - 1) / kRowsPerBlock;
   count_launch();
   dot_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, B, ldb, rows, cols, minus_identity,
-                                                    partials);
+                                                    partials, skip);
   *nblocks = nb;
   return cudaGetLastError();
 }
@@ -2148,6 +2248,18 @@ cudaError_t trace_scale(double* X, int64_t ld, int n, double target, double* fix
   trace_factor_kernel<<<1, 1024, 0, stream>>>(X, ld, n, target, fix_out);
   count_launch();
   scale_rows_kernel<<<n, 256, 0, stream>>>(X, ld, n, fix_out);
+  return cudaGetLastError();
+}
+
+__global__ void zero_column_kernel(double* A, int64_t lda, int rows, int col) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x)
+    A[i * lda + col] = 0.0;
+}
+
+cudaError_t zero_column(double* A, int64_t lda, int rows, int col, cudaStream_t stream) {
+  if (rows <= 0 || col >= lda) return cudaSuccess;
+  count_launch();
+  zero_column_kernel<<<(rows + 255) / 256, 256, 0, stream>>>(A, lda, rows, col);
   return cudaGetLastError();
 }
 

@@ -31,56 +31,6 @@ using namespace gdm;
 
 namespace {
 
-// small[] layout
-enum SmallSlot {
-  SM_BOUNDS_S = 0,   // 2
-  SM_BOUNDS_H = 2,   // 2
-  SM_COEF_A = 4,     // 3
-  SM_COEF_B = 8,     // 3
-  SM_COEF_X0 = 12,   // 3
-  SM_RED = 16,       // 8 reduction outputs
-  SM_KCOUNT = 24,    // 1: k stages issued by masked products (as an unsigned 64-bit count)
-  SM_GERSH_H = 26,   // 2: Gershgorin bounds of H~
-  SM_LANCZOS = 32,   // 2 x kMaxLanczos: alpha_k, then beta_k, of the Lanczos recurrence on H~
-};
-constexpr int kMaxLanczos = 64;
-
-// Extreme eigenvalues of the symmetric tridiagonal matrix with diagonal a[0..m) and
-// off-diagonal b[0..m-1), by bisection on Sturm counts (the number of eigenvalues below x is the
-// number of negative pivots of T - x I).
-int sturm_count(const double* a, const double* b, int m, double x) {
-  int cnt = 0;
-  double q = 1.0;
-  for (int i = 0; i < m; ++i) {
-    const double off = (i > 0) ? b[i - 1] * b[i - 1] / q : 0.0;
-    q = a[i] - x - off;
-    if (q == 0.0) q = -1e-300;
-    if (q < 0.0) ++cnt;
-  }
-  return cnt;
-}
-
-void tridiag_extremes(const double* a, const double* b, int m, double* lo, double* hi) {
-  double glo = INFINITY, ghi = -INFINITY;
-  for (int i = 0; i < m; ++i) {
-    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
-    glo = std::min(glo, a[i] - r);
-    ghi = std::max(ghi, a[i] + r);
-  }
-  double l = glo, u = ghi;  // smallest: the least x with at least one eigenvalue below it
-  for (int it = 0; it < 200 && u - l > 1e-15 * (std::fabs(l) + std::fabs(u)); ++it) {
-    const double mid = 0.5 * (l + u);
-    if (sturm_count(a, b, m, mid) >= 1) u = mid; else l = mid;
-  }
-  *lo = u;
-  l = glo;
-  u = ghi;  // largest: the least x with all m eigenvalues below it
-  for (int it = 0; it < 200 && u - l > 1e-15 * (std::fabs(l) + std::fabs(u)); ++it) {
-    const double mid = 0.5 * (l + u);
-    if (sturm_count(a, b, m, mid) >= m) u = mid; else l = mid;
-  }
-  *hi = u;
-}
 
 gdm_status set_err(gdm_handle* h, gdm_status st, const char* fmt, ...) {
   if (h != nullptr) {
@@ -288,10 +238,11 @@ cudaError_t slice(gdm_handle* h, const double* src, SliceBuf* dst, int ph, int d
     if (trunc == nullptr) return cudaSuccess;
     // FP64 products: filter the matrix in place (no slices)
     return form_and_slice(src, h->ld, nullptr, 0, n, n, nullptr, 1.0, 0.0, 0.0, nullptr, 0,
-                          nullptr, 0, nullptr, h->stream, 12, kDotNone, trunc);
+                          nullptr, 0, nullptr, h->stream, 12, kDotNone, trunc, true);
   }
   return form_and_slice(src, h->ld, nullptr, 0, n, n, nullptr, 1.0, 0.0, 0.0, nullptr, 0, dst,
-                        h->phase[ph].nslice, nullptr, h->stream, h->phase[ph].bits, dot, trunc);
+                        h->phase[ph].nslice, nullptr, h->stream, h->phase[ph].bits, dot, trunc,
+                        true);
 }
 
 int bits_for(const gdm_handle* h, int ph) { return h->phase[ph].bits; }
@@ -310,7 +261,8 @@ gdm_status dot(gdm_handle* h, const double* A, const double* B, int minus_identi
                double* out) {
   const int n = static_cast<int>(h->n);
   int nb = 0;
-  CK(dot_partials(A, h->ld, B, h->ld, n, n, minus_identity, h->partials, &nb, h->stream));
+  CK(dot_partials(A, h->ld, B, h->ld, n, n, minus_identity, h->partials, &nb, h->stream,
+                  nullptr, true));
   CK(reduce_partials(h->partials, nb, 1, h->small + SM_RED, h->stream));
   return read_small(h, SM_RED, 1, out);
 }
@@ -372,7 +324,7 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
     CK(scale_coefficients(bounds, 0, coef_inv, s));
     CK(scale_coefficients(bounds, 1, coef_isqrt, s));
     CK(form_and_slice(S, ld, nullptr, 0, n, n, coef_inv, 0, 0, 0, Y, ld, ns_sl > 0 ? sY : nullptr,
-                      ns_sl, nullptr, s, bits_for(h, GDM_PHASE_NEWTON_SCHULZ)));
+                      ns_sl, nullptr, s, bits_for(h, GDM_PHASE_NEWTON_SCHULZ), kDotNone, nullptr, true));
     CK(set_identity(Z, ld, n, s));
     CK(slice(h, Z, sZ, GDM_PHASE_NEWTON_SCHULZ));
     prev = INFINITY;
@@ -410,10 +362,10 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
       // are plain products (no addend in the epilogue)
       CK(form_and_slice(M, ld, nullptr, 0, n, n, nullptr, -0.5, 0.0, 1.5, M, ld,
                         ns_sl > 0 ? sM : nullptr, ns_sl, nullptr, s,
-                        bits_for(h, GDM_PHASE_NEWTON_SCHULZ)));
+                        bits_for(h, GDM_PHASE_NEWTON_SCHULZ), kDotNone, nullptr, true));
       CK(form_and_slice(Mt, ld, nullptr, 0, n, n, nullptr, -0.5, 0.0, 1.5, Mt, ld,
                         ns_sl > 0 ? sMt : nullptr, ns_sl, nullptr, s,
-                        bits_for(h, GDM_PHASE_NEWTON_SCHULZ)));
+                        bits_for(h, GDM_PHASE_NEWTON_SCHULZ), kDotNone, nullptr, true));
       CK(product(h, {M, sM}, {Y, sY}, Yn, nullptr, nullptr, 1.0, 0.0, 0.0, true,
                  GDM_PHASE_NEWTON_SCHULZ));
       CK(product(h, {Mt, sMt}, {Z, sZ}, Zn, nullptr, nullptr, 1.0, 0.0, 0.0, true,
@@ -432,7 +384,7 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
   double* Zc = h->f[F_Z];
   CK(form_and_slice(Z, ld, nullptr, 0, n, n, coef_isqrt, 0, 0, 0, Zc, ld,
                     ref_sl > 0 ? &h->sl[SL_Z] : nullptr, ref_sl, nullptr, s,
-                    bits_for(h, GDM_PHASE_REFINE)));
+                    bits_for(h, GDM_PHASE_REFINE), kDotNone, nullptr, true));
   CK(slice(h, S, &h->sl[SL_S], GDM_PHASE_REFINE));
   Op zc = {Zc, &h->sl[SL_Z]};
   Op zct = zc;
@@ -533,7 +485,7 @@ gdm_status metric_cleanup(gdm_handle* h, double* s_idem) {
              GDM_PHASE_TRANSFORM, nullptr, true));                   // P S P (symmetric)
   CK(form_and_slice(PSP, ld, P, ld, n, n, nullptr, 1.0, -1.0, 0.0, D, ld,
                     ns_sl > 0 ? &h->sl[SL_X2] : nullptr, ns_sl, nullptr, s,
-                    bits_for(h, GDM_PHASE_NEWTON_SCHULZ)));          // D = P S P - P
+                    bits_for(h, GDM_PHASE_NEWTON_SCHULZ), kDotNone, nullptr, true));          // D = P S P - P
   double d2 = 0.0;
   gdm_status st = dot(h, D, nullptr, 0, &d2);
   if (st != GDM_OK) return st;
@@ -587,35 +539,20 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   CK(gershgorin(Ht, ld, n, h->partials, h->small + SM_GERSH_H, s));
   const int lz = (h->bounds_method == GDM_BOUNDS_LANCZOS)
                      ? static_cast<int>(std::min<int64_t>(h->lanczos_steps, n)) : 0;
-  if (lz > 0)
+  if (lz > 0) {
     CK(lanczos(Ht, ld, n, lz, h->f[F_X], h->partials, h->small + SM_LANCZOS, s));
-  double sm[SM_LANCZOS + 2 * kMaxLanczos];
-  st = read_small(h, 0, SM_LANCZOS + 2 * lz, sm);
+    CK(lanczos_bounds(h->small, lz, SM_GERSH_H, SM_LANCZOS, SM_EST_H, s));
+  }
+  double sm[SM_EST_H + 3];
+  st = read_small(h, 0, SM_EST_H + 3, sm);
   if (st != GDM_OK) return st;
   const double g_lo = sm[SM_GERSH_H], g_hi = sm[SM_GERSH_H + 1];
   if (!std::isfinite(g_lo) || !std::isfinite(g_hi))
     return set_err(h, GDM_ERR_NONFINITE, "non-finite orthogonalised Hamiltonian");
   if (!(g_hi > g_lo)) return set_err(h, GDM_ERR_NO_GAP, "degenerate spectrum bounds");
-  double l_lo = g_lo, l_hi = g_hi;
-  bool use_lanczos = false;
-  if (lz > 0) {
-    const double* la = sm + SM_LANCZOS;
-    const double* lb = la + lz;
-    int m = lz;
-    for (int k = 0; k < lz; ++k)
-      if (!(lb[k] > 0.0)) {  // the recurrence ended at step k: T is (k+1) x (k+1)
-        m = k + 1;
-        break;
-      }
-    bool finite = true;
-    for (int k = 0; k < m; ++k) finite = finite && std::isfinite(la[k]) && std::isfinite(lb[k]);
-    double t_lo = 0.0, t_hi = 0.0;
-    if (finite) tridiag_extremes(la, lb, m, &t_lo, &t_hi);
-    const double margin = 0.02 * (t_hi - t_lo) + 1e-12 * std::max(std::fabs(t_lo), std::fabs(t_hi));
-    l_lo = std::max(g_lo, t_lo - margin);
-    l_hi = std::min(g_hi, t_hi + margin);
-    use_lanczos = finite && std::isfinite(l_lo) && std::isfinite(l_hi) && l_hi > l_lo;
-  }
+  const bool use_lanczos = lz > 0 && sm[SM_EST_H + 2] != 0.0;
+  const double l_lo = use_lanczos ? sm[SM_EST_H] : g_lo;
+  const double l_hi = use_lanczos ? sm[SM_EST_H + 1] : g_hi;
   double* X = h->f[F_X];
   double* X2 = h->f[F_X2];
   double* Xn = h->f[F_XN];
@@ -649,7 +586,7 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
     CK(cudaMemsetAsync(h->small + SM_KCOUNT, 0, sizeof(unsigned long long), s));
   CK(form_and_slice(Ht, ld, nullptr, 0, n, n, h->small + SM_COEF_X0, 0, 0, 0, X, ld,
                     pu_sl > 0 ? &h->sl[SL_X] : nullptr, pu_sl, nullptr, s,
-                    bits_for(h, GDM_PHASE_PURIFY), kDotSelf, tr));
+                    bits_for(h, GDM_PHASE_PURIFY), kDotSelf, tr, true));
 
   // TRS4
   Trs4State init;
@@ -672,9 +609,9 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
     if (tr != nullptr) {
       CK(slice(h, X2, &h->sl[SL_X2], GDM_PHASE_PURIFY, kDotNone, tr));
       x2_sliced = true;
-    } else if (pu_sl > 0 && slice_traces_fits(X2, X, ld, n, &h->sl[SL_X2], pu_sl)) {
+    } else if (pu_sl > 0 && slice_traces_fits(X2, X, ld, n, &h->sl[SL_X2], pu_sl, true)) {
       CK(slice_traces(X2, X, ld, n, &h->sl[SL_X2], pu_sl, bits_for(h, GDM_PHASE_PURIFY),
-                      h->partials, &nb, s));
+                      h->partials, &nb, s, nullptr, true));
       x2_sliced = true;
       row_terms = true;
     }
@@ -707,7 +644,7 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
     if (t.branch == 4) {  // canonical: X <- X W, W = a X + b X^2 + c I (X's slices are current)
       CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefW)), 0, 0, 0,
                         W, ld, pu_sl > 0 ? &h->sl[SL_W] : nullptr, pu_sl, nullptr, s,
-                        bits_for(h, GDM_PHASE_PURIFY), kDotX, tr));
+                        bits_for(h, GDM_PHASE_PURIFY), kDotX, tr, true));
       CK(product(h, {X, &h->sl[SL_X]}, {W, &h->sl[SL_W]}, Xn, nullptr, nullptr, 1.0, 0.0, 0.0,
                  tr == nullptr, GDM_PHASE_PURIFY, nullptr, true));
       if (tr != nullptr) CK(symmetrise(Xn, ld, n, s));
@@ -716,14 +653,14 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
       if (!x2_sliced) CK(slice(h, X2, &h->sl[SL_X2], GDM_PHASE_PURIFY));
       // W itself is needed only with filtering or FP64 products (the sliced product takes its
       // diagonal from the row dot products with X^2)
-      const bool need_w = tr != nullptr || pu_sl == 0 || n % 2 != 0 || n > kFusedMaxCols;
+      const bool need_w = tr != nullptr || pu_sl == 0 || n + (n & 1) > kFusedMaxCols;
       // W's row dot products with X^2 follow from the per-row trace terms when slice_traces
       // produced them (no filtering): a <X_i, X2_i> + b ||X2_i||^2 + c (X2)_ii
       const bool dots_from_traces = row_terms;
       const double* coefW = st_field(h, offsetof(Trs4State, coefW));
       CK(form_and_slice(X, ld, X2, ld, n, n, coefW, 0, 0, 0, need_w ? W : nullptr, ld,
                         pu_sl > 0 ? &h->sl[SL_W] : nullptr, pu_sl, nullptr, s,
-                        bits_for(h, GDM_PHASE_PURIFY), dots_from_traces ? kDotNone : kDotX2, tr));
+                        bits_for(h, GDM_PHASE_PURIFY), dots_from_traces ? kDotNone : kDotX2, tr, true));
       if (dots_from_traces) CK(w_row_dots(h->partials, n, coefW, &h->sl[SL_W], X2, s));
       // with filtering X^2 and W no longer commute: the full product is symmetrised
       CK(product(h, {X2, &h->sl[SL_X2]}, {W, &h->sl[SL_W]}, Xn, nullptr, nullptr, 1.0, 0.0, 0.0,
@@ -733,7 +670,7 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
     } else {
       CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefX)), 0, 0, 0,
                         Xn, ld, pu_sl > 0 ? &h->sl[SL_X] : nullptr, pu_sl, nullptr, s,
-                        bits_for(h, GDM_PHASE_PURIFY), kDotSelf, tr));
+                        bits_for(h, GDM_PHASE_PURIFY), kDotSelf, tr, true));
     }
     std::swap(X, Xn);
   }
@@ -810,7 +747,7 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   if (h->trace_correct && std::isfinite(trps) && trps > 0.0 &&
       std::fabs(trps - N) > h->rescale_tol) {
     CK(form_and_slice(P, ld, nullptr, 0, n, n, nullptr, N / trps, 0.0, 0.0, P, ld, nullptr, 0,
-                      nullptr, s));
+                      nullptr, s, 12, kDotNone, nullptr, true));
     st = dot(h, P, h->f[F_S], 0, &trps);
     if (st != GDM_OK) return st;
     if (info) info->trace_rescaled = 1;
@@ -913,6 +850,13 @@ gdm_status handle_reconfigure(gdm_handle* h, int64_t n, int64_t n_occ) {
                    static_cast<long long>(h->n_cap));
   h->n = n;
   h->n_occ = n_occ;
+  // the column after the n columns of every buffer must be zero (the paired kernels read it
+  // for an odd n); a larger earlier problem left data there
+  if (n < h->ld)
+    for (int i = 0; i < F_COUNT; ++i)
+      if (zero_column(h->f[i], h->ld, static_cast<int>(n), static_cast<int>(n), h->stream) !=
+          cudaSuccess)
+        return set_err(h, GDM_ERR_CUDA, "zeroing the padding column failed");
   h->have_H = false;
   h->have_S = false;
   h->have_P = false;

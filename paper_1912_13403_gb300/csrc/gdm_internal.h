@@ -97,10 +97,10 @@ struct SlicedGemmArgs {
   int unit_begin = 0;                 // grouped: first unit of this product in the launch
 };
 
-// One product of a grouped launch: its operands' tensor maps (global memory, 64-byte aligned)
-// and its arguments (C, leading dimensions, epilogue coefficients, row scales, skip flag, M, N,
-// K, tiles, unit_begin); the format fields of `a` are ignored.
-struct alignas(64) GroupItem {
+// One product of a grouped launch: its operands' tensor maps (global memory, aligned as
+// CUtensorMap requires) and its arguments (C, leading dimensions, epilogue coefficients, row
+// scales, skip flag, M, N, K, tiles, unit_begin); the format fields of `a` are ignored.
+struct GroupItem {
   CUtensorMap ta;
   CUtensorMap tb;
   SlicedGemmArgs a;
@@ -183,11 +183,17 @@ enum { kPurifyTrs4 = 0, kPurifyTrs2 = 1, kPurifyCanonical = 2 };
 // registers); wider or unaligned rows take two passes, which need Y when the forming is not
 // plain and a row dot product is asked for.
 constexpr int kFusedMaxCols = 8192;
+// zero_pad: the caller guarantees a zero column after the `cols` columns of X, X2 and Y (and
+// room for it in the slices): an odd `cols` is then processed as the even cols + 1 by the paired
+// one-pass kernels (the engine's buffers keep that column zero).
 cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64_t ldx2,
                            int rows, int cols, const double* coef_dev, double ha, double hb,
                            double hc, double* Y, int64_t ldy, SliceBuf* out, int nslice,
                            const int* skip, cudaStream_t stream, int bits = 12,
-                           int dot = kDotNone, const TruncArgs* trunc = nullptr);
+                           int dot = kDotNone, const TruncArgs* trunc = nullptr,
+                           bool zero_pad = false);
+// A[i, col] = 0 for i < rows (the zero column after an odd n).
+cudaError_t zero_column(double* A, int64_t lda, int rows, int col, cudaStream_t stream);
 
 // Power iteration for lambda_max of a symmetric positive matrix (iters matrix-vector products
 // in double-float from a fixed start vector), then bounds_dev[1] <- min(bounds_dev[1],
@@ -204,6 +210,14 @@ cudaError_t power_bound(const double* A, int64_t lda, int n, int iters, double f
 cudaError_t lanczos(const double* A, int64_t lda, int n, int steps, double* work,
                     double* partials, double* ab_dev, cudaStream_t stream);
 
+// Spectral bounds from a Lanczos tridiagonal (small[lanczos_at..]: alpha_0..alpha_{steps-1},
+// beta_0..beta_{steps-1}) and Gershgorin's interval (small[gersh_at..+1]): the extreme Ritz values
+// by bisection on Sturm counts, widened by 2% of their span and clamped to Gershgorin's
+// interval, into small[bounds_at..+1]; small[bounds_at + 2] = 1 when the estimate is used, 0
+// when Gershgorin's interval is (a non-finite or degenerate recurrence).  One device thread.
+cudaError_t lanczos_bounds(double* small, int steps, int gersh_at, int lanczos_at, int bounds_at,
+                           cudaStream_t stream);
+
 // Gershgorin bounds of a symmetric n x n matrix: writes {min_i(a_ii - r_i), max_i(a_ii + r_i)}
 // into out_dev[0..1].  `partials` holds >= 2 * ceil(n / 8) doubles.
 cudaError_t gershgorin(const double* A, int64_t lda, int n, double* partials, double* out_dev,
@@ -215,23 +229,26 @@ constexpr int kTraceTerms = 5;
 // TRS4 trace terms per row (partials: n x kTraceTerms) and the slices of X2 in one pass;
 // slice_traces_fits says whether the shapes and alignments allow it.
 cudaError_t slice_traces(const double* X2, const double* X, int64_t ld, int n, SliceBuf* out,
-                         int nslice, int bits, double* partials, int* nrows, cudaStream_t stream);
+                         int nslice, int bits, double* partials, int* nrows, cudaStream_t stream,
+                         const int* skip = nullptr, bool zero_pad = false);
 bool slice_traces_fits(const double* X2, const double* X, int64_t ld, int n, const SliceBuf* out,
-                       int nslice);
+                       int nslice, bool zero_pad = false);
 // w->row_dot[i] = <W_i, X2_i> for W = coef[0] X + coef[1] X2 + coef[2] I, from slice_traces'
 // per-row terms (so the slicing of W needs no row dot); records X2 as w's dot partner.
 cudaError_t w_row_dots(const double* partials, int n, const double* coef_dev, SliceBuf* w,
                        const double* X2, cudaStream_t stream);
 cudaError_t trs4_traces(const double* X, const double* X2, int64_t ld, int n, double* partials,
-                        int* nblocks, cudaStream_t stream);
+                        int* nblocks, cudaStream_t stream, const int* skip = nullptr);
 
+// (skip: a non-zero flag makes the launch a no-op, for the problems of a lockstep batch that
+// have finished.)
 // Deterministic partial dot products of sum_ij A_ij B_ij (B null -> A_ij^2), with an optional
 // -1 on the diagonal of A first when `minus_identity` (||A - I||^2): one partial per row (rows of
 // at most kFusedMaxCols columns), else one per block of rows; *nblocks gives the count, and
 // partials must hold `rows` doubles.
 cudaError_t dot_partials(const double* A, int64_t lda, const double* B, int64_t ldb, int rows,
                          int cols, int minus_identity, double* partials, int* nblocks,
-                         cudaStream_t stream);
+                         cudaStream_t stream, const int* skip = nullptr, bool zero_pad = false);
 cudaError_t reduce_partials(const double* partials, int nblocks, int nterms, double* out_dev,
                             cudaStream_t stream);
 

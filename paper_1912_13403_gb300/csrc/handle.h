@@ -13,6 +13,23 @@ namespace gdm {
 
 enum FBuf { F_H, F_S, F_Z, F_ZT, F_X, F_X2, F_XN, F_T, F_U, F_V, F_COUNT };
 enum SBuf { SL_S, SL_Z, SL_ZT, SL_A, SL_B, SL_X, SL_X2, SL_W, SL_COUNT };
+// Layout of a handle's small[] device scratch (doubles)
+enum SmallSlot {
+  SM_BOUNDS_S = 0,   // 2
+  SM_BOUNDS_H = 2,   // 2
+  SM_COEF_A = 4,     // 3
+  SM_COEF_B = 8,     // 3
+  SM_COEF_X0 = 12,   // 3
+  SM_RED = 16,       // 8 reduction outputs
+  SM_KCOUNT = 24,    // 1: k stages issued by masked products (as an unsigned 64-bit count)
+  SM_GERSH_H = 26,   // 2: Gershgorin bounds of H~
+  SM_EST_H = 28,     // 3: estimated bounds of H~ and whether the estimate was used
+  SM_LANCZOS = 32,   // 2 x kMaxLanczos: alpha_k, then beta_k, of the Lanczos recurrence on H~
+};
+constexpr int kMaxLanczos = 64;
+  // lockstep batches: the problem's BatchCtl (batch.cu) from this double on
+constexpr int SM_BATCH = 256;
+
 constexpr int kSplitTiles = 160;  // split-k: most tiles split at once (>= the SM count)
 constexpr int kSmall = 4096;  // doubles of small device scratch beyond the partials
 

@@ -90,6 +90,17 @@ bool valid_problem(const gdm_problem& p) {
 // ==========================================================================================
 // batch
 // ==========================================================================================
+namespace gdm {
+gdm_status batch_solve_grouped(const gdm_problem* pr, int count, gdm_result* res, int device,
+                               std::vector<int>* resolve);
+void batch_release();
+}  // namespace gdm
+
+namespace {
+gdm_status solve_concurrent(const gdm_problem* problems, int count, gdm_result* results,
+                            int device, int conc, gdm_precision prec);
+}  // namespace
+
 extern "C" gdm_status gdm_solve_batch(const gdm_problem* problems, int count, gdm_result* results,
                                       const gdm_batch_config* cfg) {
   if (count < 0 || (count > 0 && (problems == nullptr || results == nullptr))) return GDM_ERR_ARG;
@@ -98,8 +109,42 @@ extern "C" gdm_status gdm_solve_batch(const gdm_problem* problems, int count, gd
   const int device = cfg ? cfg->device : 0;
   int conc = (cfg && cfg->concurrency > 0) ? cfg->concurrency : 4;
   const gdm_precision prec = cfg ? cfg->precision : GDM_PREC_MIXED;
-  if (conc > count) conc = count;
+  const int engine = cfg ? cfg->engine : GDM_BATCH_GROUPED;
+  if (engine != GDM_BATCH_GROUPED && engine != GDM_BATCH_CONCURRENT) return GDM_ERR_ARG;
   if (count == 0) return GDM_OK;
+  if (prec != GDM_PREC_MIXED || engine == GDM_BATCH_CONCURRENT)
+    return solve_concurrent(problems, count, results, device, conc, prec);
+  // lockstep grouped batch; problems that fail in the lockstep are solved again alone
+  std::vector<int> resolve;
+  gdm_status st = batch_solve_grouped(problems, count, results, device, &resolve);
+  if (st != GDM_OK) return st;
+  std::vector<gdm_problem> again;
+  std::vector<int> where;
+  for (int i = 0; i < count; ++i)
+    if (resolve[i]) {
+      again.push_back(problems[i]);
+      where.push_back(i);
+    }
+  if (!again.empty()) {
+    std::vector<gdm_result> r2(again.size());
+    solve_concurrent(again.data(), static_cast<int>(again.size()), r2.data(), device, conc, prec);
+    for (size_t k = 0; k < again.size(); ++k) {
+      r2[k].latency_ms += results[where[k]].latency_ms;
+      results[where[k]] = r2[k];
+    }
+  }
+  for (int i = 0; i < count; ++i)
+    if (results[i].status != GDM_OK && results[i].status != GDM_ERR_NOT_CONVERGED)
+      return results[i].status;
+  return GDM_OK;
+}
+
+extern "C" void gdm_batch_release(void) { batch_release(); }
+
+namespace {
+gdm_status solve_concurrent(const gdm_problem* problems, int count, gdm_result* results,
+                            int device, int conc, gdm_precision prec) {
+  if (conc > count) conc = count;
   // largest first, so each worker's first problem sizes its handle for the rest
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
@@ -132,6 +177,7 @@ extern "C" gdm_status gdm_solve_batch(const gdm_problem* problems, int count, gd
       return results[i].status;
   return GDM_OK;
 }
+}  // namespace
 
 // ==========================================================================================
 // server

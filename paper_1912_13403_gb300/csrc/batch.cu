@@ -8,7 +8,7 @@
 // control kernels set from its reductions - Newton-Schulz converged or diverged, refinement
 // done, the TRS4 branch, stop - and every kernel that could overwrite a finished problem's
 // result reads a skip flag.  The phases are captured once per batch shape as CUDA graphs:
-//   pre   ingest-independent set-up: S bounds, Y_0 = S / c, Z_0 = I, slices
+//   pre   S's bounds (Gershgorin, Lanczos), the scale c, Y_0 = S / c, Z_0 = I, slices
 //   ns    two unrolled Newton-Schulz iterations (buffers alternate by iteration parity)
 //   rf    the Z refinement (unrolled: three evaluations of Z^T S Z - I, two updates), H~,
 //         spectral bounds (Gershgorin + Lanczos + bisection on the device), X_0
@@ -55,6 +55,8 @@ struct BatchCtl {
   int rescaled;    // the last-resort count rescale fired
   int pad_;
   double ns_prev, rf_prev, rf_derr, count_raw, factor;
+  double ns_l;       // lower end of M's spectrum for the scaled Newton-Schulz steps
+  double ns_coef[3]; // T = coef[0] M + coef[2] I of this step
 };
 static_assert(sizeof(BatchCtl) <= 512, "BatchCtl fits the small[] tail");
 
@@ -63,6 +65,7 @@ namespace {
 constexpr int kSideStreams = 16;
 constexpr int kNref = 2;         // refinement updates at most (as the single engine)
 constexpr int kLanczosSteps = 24;
+constexpr int kLanczosS = 16;  // as the single engine (engine.cu)
 
 __global__ void batch_init_kernel(BatchCtl* c, Trs4State* st, double n_occ, int n, int max_purif) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -78,8 +81,27 @@ __global__ void batch_init_kernel(BatchCtl* c, Trs4State* st, double n_occ, int 
   st->n = static_cast<double>(n);
 }
 
+// The single engine's Newton-Schulz eigenvalue map and step scale (engine.cu, compute_z).
+__device__ double ns_g_dev(double x) { return x * (3.0 - x) * (3.0 - x) * 0.25; }
+__device__ double ns_alpha_dev(int it, double l) {
+  if (it == 0 || !(l > 0.0) || l >= 0.3) return 1.0;
+  const double r = sqrt(l);
+  return fmin(2.9, 3.0 / (1.0 + r + l));
+}
+
+// The scale c of S (1.05 x the largest Ritz value, at most Gershgorin's bound) into
+// small[SM_BOUNDS_S + 1], and the lower end l = smallest Ritz value / c of the first step.
+__global__ void ns_init_kernel(double* small, BatchCtl* c) {
+  const double g_hi = small[SM_BOUNDS_S + 1];
+  const double rmin = small[SM_EST_S + 3], rmax = small[SM_EST_S + 4];
+  const double sc = (rmax > 0.0 && isfinite(rmax)) ? fmin(g_hi, 1.05 * rmax) : g_hi;
+  small[SM_BOUNDS_S + 1] = sc;
+  c->ns_l = (rmin > 0.0 && isfinite(rmin)) ? fmin(1.0, rmin / sc) : 1.0;
+}
+
 // After M = Y Z and ||I - M||_F^2 in *red: the single engine's stopping rules (hand over at
-// ||I - M||_F <= handoff, the rounding floor, or a stall below 1e-2 sqrt n; divergence).
+// ||I - M||_F <= handoff, the rounding floor, or a stall below 1e-2 sqrt n; divergence), then
+// the coefficients of this step's T = sqrt(alpha) (3I - alpha M)/2.
 __global__ void ns_control_kernel(BatchCtl* c, const double* red, double rn, double handoff,
                                   int parity, int max_ns) {
   if (c->ns_off) return;
@@ -97,11 +119,15 @@ __global__ void ns_control_kernel(BatchCtl* c, const double* red, double rn, dou
     return;
   }
   c->ns_prev = res;
+  const double alpha = ns_alpha_dev(c->ns_iters, c->ns_l);
+  c->ns_l = ns_g_dev(alpha * c->ns_l);
+  c->ns_coef[0] = -0.5 * alpha * sqrt(alpha);
+  c->ns_coef[1] = 0.0;
+  c->ns_coef[2] = 1.5 * sqrt(alpha);
   c->ns_iters += 1;
 }
 
-// After delta = Z_r^T S Z_r - I and ||delta||_F^2 in *red, at evaluation r (the single engine's
-// rules: stop at the last evaluation, at delta = 0, or after a step taken from ||delta|| <= 1e-3).
+// After delta = Z_r^T S Z_r - I and ||delta||_F^2 in *red, at evaluation r.
 __global__ void rf_control_kernel(BatchCtl* c, const double* red, int r, int nref) {
   if (c->rf_off) return;
   const double derr = sqrt(*red);
@@ -112,7 +138,10 @@ __global__ void rf_control_kernel(BatchCtl* c, const double* red, int r, int nre
     c->rf_final = r;
     return;
   }
-  if (r == nref || derr == 0.0 || c->rf_prev <= 1e-3) {
+  // (the single engine's rules: the last evaluation, delta = 0, or the rounding floor reached,
+  // i.e. the third-order prediction (5/8) prev^3 at or below what was measured)
+  if (r == nref || derr == 0.0 ||
+      (isfinite(c->rf_prev) && 0.625 * c->rf_prev * c->rf_prev * c->rf_prev <= derr)) {
     c->rf_off = 1;
     c->rf_final = r;
     return;
@@ -346,9 +375,15 @@ struct BatchExec {
       count_launch();
       double* bounds = q->small + SM_BOUNDS_S;
       if ((e = gershgorin(q->f[F_S], q->ld, n, q->partials, bounds, st)) != cudaSuccess) return e;
-      if ((e = power_bound(q->f[F_S], q->ld, n, 12, 1.25, q->f[F_T], q->partials, bounds,
-                           q->small + SM_RED + 7, st)) != cudaSuccess)
+      const int lzs = std::min(kLanczosS, n);
+      if ((e = lanczos(q->f[F_S], q->ld, n, lzs, q->lanczos_ws, q->partials, q->small + SM_LANCZOS,
+                       st)) != cudaSuccess)
         return e;
+      if ((e = lanczos_bounds(q->small, lzs, SM_BOUNDS_S, SM_LANCZOS, SM_EST_S, st)) !=
+          cudaSuccess)
+        return e;
+      ns_init_kernel<<<1, 1, 0, st>>>(q->small, ctl(p));
+      count_launch();
       if ((e = scale_coefficients(bounds, 0, q->small + SM_COEF_A, st)) != cudaSuccess) return e;
       if ((e = scale_coefficients(bounds, 1, q->small + SM_COEF_B, st)) != cudaSuccess) return e;
       if ((e = fas(p, st, q->f[F_S], nullptr, q->small + SM_COEF_A, 0, 0, 0, q->f[F_X],
@@ -383,15 +418,16 @@ struct BatchExec {
                                    &ctl(p)->ns_off, true);
       if (e != cudaSuccess) return e;
       if ((e = reduce_partials(q->partials, nb, 1, q->small + SM_RED, st)) != cudaSuccess) return e;
-      const double handoff = (q->n_refine >= 2) ? 0.05 : 0.0;
+      const double handoff = (q->n_refine >= 1) ? 0.005 : 0.0;  // as the single engine
       ns_control_kernel<<<1, 1, 0, st>>>(ctl(p), q->small + SM_RED, std::sqrt(double(n)), handoff,
                                          par, q->max_ns);
       count_launch();
       const int* skip = &ctl(p)->ns_off;
-      if ((e = fas(p, st, q->f[F_T], nullptr, nullptr, -0.5, 0.0, 1.5, q->f[F_T], &q->sl[SL_A],
+      const double* coef = &ctl(p)->ns_coef[0];
+      if ((e = fas(p, st, q->f[F_T], nullptr, coef, 0, 0, 0, q->f[F_T], &q->sl[SL_A],
                    GDM_PHASE_NEWTON_SCHULZ, skip)) != cudaSuccess)
         return e;
-      return fas(p, st, q->f[F_U], nullptr, nullptr, -0.5, 0.0, 1.5, q->f[F_U], &q->sl[SL_B],
+      return fas(p, st, q->f[F_U], nullptr, coef, 0, 0, 0, q->f[F_U], &q->sl[SL_B],
                  GDM_PHASE_NEWTON_SCHULZ, skip);
     });
     grouped(GDM_PHASE_NEWTON_SCHULZ, [&](int p, SlicedGemmArgs& a, const SliceBuf*& A,
@@ -602,7 +638,7 @@ struct BatchExec {
       const int lz = std::min(kLanczosSteps, n);
       cudaError_t e = gershgorin(q->f[F_U], q->ld, n, q->partials, q->small + SM_GERSH_H, st);
       if (e != cudaSuccess) return e;
-      if ((e = lanczos(q->f[F_U], q->ld, n, lz, q->f[F_X], q->partials, q->small + SM_LANCZOS,
+      if ((e = lanczos(q->f[F_U], q->ld, n, lz, q->lanczos_ws, q->partials, q->small + SM_LANCZOS,
                        st)) != cudaSuccess)
         return e;
       if ((e = lanczos_bounds(q->small, lz, SM_GERSH_H, SM_LANCZOS, SM_EST_H, st)) !=

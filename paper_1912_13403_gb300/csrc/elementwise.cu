@@ -1080,7 +1080,7 @@ __global__ void __launch_bounds__(THREADS)
   }
 }
 
-// y = A x for the power iteration, one row per block with all of the row's loads in flight;
+// y = A x for the Lanczos recurrence, one row per block with all of the row's loads in flight;
 // x as double-float (xh + xl), sums in double-float; partials[row] = y_row^2.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS)
@@ -1524,20 +1524,8 @@ __global__ void x0_coef_kernel(const double* bounds, double* coef) {
   coef[2] = hi / w;
 }
 
-// ---- power iteration for lambda_max of a symmetric positive matrix --------------------------
-// x is kept as a double-float pair (xh, xl) so that y = A x needs no FP64 instruction.
-
-// Start vector: a fixed pseudo-random positive vector (integer hash), as a double-float pair.
-__global__ void power_init_kernel(int n, float* xh, float* xl) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    unsigned h = static_cast<unsigned>(i) * 2654435761u + 0x9E3779B9u;
-    h ^= h >> 16;
-    h *= 0x85EBCA6Bu;
-    h ^= h >> 13;
-    xh[i] = 0.5f + __uint_as_float(0x3F800000u | (h >> 9)) - 1.0f;  // in [0.5, 1.5)
-    xl[i] = 0.0f;
-  }
-}
+// ---- matrix-vector products in double-float (the Lanczos recurrence's y = A v) --------------
+// v is kept as a double-float pair (xh, xl) so that y = A v needs no FP64 instruction.
 
 // y_i = sum_j A_ij x_j (double-float), one warp per row; per-block partial sums of y_i^2.
 __global__ void __launch_bounds__(kRowsPerBlock * 32)
@@ -1569,39 +1557,6 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32)
   }
 }
 
-// ||y|| from the partials (fixed order), x = y / ||y|| as a double-float pair; *est = ||y||.
-// With `init`, y is the start vector (xh, xl) itself.
-__global__ void power_scale_kernel(const double* y, int n, const double* partials, int nb,
-                                   float* xh, float* xl, double* est, int init) {
-  __shared__ double red[32];
-  __shared__ double norm_sh;
-  double acc = 0.0;
-  if (init) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += static_cast<double>(xh[i]) * xh[i];
-  } else {
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partials[i];
-  }
-  acc = block_sum(acc, red);
-  if (threadIdx.x == 0) {
-    norm_sh = sqrt(acc);
-    if (!init) *est = norm_sh;
-  }
-  __syncthreads();
-  const double inv = (norm_sh > 0.0) ? 1.0 / norm_sh : 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double v = (init ? static_cast<double>(xh[i]) : y[i]) * inv;
-    const float hi = static_cast<float>(v);
-    xh[i] = hi;
-    xl[i] = static_cast<float>(v - static_cast<double>(hi));
-  }
-}
-
-// bounds[1] <- min(bounds[1], factor * est): a tighter scale for the Newton-Schulz start.
-__global__ void tighten_bound_kernel(double* bounds, const double* est, double factor) {
-  const double c = factor * (*est);
-  if (isfinite(c) && c > 0.0 && c < bounds[1]) bounds[1] = c;
-}
-
 // ---- Lanczos estimates of the extreme eigenvalues of a symmetric matrix ---------------------
 // Three-term recurrence without reorthogonalisation (its extreme Ritz values converge first and
 // are not disturbed by the loss of orthogonality, which only adds copies of converged values):
@@ -1609,7 +1564,7 @@ __global__ void tighten_bound_kernel(double* bounds, const double* est, double f
 //   v_{k+1} = w / beta_k.
 // v lives in FP64 (v, vprev) and as a double-float pair (xh, xl) for the matrix-vector product.
 
-// Start vector: the power iteration's fixed pseudo-random vector, normalised; vprev = 0.
+// Start vector: a fixed pseudo-random vector (integer hash) in [-0.5, 0.5), normalised; vprev = 0.
 __global__ void lanczos_init_kernel(int n, float* xh, float* xl, double* v, double* vprev) {
   __shared__ double red[32];
   __shared__ double inv_sh;
@@ -1719,6 +1674,7 @@ __global__ void lanczos_bounds_kernel(double* small, int steps, int gersh_at, in
     ghi = fmax(ghi, a[i] + r);
   }
   double lo = g_lo, hi = g_hi;
+  double t_raw[2] = {g_lo, g_hi};
   if (finite) {
     double t[2];
     for (int end = 0; end < 2; ++end) {
@@ -1738,6 +1694,8 @@ __global__ void lanczos_bounds_kernel(double* small, int steps, int gersh_at, in
       }
       t[end] = u;
     }
+    t_raw[0] = t[0];
+    t_raw[1] = t[1];
     const double margin = 0.02 * (t[1] - t[0]) + 1e-12 * fmax(fabs(t[0]), fabs(t[1]));
     const double c_lo = fmax(g_lo, t[0] - margin), c_hi = fmin(g_hi, t[1] + margin);
     if (isfinite(c_lo) && isfinite(c_hi) && c_hi > c_lo) {
@@ -1749,6 +1707,8 @@ __global__ void lanczos_bounds_kernel(double* small, int steps, int gersh_at, in
     small[bounds_at] = lo;
     small[bounds_at + 1] = hi;
     small[bounds_at + 2] = (lo == g_lo && hi == g_hi) ? 0.0 : 1.0;  // 1: the estimate was used
+    small[bounds_at + 3] = finite ? t_raw[0] : g_lo;                 // the extreme Ritz values
+    small[bounds_at + 4] = finite ? t_raw[1] : g_hi;
   }
 }
 
@@ -2003,40 +1963,6 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
                                                         ha, hb, hc, Y, ldy, od, osc, old, plane,
                                                         nslice, skip, step);
   }
-  return cudaGetLastError();
-}
-
-cudaError_t power_bound(const double* A, int64_t lda, int n, int iters, double factor,
-                        double* work, double* partials, double* bounds_dev, double* est_dev,
-                        cudaStream_t stream) {
-  if (n <= 0) return cudaSuccess;
-  float* xh = reinterpret_cast<float*>(work);
-  float* xl = xh + n;
-  double* y = work + n;  // n doubles after the two float vectors (n doubles of room)
-  // one block per row (partials: one value per row) when the row fits in registers and the
-  // float vectors are 8-byte aligned (n even), else one warp per row
-  const bool rows_fit = n % 2 == 0 && n <= kFusedMaxCols && lda % 2 == 0 &&
-                        (reinterpret_cast<uintptr_t>(A) & 15) == 0;
-  const int nb = rows_fit ? n : (n + kRowsPerBlock - 1) / kRowsPerBlock;
-  count_launch();
-  power_init_kernel<<<(n + 255) / 256, 256, 0, stream>>>(n, xh, xl);
-  count_launch();
-  power_scale_kernel<<<1, 1024, 0, stream>>>(y, n, partials, 0, xh, xl, est_dev, 1);
-  for (int k = 0; k < iters; ++k) {
-    count_launch();
-    if (!rows_fit)
-      matvec_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, n, xh, xl, y, partials);
-    else if (n / 2 <= 128 * kFusedPPT)
-      matvec_rows_kernel<128><<<n, 128, 0, stream>>>(A, lda, n, xh, xl, y, partials);
-    else if (n / 2 <= 256 * kFusedPPT)
-      matvec_rows_kernel<256><<<n, 256, 0, stream>>>(A, lda, n, xh, xl, y, partials);
-    else
-      matvec_rows_kernel<512><<<n, 512, 0, stream>>>(A, lda, n, xh, xl, y, partials);
-    count_launch();
-    power_scale_kernel<<<1, 1024, 0, stream>>>(y, n, partials, nb, xh, xl, est_dev, 0);
-  }
-  count_launch();
-  tighten_bound_kernel<<<1, 1, 0, stream>>>(bounds_dev, est_dev, factor);
   return cudaGetLastError();
 }
 

@@ -280,6 +280,24 @@ gdm_status check_device_error(gdm_handle* h) {
 // ------------------------------------------------------------------------------------------
 // step 1: Z with Z^T S Z = I
 // ------------------------------------------------------------------------------------------
+constexpr int kLanczosS = 16;  // Lanczos steps on S for its spectral estimates
+constexpr double kNsHandoff = 0.005;  // ||I - M||_F at which Newton-Schulz hands over
+
+// Whether a refinement step taken from ||delta||_F = before, which measured `after`, reached
+// the rounding floor (the third-order prediction (5/8) before^3 is at or below what is left).
+bool refine_at_floor(double before, double after) {
+  return std::isfinite(before) && 0.625 * before * before * before <= after;
+}
+
+// The Newton-Schulz eigenvalue map g(x) = x (3 - x)^2 / 4 and the scale of step `it` for a
+// smallest eigenvalue l of M: the first step is plain (it brings every eigenvalue into (0, 1]),
+// later ones take alpha = 3 / (1 + sqrt(l) + l) (capped at 2.9) until l passes 0.3.
+double ns_g(double x) { return x * (3.0 - x) * (3.0 - x) * 0.25; }
+double ns_alpha(int it, double l) {
+  if (it == 0 || !(l > 0.0) || l >= 0.3) return 1.0;
+  const double r = std::sqrt(l);
+  return std::min(2.9, 3.0 / (1.0 + r + l));
+}
 gdm_status compute_z(gdm_handle* h, gdm_info* info) {
   const int n = static_cast<int>(h->n);
   const int64_t ld = h->ld;
@@ -291,36 +309,48 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
   double* coef_inv = h->small + SM_COEF_A;
   double* coef_isqrt = h->small + SM_COEF_B;
 
+  // Gershgorin's interval of S and the extreme Ritz values of a short Lanczos recurrence
+  // (estimates of lambda_max and lambda_min of S from inside the spectrum)
   CK(gershgorin(S, ld, n, h->partials, bounds, s));
-  double bnd[2];
-  gdm_status st = read_small(h, SM_BOUNDS_S, 2, bnd);
+  const int lzs = std::min(kLanczosS, n);
+  CK(lanczos(S, ld, n, lzs, h->lanczos_ws, h->partials, h->small + SM_LANCZOS, s));
+  CK(lanczos_bounds(h->small, lzs, SM_BOUNDS_S, SM_LANCZOS, SM_EST_S, s));
+  double smv[SM_EST_S + 5];
+  gdm_status st = read_small(h, 0, SM_EST_S + 5, smv);
   if (st != GDM_OK) return st;
+  const double bnd[2] = {smv[SM_BOUNDS_S], smv[SM_BOUNDS_S + 1]};
   if (!std::isfinite(bnd[0]) || !std::isfinite(bnd[1]))
     return set_err(h, GDM_ERR_NONFINITE, "overlap matrix has non-finite entries");
   if (bnd[1] <= 0.0) return set_err(h, GDM_ERR_NOT_SPD, "overlap Gershgorin bound <= 0");
+  const double ritz_min = smv[SM_EST_S + 3], ritz_max = smv[SM_EST_S + 4];
 
   double *Y = h->f[F_X], *Z = h->f[F_XN], *M = h->f[F_T], *Mt = h->f[F_U];
   double *Yn = h->f[F_X2], *Zn = h->f[F_V];
   SliceBuf *sY = &h->sl[SL_X], *sZ = &h->sl[SL_Z], *sM = &h->sl[SL_A], *sMt = &h->sl[SL_B];
   const double rn = std::sqrt(static_cast<double>(n));
-  const double ns_handoff = (mixed(h) && h->n_refine >= 2) ? 0.05 : 0.0;
+  const double ns_handoff = (mixed(h) && h->n_refine >= 1) ? kNsHandoff : 0.0;
   double prev = INFINITY, res = INFINITY;
   int it = 0;
   bool converged = false;
   // The iteration converges for every scale c with lambda_max(S)/c < 3, and the number of
   // steps grows with c/lambda_min(S).  Gershgorin's bound can exceed lambda_max many times over
-  // for a dense S, so the first attempt uses 1.25 x a power-iteration estimate of lambda_max
-  // (never above Gershgorin); if that attempt diverges, the second uses Gershgorin's guaranteed
-  // bound.
+  // for a dense S, so the first attempt uses 1.05 x the largest Ritz value (never above
+  // Gershgorin); if that attempt diverges, the second uses Gershgorin's guaranteed bound.
+  // Scaled steps.  Each eigenvalue m of M = Y Z (in (0, 1] after one plain step) maps to
+  // g(alpha m), g(x) = x (3 - x)^2 / 4, when T = sqrt(alpha) (3I - alpha M)/2 (alpha = 1 is the
+  // plain step).  With the smallest eigenvalue at l, alpha = 3 / (1 + r + r^2), r = sqrt(l),
+  // solves g(alpha l) = g(alpha), so the whole interval [l, 1] lands in [g(alpha l), 1]: the
+  // lower end grows ~6.5-fold per step instead of 2.25-fold (cond(S) = 1e3: 11 -> 8 steps).
+  // l comes from the smallest Ritz value, which lies above lambda_min, so alpha errs on the
+  // small side; every alpha in [1, 3) keeps all eigenvalues in (0, 1], so the iteration
+  // converges whatever l is.
   for (int attempt = 0; attempt < 2; ++attempt) {
-    if (attempt == 0) {
-      CK(power_bound(S, ld, n, 12, 1.25, h->f[F_T], h->partials, bounds, h->small + SM_RED + 7,
-                     s));
-    } else {
-      h->host_buf[0] = bnd[0];
-      h->host_buf[1] = bnd[1];
-      CK(cudaMemcpyAsync(bounds, h->host_buf, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
-    }
+    const double c = (attempt == 0 && ritz_max > 0.0 && std::isfinite(ritz_max))
+                         ? std::min(bnd[1], 1.05 * ritz_max) : bnd[1];
+    double lsc = (ritz_min > 0.0 && std::isfinite(ritz_min)) ? std::min(1.0, ritz_min / c) : 1.0;
+    h->host_buf[0] = bnd[0];
+    h->host_buf[1] = c;
+    CK(cudaMemcpyAsync(bounds, h->host_buf, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(scale_coefficients(bounds, 0, coef_inv, s));
     CK(scale_coefficients(bounds, 1, coef_isqrt, s));
     CK(form_and_slice(S, ld, nullptr, 0, n, n, coef_inv, 0, 0, 0, Y, ld, ns_sl > 0 ? sY : nullptr,
@@ -350,20 +380,25 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
                        "Newton-Schulz for S^-1/2 diverged (residual %g): S not positive definite",
                        res);
       }
-      // With two or more refinement steps to follow, stop once ||I - M||_F <= 0.05: the
-      // refinement's third-order steps take 0.05 to about (5/8) 0.05^3 = 7.8e-5 and then below the
-      // rounding floor, which is what the last two Newton-Schulz steps would have done.
+      // Hand over to the refinement once ||I - M||_F <= 0.005: one third-order refinement step
+      // then takes Z^T S Z - I to about (5/8) 0.005^3 = 7.8e-8, at the products' rounding floor.
+      // A refinement step (four 4-slice products) costs about five Newton-Schulz steps (three
+      // 2-slice products), so the last quadratic Newton-Schulz step from ~0.05 is the cheaper way
+      // down to 0.005 than a second refinement step.
       if (res <= ns_handoff || res <= 1e-13 * rn || (res < 1e-2 * rn && res > 0.5 * prev)) {
         converged = true;
         break;
       }
       prev = res;
-      // T = (3I - M)/2 and T^T, formed in place while slicing, so that Y <- T Y and Z <- T^T Z
-      // are plain products (no addend in the epilogue)
-      CK(form_and_slice(M, ld, nullptr, 0, n, n, nullptr, -0.5, 0.0, 1.5, M, ld,
+      // T = sqrt(alpha) (3I - alpha M)/2 and T^T, formed in place while slicing, so that
+      // Y <- T Y and Z <- T^T Z are plain products (no addend in the epilogue)
+      const double alpha = ns_alpha(it, lsc);
+      lsc = ns_g(alpha * lsc);
+      const double ta = -0.5 * alpha * std::sqrt(alpha), tc = 1.5 * std::sqrt(alpha);
+      CK(form_and_slice(M, ld, nullptr, 0, n, n, nullptr, ta, 0.0, tc, M, ld,
                         ns_sl > 0 ? sM : nullptr, ns_sl, nullptr, s,
                         bits_for(h, GDM_PHASE_NEWTON_SCHULZ), kDotNone, nullptr, true));
-      CK(form_and_slice(Mt, ld, nullptr, 0, n, n, nullptr, -0.5, 0.0, 1.5, Mt, ld,
+      CK(form_and_slice(Mt, ld, nullptr, 0, n, n, nullptr, ta, 0.0, tc, Mt, ld,
                         ns_sl > 0 ? sMt : nullptr, ns_sl, nullptr, s,
                         bits_for(h, GDM_PHASE_NEWTON_SCHULZ), kDotNone, nullptr, true));
       CK(product(h, {M, sM}, {Y, sY}, Yn, nullptr, nullptr, 1.0, 0.0, 0.0, true,
@@ -412,10 +447,10 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
     if (r == nref || derr == 0.0) break;
     // The step is third order: with F = I - delta/2 + 3 delta^2/8 (delta symmetric, so F
     // commutes with it), delta' = (I + delta) F^2 - I = (5/8) delta^3 - (15/64) delta^4 +
-    // (9/64) delta^5.  After a step taken from ||delta||_F <= 1e-3 the remainder (<= 6.3e-10)
-    // lies below the rounding floor that the sliced products leave in Z^T S Z, so this delta is
-    // that floor and another step cannot lower it.
-    if (derr_prev <= 1e-3) break;
+    // (9/64) delta^5, so ||delta'||_F <= (5/8) ||delta||_F^3 to leading order.  When the
+    // delta measured after a step is at or above that prediction, it is the rounding floor that
+    // the sliced products leave in Z^T S Z, and another step cannot lower it.
+    if (refine_at_floor(derr_prev, derr)) break;
     derr_prev = derr;
     CK(slice(h, Dl, &h->sl[SL_B], GDM_PHASE_REFINE, kDotSelf));
     CK(product(h, {Dl, &h->sl[SL_B]}, {Dl, &h->sl[SL_B]}, F, nullptr, Dl, 0.375, -0.5, 1.0, true,
@@ -540,7 +575,7 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   const int lz = (h->bounds_method == GDM_BOUNDS_LANCZOS)
                      ? static_cast<int>(std::min<int64_t>(h->lanczos_steps, n)) : 0;
   if (lz > 0) {
-    CK(lanczos(Ht, ld, n, lz, h->f[F_X], h->partials, h->small + SM_LANCZOS, s));
+    CK(lanczos(Ht, ld, n, lz, h->lanczos_ws, h->partials, h->small + SM_LANCZOS, s));
     CK(lanczos_bounds(h->small, lz, SM_GERSH_H, SM_LANCZOS, SM_EST_H, s));
   }
   double sm[SM_EST_H + 3];
@@ -812,7 +847,7 @@ namespace {
 
 // Byte layout of a handle's single device allocation for capacity n.
 struct PoolLayout {
-  size_t fbytes, sdata, sscale, pbytes, small_bytes, st_bytes, flag_bytes, split_slots,
+  size_t fbytes, sdata, sscale, pbytes, lbytes, small_bytes, st_bytes, flag_bytes, split_slots,
       split_bytes, total;
   explicit PoolLayout(int64_t n) {
     auto up = [](size_t x) { return (x + 1023) / 1024 * 1024; };
@@ -824,6 +859,9 @@ struct PoolLayout {
     // row scales, row dot products, then the 128 x 128 tile occupancy words
     sscale = up(2 * sizeof(double) * rows_alloc + sizeof(uint32_t) * tiles * tiles);
     pbytes = up(sizeof(double) * (kTraceTerms * static_cast<size_t>(n) + 64));
+    // the Lanczos recurrence's vectors (x as two float halves, y, v, v_prev); kept out of the
+    // n x n buffers, whose column n must stay zero
+    lbytes = up(sizeof(double) * 4 * static_cast<size_t>(n));
     small_bytes = up(sizeof(double) * kSmall);
     st_bytes = up(sizeof(Trs4State));
     // the device error word, then the split-k counters
@@ -831,8 +869,8 @@ struct PoolLayout {
     // split-k partial sums: a part per SM at most, and never more than 4 per tile
     split_slots = std::min<size_t>(kSplitTiles, 4 * tiles * tiles);
     split_bytes = up(sizeof(long long) * 128 * 128 * split_slots);
-    total = F_COUNT * fbytes + SL_COUNT * (sdata + sscale) + pbytes + small_bytes + st_bytes +
-            flag_bytes + split_bytes;
+    total = F_COUNT * fbytes + SL_COUNT * (sdata + sscale) + pbytes + lbytes + small_bytes +
+            st_bytes + flag_bytes + split_bytes;
   }
 };
 
@@ -944,6 +982,8 @@ gdm_status gdm_init(gdm_handle** out, int64_t n_basis, int64_t n_occ, int device
   }
   h->partials = reinterpret_cast<double*>(p);
   p += L.pbytes;
+  h->lanczos_ws = reinterpret_cast<double*>(p);
+  p += L.lbytes;
   h->small = reinterpret_cast<double*>(p);
   p += L.small_bytes;
   h->st_dev = reinterpret_cast<Trs4State*>(p);

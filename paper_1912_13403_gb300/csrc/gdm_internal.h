@@ -195,14 +195,6 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
 // A[i, col] = 0 for i < rows (the zero column after an odd n).
 cudaError_t zero_column(double* A, int64_t lda, int rows, int col, cudaStream_t stream);
 
-// Power iteration for lambda_max of a symmetric positive matrix (iters matrix-vector products
-// in double-float from a fixed start vector), then bounds_dev[1] <- min(bounds_dev[1],
-// factor * estimate); the estimate is also written to *est_dev.  `work` holds >= 2 n doubles,
-// `partials` >= n.
-cudaError_t power_bound(const double* A, int64_t lda, int n, int iters, double factor,
-                        double* work, double* partials, double* bounds_dev, double* est_dev,
-                        cudaStream_t stream);
-
 // `steps` Lanczos steps on the symmetric n x n matrix A from a fixed start vector (no
 // reorthogonalisation): ab_dev[k] = alpha_k and ab_dev[steps + k] = beta_k for k < steps, the
 // diagonal and off-diagonal of the tridiagonal whose extreme eigenvalues estimate A's from inside.
@@ -214,7 +206,8 @@ cudaError_t lanczos(const double* A, int64_t lda, int n, int steps, double* work
 // beta_0..beta_{steps-1}) and Gershgorin's interval (small[gersh_at..+1]): the extreme Ritz values
 // by bisection on Sturm counts, widened by 2% of their span and clamped to Gershgorin's
 // interval, into small[bounds_at..+1]; small[bounds_at + 2] = 1 when the estimate is used, 0
-// when Gershgorin's interval is (a non-finite or degenerate recurrence).  One device thread.
+// when Gershgorin's interval is (a non-finite or degenerate recurrence); small[bounds_at + 3..4]
+// the extreme Ritz values themselves (Gershgorin's bounds when there are none).  One warp.
 cudaError_t lanczos_bounds(double* small, int steps, int gersh_at, int lanczos_at, int bounds_at,
                            cudaStream_t stream);
 

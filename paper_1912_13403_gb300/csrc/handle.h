@@ -23,7 +23,8 @@ enum SmallSlot {
   SM_RED = 16,       // 8 reduction outputs
   SM_KCOUNT = 24,    // 1: k stages issued by masked products (as an unsigned 64-bit count)
   SM_GERSH_H = 26,   // 2: Gershgorin bounds of H~
-  SM_EST_H = 28,     // 3: estimated bounds of H~ and whether the estimate was used
+  SM_EST_H = 160,    // 5: estimated bounds of H~, whether used, the raw extreme Ritz values
+  SM_EST_S = 168,    // 5: the same for S
   SM_LANCZOS = 32,   // 2 x kMaxLanczos: alpha_k, then beta_k, of the Lanczos recurrence on H~
 };
 constexpr int kMaxLanczos = 64;
@@ -67,6 +68,7 @@ struct gdm_handle {
   double* f[gdm::F_COUNT] = {};
   gdm::SliceBuf sl[gdm::SL_COUNT];
   double* partials = nullptr;  // >= 5 * ceil(n/8) doubles
+  double* lanczos_ws = nullptr;  // 4 * n_cap doubles: the Lanczos recurrence's vectors
   double* small = nullptr;     // kSmall doubles: coefficients, bounds, reductions
   gdm::Trs4State* st_dev = nullptr;
   uint32_t* err_dev = nullptr;

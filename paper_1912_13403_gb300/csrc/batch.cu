@@ -324,11 +324,11 @@ struct BatchExec {
   // and epilogue as `make(p, args)` describes them, for each variant's k tile); in the capture
   // pass, the launch of the chosen variant's table.
   template <class F>
-  void grouped(int ph, F&& make) {
+  void grouped(int ph, F&& make, const Precision* fmt = nullptr) {
     const int idx = site_cursor++;
     if (planning) {
       Site s;
-      s.prec = h[0]->phase[ph];
+      s.prec = fmt != nullptr ? *fmt : h[0]->phase[ph];
       for (int v = 0; v < grouped_variant_count(s.prec.nslice); ++v) {
         const int bk = grouped_variant_bk(s.prec.nslice, v);
         s.host[v].resize(count());
@@ -466,6 +466,7 @@ struct BatchExec {
   // Evaluation r of the refinement on Z_r (FP64 zf / zt, slices zs / zts), then (r < kNref)
   // the update Z_{r+1} = Z_r F into (nz, nzt).
   void refine_step(int r, int zf, int ztf, int nzf, int nztf) {
+    (void)zf;  // Z_r enters through its slices and, transposed, through ztf
     // T = Z^T S (exact diagonal), delta = T Z - I (exact diagonal)
     const int zs = (r == 0) ? SL_Z : SL_ZT;  // Z^T's slices (Z_0 is symmetric)
     grouped(GDM_PHASE_REFINE, [&](int p, SlicedGemmArgs& a, const SliceBuf*& A,
@@ -516,6 +517,12 @@ struct BatchExec {
                  GDM_PHASE_REFINE, &ctl(p)->rf_off, kDotSelf);
     });
     if (r == kNref) return;
+    // the update as Z + Z G, G = -delta/2 + 3 delta^2/8, with the single engine's short
+    // formats for the two products with a small factor (engine.cu, compute_z)
+    const Precision& rp = h[0]->phase[GDM_PHASE_REFINE];
+    const int sq_ns = std::min(rp.nslice, 2), zg_ns = std::min(rp.nslice, 3);
+    const Precision sq_fmt{sq_ns, std::min(1, 2 * (sq_ns - 1)), rp.bits};
+    const Precision zg_fmt{zg_ns, std::min(2, 2 * (zg_ns - 1)), rp.bits};
     grouped(GDM_PHASE_REFINE, [&](int p, SlicedGemmArgs& a, const SliceBuf*& A,
                                   const SliceBuf*& B) {
       gdm_handle* q = h[p];
@@ -528,43 +535,39 @@ struct BatchExec {
       a.ldd = q->ld;
       a.alpha = 0.375;
       a.beta = -0.5;
-      a.diag = 1.0;
+      a.diag = 0.0;
       a.diag_dot = rowdots(p) ? q->sl[SL_B].row_dot : nullptr;
       a.skip = &ctl(p)->rf_off;
-    });
+    }, &sq_fmt);
     per_problem([&](int p, cudaStream_t st) -> cudaError_t {
       gdm_handle* q = h[p];
       const int n = static_cast<int>(q->n);
       if (!rowdots(p)) {
         cudaError_t e = diag_fix(q->f[F_U], q->ld, q->f[F_U], q->ld, q->f[F_V], q->ld, n, n, 0.375,
-                                 -0.5, q->f[F_U], q->ld, 1.0, nullptr, st, &ctl(p)->rf_off);
+                                 -0.5, q->f[F_U], q->ld, 0.0, nullptr, st, &ctl(p)->rf_off);
         if (e != cudaSuccess) return e;
       }
       return fas(p, st, q->f[F_V], nullptr, nullptr, 1.0, 0, 0, nullptr, &q->sl[SL_A],
                  GDM_PHASE_REFINE, &ctl(p)->rf_off);
     });
-    const int za = (r == 0) ? SL_Z : SL_Z;  // Z's own slices
     grouped(GDM_PHASE_REFINE, [&](int p, SlicedGemmArgs& a, const SliceBuf*& A,
                                   const SliceBuf*& B) {
       gdm_handle* q = h[p];
-      A = &q->sl[za];
+      A = &q->sl[SL_Z];
       B = &q->sl[SL_A];
       a.C = q->f[nzf];
       a.ldc = q->ld;
       a.Ct = q->f[nztf];
       a.ldct = q->ld;
+      a.D = q->f[ztf];  // read transposed: Z itself
+      a.ldd = q->ld;
+      a.beta = 1.0;
       a.skip = &ctl(p)->rf_off;
-    });
+    }, &zg_fmt);
     per_problem([&](int p, cudaStream_t st) -> cudaError_t {
       gdm_handle* q = h[p];
-      const int n = static_cast<int>(q->n);
       const int* skip = &ctl(p)->rf_off;
-      cudaError_t e = diag_fix(q->f[zf], q->ld, q->f[F_V], q->ld, q->f[nzf], q->ld, n, n, 1.0,
-                               0.0, nullptr, 0, 0.0, nullptr, st, skip);
-      if (e != cudaSuccess) return e;
-      if ((e = diag_fix(q->f[zf], q->ld, q->f[F_V], q->ld, q->f[nztf], q->ld, n, n, 1.0, 0.0,
-                        nullptr, 0, 0.0, nullptr, st, skip)) != cudaSuccess)
-        return e;
+      cudaError_t e;
       if ((e = fas(p, st, q->f[nzf], nullptr, nullptr, 1.0, 0, 0, nullptr, &q->sl[SL_Z],
                    GDM_PHASE_REFINE, skip)) != cudaSuccess)
         return e;

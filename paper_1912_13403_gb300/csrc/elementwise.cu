@@ -143,6 +143,33 @@ __device__ __forceinline__ void split_words(unsigned whi, unsigned wlo, float& h
   lo = __uint_as_float((normal && rem != 0u && el > 0) ? lbits : 0u);
 }
 
+// x truncated to FP32 from the two words of the double (integer operations only): the top 24
+// significant bits; 0 below FP32's normal range, +-Inf above it and for Inf, NaN kept.
+__device__ __forceinline__ float trunc_words(unsigned whi, unsigned wlo) {
+  const int E = static_cast<int>((whi >> 20) & 0x7FF);
+  const unsigned sign = whi & 0x80000000u;
+  const int ef = E - 1023 + 127;
+  const unsigned bits = sign | (static_cast<unsigned>(ef) << 23) | ((whi & 0xFFFFFu) << 3) |
+                        (wlo >> 29);
+  const unsigned nan_bit = (E == 0x7FF && ((whi & 0xFFFFFu) | wlo) != 0u) ? 1u : 0u;
+  const unsigned special = (E == 0x7FF || ef >= 255) ? (sign | 0x7F800000u | nan_bit) : sign;
+  return __uint_as_float((E != 0 && E != 0x7FF && ef > 0 && ef < 255) ? bits : special);
+}
+
+// Sum of v over the block (FP32, a fixed order); every thread gets the result.  scratch >= 32.
+__device__ __forceinline__ float block_sum_f(float v, float* scratch) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  float t = 0.0f;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int j = 0; j < nw; ++j) t += scratch[j];
+  return t;
+}
+
 // +-2^k x on the two words of x: only the high word changes (exponent and sign); zero and
 // subnormal x give 0, results below the normal range 0 (signed), above it Inf, Inf/NaN stay.
 __device__ __forceinline__ void pow2_words(unsigned& whi, unsigned& wlo, int k, bool neg) {
@@ -429,7 +456,59 @@ __device__ __forceinline__ bool pow2_coef(double a, int& k, bool& neg) {
 // v - 1, out of line for the same reason (the identity's diagonal in a residual)
 __device__ __noinline__ double minus_one(double v) { return v - 1.0; }
 
-enum { kFormPlain = 0, kFormPow2 = 1, kFormGeneral = 2 };
+enum { kFormPlain = 0, kFormPow2 = 1, kFormGeneral = 2, kFormSplit = 3 };
+
+// kFormSplit: y = a x + b x2 (+ c on the diagonal) in FP32 double-float arithmetic straight to
+// y's split (hi, lo) - for passes whose only outputs are slices, norms and row dots (no FP64
+// result written, no filtering), which are cut from that split anyway.  Each product is
+// Dekker's (the exact hi*hi term by an FMA, the cross terms in FP32), the sum a two-sum
+// renormalised by a fast two-sum: y to ~2^-46 of |a x| + |b x2|, far below the slices' last
+// digit, and no FP64 instruction (GB300 issues FP64 at ~1/64 of the FP32 rate).
+struct DFCoef {
+  float ah, al, bh, bl, ch, cl;
+};
+__device__ __forceinline__ DFCoef df_coef(double a, double b, double c) {
+  DFCoef k;
+  k.ah = __double2float_rn(a);
+  k.al = __double2float_rn(a - static_cast<double>(k.ah));
+  k.bh = __double2float_rn(b);
+  k.bl = __double2float_rn(b - static_cast<double>(k.bh));
+  k.ch = __double2float_rn(c);
+  k.cl = __double2float_rn(c - static_cast<double>(k.ch));
+  return k;
+}
+// (hi, lo) = two_sum(a, b) for any a, b
+__device__ __forceinline__ void two_sum_f(float a, float b, float& hi, float& lo) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  lo = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  hi = s;
+}
+// a x + b x2 (+ c) as a normalised pair from the splits of x and x2
+__device__ __forceinline__ void df_axpby(const DFCoef& k, float xh, float xl, float x2h,
+                                         float x2l, bool with_x2, bool add_c, float& yh,
+                                         float& yl) {
+  float p = __fmul_rn(k.ah, xh);
+  float pe = __fmaf_rn(k.ah, xh, -p);
+  pe = __fmaf_rn(k.ah, xl, __fmaf_rn(k.al, xh, pe));
+  float s = p, e = pe;
+  if (with_x2) {
+    const float q = __fmul_rn(k.bh, x2h);
+    float qe = __fmaf_rn(k.bh, x2h, -q);
+    qe = __fmaf_rn(k.bh, x2l, __fmaf_rn(k.bl, x2h, qe));
+    float t;
+    two_sum_f(p, q, s, t);
+    e = __fadd_rn(__fadd_rn(pe, qe), t);
+  }
+  if (add_c) {
+    float t;
+    const float s0 = s;
+    two_sum_f(s0, k.ch, s, t);
+    e = __fadd_rn(__fadd_rn(e, k.cl), t);
+  }
+  yh = __fadd_rn(s, e);
+  yl = __fsub_rn(e, __fsub_rn(yh, s));
+}
 
 // y_jj + c on the word pair of a diagonal element, out of line (once per row).
 __device__ __noinline__ uint2 add_on_diagonal_words(uint2 w, double c) {
@@ -473,7 +552,37 @@ template <int MODE, int DOT>
 __device__ __forceinline__ bool form_pair(int p, int row, uint4 x, uint4 x2, bool with_x2,
                                           double a, double b, int ak, bool aneg, bool has_c,
                                           double c, const TruncArgs& tr, uint4* yr, uint4& y,
-                                          float& ss, DF& acc) {
+                                          float& ss, DF& acc, uint4* split = nullptr) {
+  if constexpr (MODE == kFormSplit) {
+    // slices-only pass (the host picks this mode only without an FP64 output and filtering)
+    const DFCoef k = df_coef(a, b, c);
+    float xh0, xl0, xh1, xl1, zh0 = 0.f, zl0 = 0.f, zh1 = 0.f, zl1 = 0.f;
+    split_words(x.y, x.x, xh0, xl0);
+    split_words(x.w, x.z, xh1, xl1);
+    if (with_x2) {
+      split_words(x2.y, x2.x, zh0, zl0);
+      split_words(x2.w, x2.z, zh1, zl1);
+    }
+    float h0, l0, h1, l1;
+    df_axpby(k, xh0, xl0, zh0, zl0, with_x2, has_c && 2 * p == row, h0, l0);
+    df_axpby(k, xh1, xl1, zh1, zl1, with_x2, has_c && 2 * p + 1 == row, h1, l1);
+    y = make_uint4(0u, 0u, 0u, 0u);
+    ss = fmaf(h0, h0, fmaf(h1, h1, ss));
+    if (split != nullptr)
+      *split = make_uint4(__float_as_uint(h0), __float_as_uint(l0), __float_as_uint(h1),
+                          __float_as_uint(l1));
+    if (DOT != kDotNone) {
+      float ph0 = h0, pl0 = l0, ph1 = h1, pl1 = l1;
+      if (DOT == kDotX2) {
+        ph0 = zh0; pl0 = zl0; ph1 = zh1; pl1 = zl1;
+      } else if (DOT == kDotX) {
+        ph0 = xh0; pl0 = xl0; ph1 = xh1; pl1 = xl1;
+      }
+      acc = df_fma(acc, h0, l0, ph0, pl0);
+      acc = df_fma(acc, h1, l1, ph1, pl1);
+    }
+    return false;
+  }
   y = x;
   if (MODE == kFormPow2) {
     pow2_words(y.y, y.x, ak, aneg);
@@ -505,6 +614,9 @@ __device__ __forceinline__ bool form_pair(int p, int row, uint4 x, uint4 x2, boo
   split_words(y.y, y.x, h0, l0);
   split_words(y.w, y.z, h1, l1);
   ss = fmaf(h0, h0, fmaf(h1, h1, ss));  // the truncated value bounds |y| from below by 2^-23
+  if (split != nullptr)
+    *split = make_uint4(__float_as_uint(h0), __float_as_uint(l0), __float_as_uint(h1),
+                        __float_as_uint(l1));
   if (DOT != kDotNone) {
     float ph0 = h0, pl0 = l0, ph1 = h1, pl1 = l1;
     if (DOT == kDotX2) {
@@ -710,29 +822,80 @@ __global__ void __launch_bounds__(kSliceThreads)
 constexpr int kFusedPPT = 8;
 static_assert(kFusedMaxCols == 2 * 512 * kFusedPPT, "fused slicing: up to 512 threads per row");
 
-// The slices of a row held in registers (kFusedPPT column pairs a thread): digits of
-// round(y 2^p2) (p2 <= -1000: an all-zero row), written as FP16 pairs, one plane per slice.
+// x rounded to an integer (nearest, ties to even) on the FP32 pipe, |x| < 2^22: the 1.5 * 2^23
+// shift in two additions that the compiler may not contract or reorder.
+__device__ __forceinline__ float rint_f(float x) {
+  return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+}
+
+// Balanced digits of t = y 2^k (|t| < 2^11) from y's FP32 split y = hi + lo (split_words: hi the
+// top 24 bits, lo the next 24, together y to 2^-47), on the FP32 pipe.  What remains of t after
+// each digit is kept exactly as an unevaluated pair (r_hi, r_lo) with |r_lo| <= ulp(r_hi) / 2:
+//   d_0 = rint(t_hi),                 (r_hi, r_lo) = two_sum(t_hi - d_0, t_lo)
+//   d_s = rint(r_hi 2^b),             (r_hi, r_lo) = two_sum(r_hi 2^b - d_s, r_lo 2^b)
+//   d_last = rint(r_hi 2^b + r_lo 2^b).
+// Each digit is subtracted from the value it rounds, so the subtraction is exact, and the
+// two-sum (Dekker's fast form: |first| >= |second| or first = 0 holds here) is exact; the digits
+// therefore represent t to half a unit of the last slice (plus the split's 2^-47 |t|).  Deciding
+// a digit from r_hi alone leaves at most 1/2 + 2^-13 units, so every later digit stays within
+// +-2^(b-1) (2^(b-1) + 1/2 rounds to even) and d_0 within +-2^11: all exact in FP16.
+template <int NS, int BITS>
+__device__ __forceinline__ void slice_digits_f(float hi, float lo, float scale, int nslice_rt,
+                                               int bits_rt, float* d) {
+  const int nslice = NS ? NS : nslice_rt;
+  const float w = NS ? static_cast<float>(1 << BITS) : __int_as_float((127 + bits_rt) << 23);
+  const float th = hi * scale, tl = lo * scale;  // exact: powers of two, in FP32's range
+  d[0] = rint_f(th);
+  float a = __fsub_rn(th, d[0]);
+  float rh = __fadd_rn(a, tl);
+  float rl = __fsub_rn(tl, __fsub_rn(rh, a));
+#pragma unroll
+  for (int sl = 1; sl < 4; ++sl) {
+    if (sl < nslice) {
+      const float x = rh * w, xl = rl * w;
+      if (sl == nslice - 1) {
+        d[sl] = rint_f(__fadd_rn(x, xl));
+      } else {
+        d[sl] = rint_f(x);
+        a = __fsub_rn(x, d[sl]);
+        rh = __fadd_rn(a, xl);
+        rl = __fsub_rn(xl, __fsub_rn(rh, a));
+      }
+    }
+  }
+}
+
+// The slices of a row held in registers (kFusedPPT column pairs a thread, each element as its
+// FP32 split (hi, lo) in the bits of v: {hi_0, lo_0, hi_1, lo_1}): digits of y 2^k with
+// k = p2 - bits (nslice - 1) (p2 <= -1000: an all-zero row), written as FP16 pairs, one plane
+// per slice.
 template <int NS, int BITS, int THREADS>
 __device__ __forceinline__ void write_row_slices(const uint4 (&v)[kFusedPPT], int npairs, int p2,
                                                  uint32_t* orow, int64_t plane2, int nslice,
                                                  int bits) {
   const int ns = NS ? NS : nslice;
+  const int b = BITS ? BITS : bits;
+  // k is within [-54, 85] for any finite non-zero row (the FP32 norm's range); clamped anyway
+  const int k = min(max(p2 - b * (ns - 1), -126), 127);
+  const float scale = __int_as_float((k + 127) << 23);
+  const bool zero = p2 <= -1000;
 #pragma unroll
   for (int i = 0; i < kFusedPPT; ++i) {
     const int p = i * THREADS + threadIdx.x;
     if (p < npairs) {
-      int d0[4] = {0, 0, 0, 0}, d1[4] = {0, 0, 0, 0};
-      if (p2 > -1000) {
-        slice_digits_t<NS, BITS>(
-            static_cast<long long>((static_cast<unsigned long long>(v[i].y) << 32) | v[i].x), p2,
-            nslice, bits, d0);
-        slice_digits_t<NS, BITS>(
-            static_cast<long long>((static_cast<unsigned long long>(v[i].w) << 32) | v[i].z), p2,
-            nslice, bits, d1);
+      float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+      if (!zero) {
+        slice_digits_f<NS, BITS>(__uint_as_float(v[i].x), __uint_as_float(v[i].y), scale, ns, b,
+                                 d0);
+        slice_digits_f<NS, BITS>(__uint_as_float(v[i].z), __uint_as_float(v[i].w), scale, ns, b,
+                                 d1);
       }
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
-        if (s < ns) orow[s * plane2 + p] = half_pair(d0[s], d1[s]);
+      for (int sl = 0; sl < 4; ++sl)
+        if (sl < ns) {
+          const __half2 hh = __floats2half2_rn(d0[sl], d1[sl]);
+          orow[sl * plane2 + p] = *reinterpret_cast<const uint32_t*>(&hh);
+        }
     }
   }
 }
@@ -761,7 +924,8 @@ __device__ __forceinline__ void form_slice_row(const uint4* xr, const uint4* x2r
                                                int64_t plane, int nslice, int bits,
                                                double* out_scale, double* row_dot, float* red_ss,
                                                DF* red_dot, int* shift_sh) {
-  constexpr bool kNeedX2 = HAS_X2 && ((MODE == kFormGeneral) || (DOT == kDotX2));
+  constexpr bool kNeedX2 =
+      HAS_X2 && ((MODE == kFormGeneral) || (MODE == kFormSplit) || (DOT == kDotX2));
   const bool with_x2 = HAS_X2;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint4 v[kFusedPPT], v2[kNeedX2 ? kFusedPPT : 1];
@@ -786,10 +950,10 @@ __device__ __forceinline__ void form_slice_row(const uint4* xr, const uint4* x2r
       const int p = p0 + lane;
       bool nz = false;
       if (p < npairs) {
-        uint4 y;
+        uint4 y, sp;
         nz = form_pair<MODE, DOT>(p, row, v[i], kNeedX2 ? v2[i] : v[i], with_x2, a, b, ak, aneg,
-                                  has_c, c, tr, yr, y, ss, acc);
-        v[i] = y;
+                                  has_c, c, tr, yr, y, ss, acc, &sp);
+        v[i] = sp;  // from here on the row is held as its FP32 splits
       }
       if (mrow != nullptr) {
         // 32 pairs = half a 128-column tile
@@ -861,7 +1025,7 @@ __device__ __forceinline__ void form_slice_dispatch(int dot, const uint4* xr, co
 }
 
 template <int THREADS, bool HAS_X2>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, HAS_X2 ? 1 : 1024 / THREADS)
     form_slice_fused_kernel(const double* X, int64_t ldx, const double* X2, int64_t ldx2,
                             int rows, int cols, const double* __restrict__ coef_dev, double ha,
                             double hb, double hc, double* Y, int64_t ldy, __half* out,
@@ -887,11 +1051,17 @@ __global__ void __launch_bounds__(THREADS)
   int mode = kFormGeneral;
   if (no_x2 && a == 1.0) mode = kFormPlain;
   else if (no_x2 && pow2_coef(a, ak, aneg)) mode = kFormPow2;
+  // slices only: form in double-float (no FP64 result to write, no filtering)
+  if (mode == kFormGeneral && Y == nullptr && tr.tau_bits == 0ull) mode = kFormSplit;
   const uint4* xr = reinterpret_cast<const uint4*>(X + row * ldx);
   const uint4* x2r = HAS_X2 ? reinterpret_cast<const uint4*>(X2 + row * ldx2) : nullptr;
   uint4* yr = (Y != nullptr) ? reinterpret_cast<uint4*>(Y + row * ldy) : nullptr;
   const int npairs = cols >> 1;
-  if (mode == kFormPlain)
+  if (mode == kFormSplit)
+    form_slice_dispatch<kFormSplit, THREADS, HAS_X2>(dot, xr, x2r, yr, npairs, row, a, b, ak, aneg,
+                                               has_c, c, tr, out, out_ld, plane, nslice, bits,
+                                               out_scale, row_dot, red_ss, red_dot, shift_sh);
+  else if (mode == kFormPlain)
     form_slice_dispatch<kFormPlain, THREADS, HAS_X2>(dot, xr, x2r, yr, npairs, row, a, b, ak, aneg, has_c,
                                              c, tr, out, out_ld, plane, nslice, bits, out_scale,
                                              row_dot, red_ss, red_dot, shift_sh);
@@ -954,6 +1124,8 @@ __global__ void __launch_bounds__(THREADS)
       split_words(v[i].w, v[i].z, h1, l1);
       split_words(x[i].y, x[i].x, g0, k0);
       split_words(x[i].w, x[i].z, g1, k1);
+      v[i] = make_uint4(__float_as_uint(h0), __float_as_uint(l0), __float_as_uint(h1),
+                        __float_as_uint(l1));  // the slices are cut from the FP32 splits
       ss = fmaf(h0, h0, fmaf(h1, h1, ss));
       a3 = df_fma(df_fma(a3, h0, l0, g0, k0), h1, l1, g1, k1);
       a4 = df_fma(df_fma(a4, h0, l0, h0, l0), h1, l1, h1, l1);
@@ -1077,50 +1249,6 @@ __global__ void __launch_bounds__(THREADS)
     DF t{0.0f, 0.0f};
     for (int j = 0; j < THREADS / 32; ++j) t = df_add(t, red[j]);
     partials[row] = df_to_double(t);
-  }
-}
-
-// y = A x for the Lanczos recurrence, one row per block with all of the row's loads in flight;
-// x as double-float (xh + xl), sums in double-float; partials[row] = y_row^2.
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS)
-    matvec_rows_kernel(const double* A, int64_t lda, int n, const float* __restrict__ xh,
-                       const float* __restrict__ xl, double* y, double* partials) {
-  __shared__ DF red[THREADS / 32];
-  const int row = blockIdx.x;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int npairs = n >> 1;
-  const uint4* ar = reinterpret_cast<const uint4*>(A + row * lda);
-  const float2* xh2 = reinterpret_cast<const float2*>(xh);
-  const float2* xl2 = reinterpret_cast<const float2*>(xl);
-  uint4 va[kFusedPPT];
-#pragma unroll
-  for (int i = 0; i < kFusedPPT; ++i) {
-    const int p = i * THREADS + threadIdx.x;
-    va[i] = make_uint4(0u, 0u, 0u, 0u);
-    if (p < npairs) va[i] = ar[p];
-  }
-  DF acc{0.0f, 0.0f};
-#pragma unroll
-  for (int i = 0; i < kFusedPPT; ++i) {
-    const int p = i * THREADS + threadIdx.x;
-    if (p < npairs) {
-      const float2 bh = xh2[p], bl = xl2[p];
-      float h0, l0, h1, l1;
-      split_words(va[i].y, va[i].x, h0, l0);
-      split_words(va[i].w, va[i].z, h1, l1);
-      acc = df_fma(df_fma(acc, h0, l0, bh.x, bl.x), h1, l1, bh.y, bl.y);
-    }
-  }
-  acc = df_warp_sum(acc);
-  if (lane == 0) red[w] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    DF t{0.0f, 0.0f};
-    for (int j = 0; j < THREADS / 32; ++j) t = df_add(t, red[j]);
-    const double yi = df_to_double(t);
-    y[row] = yi;
-    partials[row] = yi * yi;
   }
 }
 
@@ -1524,192 +1652,234 @@ __global__ void x0_coef_kernel(const double* bounds, double* coef) {
   coef[2] = hi / w;
 }
 
-// ---- matrix-vector products in double-float (the Lanczos recurrence's y = A v) --------------
-// v is kept as a double-float pair (xh, xl) so that y = A v needs no FP64 instruction.
-
-// y_i = sum_j A_ij x_j (double-float), one warp per row; per-block partial sums of y_i^2.
-__global__ void __launch_bounds__(kRowsPerBlock * 32)
-    matvec_kernel(const double* __restrict__ A, int64_t lda, int n, const float* __restrict__ xh,
-                  const float* __restrict__ xl, double* y, double* partials) {
-  __shared__ double sq[kRowsPerBlock];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = blockIdx.x * kRowsPerBlock + w;
-  double yi = 0.0;
-  if (row < n) {
-    const uint2* ar = reinterpret_cast<const uint2*>(A + row * lda);
-    DF acc{0.0f, 0.0f};
-    for (int j = lane; j < n; j += 32) {
-      const uint2 a = ar[j];
-      float ah, al;
-      split_words(a.y, a.x, ah, al);
-      acc = df_fma(acc, ah, al, xh[j], xl[j]);
-    }
-    acc = df_warp_sum(acc);
-    yi = df_to_double(acc);
-    if (lane == 0) y[row] = yi;
-  }
-  if (lane == 0) sq[w] = yi * yi;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < kRowsPerBlock; ++i) t += sq[i];
-    partials[blockIdx.x] = t;
-  }
-}
-
 // ---- Lanczos estimates of the extreme eigenvalues of a symmetric matrix ---------------------
 // Three-term recurrence without reorthogonalisation (its extreme Ritz values converge first and
 // are not disturbed by the loss of orthogonality, which only adds copies of converged values):
 //   w = A v_k - beta_{k-1} v_{k-1},  alpha_k = v_k . w,  w -= alpha_k v_k,  beta_k = ||w||,
 //   v_{k+1} = w / beta_k.
-// v lives in FP64 (v, vprev) and as a double-float pair (xh, xl) for the matrix-vector product.
+// The estimates only place the Newton-Schulz scale and the bounds of the initial guess, both
+// with margins of several percent, so the recurrence runs in FP32: matrix elements truncated to
+// FP32 from their bit patterns (relative error below 2^-23, no FP64 instruction), FP32 vectors
+// and sums in a fixed order.  The Ritz values then carry errors of order 1e-6 ||A||, far inside
+// the margins.
 
-// Start vector: a fixed pseudo-random vector (integer hash) in [-0.5, 0.5), normalised; vprev = 0.
-__global__ void lanczos_init_kernel(int n, float* xh, float* xl, double* v, double* vprev) {
-  __shared__ double red[32];
-  __shared__ double inv_sh;
-  double acc = 0.0;
+// Start vector: a fixed pseudo-random vector (integer hash) in [-0.5, 0.5), normalised; the
+// previous vector 0.  One block.
+__global__ void lanczos_init_kernel(int n, float* x, float* xprev) {
+  __shared__ float red[32];
+  __shared__ float inv_sh;
+  float acc = 0.0f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     unsigned h = static_cast<unsigned>(i) * 2654435761u + 0x9E3779B9u;
     h ^= h >> 16;
     h *= 0x85EBCA6Bu;
     h ^= h >> 13;
-    const double x = static_cast<double>(__uint_as_float(0x3F800000u | (h >> 9))) - 1.5;
-    v[i] = x;  // in [-0.5, 0.5)
-    acc += x * x;
+    const float v = __uint_as_float(0x3F800000u | (h >> 9)) - 1.5f;  // in [-0.5, 0.5)
+    x[i] = v;
+    acc = fmaf(v, v, acc);
   }
-  acc = block_sum(acc, red);
-  if (threadIdx.x == 0) inv_sh = acc > 0.0 ? 1.0 / sqrt(acc) : 0.0;
+  acc = block_sum_f(acc, red);
+  if (threadIdx.x == 0) inv_sh = acc > 0.0f ? rsqrtf(acc) : 0.0f;
   __syncthreads();
+  const float inv = inv_sh;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double x = v[i] * inv_sh;
-    v[i] = x;
-    vprev[i] = 0.0;
-    const float hi = static_cast<float>(x);
-    xh[i] = hi;
-    xl[i] = static_cast<float>(x - static_cast<double>(hi));
+    x[i] *= inv;
+    xprev[i] = 0.0f;
   }
+}
+
+// y = A x, one row per block with all of the row's loads in flight (rows of even length up to
+// kFusedMaxCols, 16-byte aligned).
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+    matvec_rows_f32_kernel(const double* A, int64_t lda, int n, const float* __restrict__ x,
+                           float* y) {
+  __shared__ float red[THREADS / 32];
+  const int row = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int npairs = n >> 1;
+  const uint4* ar = reinterpret_cast<const uint4*>(A + row * lda);
+  const float2* x2 = reinterpret_cast<const float2*>(x);
+  uint4 va[kFusedPPT];
+#pragma unroll
+  for (int i = 0; i < kFusedPPT; ++i) {
+    const int p = i * THREADS + threadIdx.x;
+    va[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (p < npairs) va[i] = ar[p];
+  }
+  float acc = 0.0f;
+#pragma unroll
+  for (int i = 0; i < kFusedPPT; ++i) {
+    const int p = i * THREADS + threadIdx.x;
+    if (p < npairs) {
+      const float2 xv = x2[p];
+      acc = fmaf(trunc_words(va[i].y, va[i].x), xv.x, acc);
+      acc = fmaf(trunc_words(va[i].w, va[i].z), xv.y, acc);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) red[w] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int j = 0; j < THREADS / 32; ++j) t += red[j];
+    y[row] = t;
+  }
+}
+
+// y = A x for any n and leading dimension: one warp per row.
+__global__ void __launch_bounds__(kRowsPerBlock * 32)
+    matvec_f32_kernel(const double* __restrict__ A, int64_t lda, int n,
+                      const float* __restrict__ x, float* y) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * kRowsPerBlock + w;
+  if (row >= n) return;
+  const uint2* ar = reinterpret_cast<const uint2*>(A + row * lda);
+  float acc = 0.0f;
+  for (int j = lane; j < n; j += 32) {
+    const uint2 a = ar[j];
+    acc = fmaf(trunc_words(a.y, a.x), x[j], acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[row] = acc;
 }
 
 // One step after y = A v: alpha_k and beta_k into ab[k] and ab[kmax + k], then the next v.
-// A beta at the rounding level (an invariant subspace) ends the recurrence: the next vector is
-// left zero, so every later alpha and beta is zero and the Ritz values stay those found.
-__global__ void lanczos_update_kernel(double* y, double* v, double* vprev, float* xh, float* xl,
-                                      int n, double* ab, int k, int kmax) {
-  __shared__ double red[32];
-  __shared__ double alpha_sh, inv_sh;
-  const double beta_prev = (k > 0) ? ab[kmax + k - 1] : 0.0;
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += v[i] * y[i];
-  acc = block_sum(acc, red);
+// A beta at the FP32 rounding level of the step (an invariant subspace) ends the recurrence: the
+// next vector is left zero, so every later alpha and beta is zero and the Ritz values stay
+// those found.  One block.
+__global__ void lanczos_update_kernel(float* y, float* x, float* xprev, int n, double* ab, int k,
+                                      int kmax) {
+  __shared__ float red[32];
+  __shared__ float alpha_sh, inv_sh;
+  const float beta_prev = (k > 0) ? static_cast<float>(ab[kmax + k - 1]) : 0.0f;
+  float acc = 0.0f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc = fmaf(x[i], y[i], acc);
+  acc = block_sum_f(acc, red);
   if (threadIdx.x == 0) alpha_sh = acc;
   __syncthreads();
-  const double alpha = alpha_sh;
-  double ss = 0.0;
+  const float alpha = alpha_sh;
+  float ss = 0.0f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double w = y[i] - alpha * v[i] - beta_prev * vprev[i];
-    y[i] = w;
-    ss += w * w;
+    const float wv = y[i] - alpha * x[i] - beta_prev * xprev[i];
+    y[i] = wv;
+    ss = fmaf(wv, wv, ss);
   }
-  ss = block_sum(ss, red);
+  ss = block_sum_f(ss, red);
   if (threadIdx.x == 0) {
-    const double beta = sqrt(ss);
-    ab[k] = alpha;
-    // relative to the size of the recurrence's terms (v has unit norm, or is zero once the
-    // recurrence has ended): below it the new direction is rounding noise
-    const bool ends = !(beta > 1e-12 * (fabs(alpha) + beta_prev));
-    ab[kmax + k] = ends ? 0.0 : beta;
-    inv_sh = ends ? 0.0 : 1.0 / beta;
+    const float beta = sqrtf(ss);
+    ab[k] = static_cast<double>(alpha);
+    // relative to the size of the step's terms (v has unit norm, or is zero once the recurrence
+    // has ended): below it the new direction is FP32 rounding noise
+    const bool ends = !(beta > 1e-5f * (fabsf(alpha) + beta_prev));
+    ab[kmax + k] = ends ? 0.0 : static_cast<double>(beta);
+    inv_sh = ends ? 0.0f : 1.0f / beta;
   }
   __syncthreads();
-  const double inv = inv_sh;
+  const float inv = inv_sh;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double vn = y[i] * inv;
-    vprev[i] = v[i];
-    v[i] = vn;
-    const float hi = static_cast<float>(vn);
-    xh[i] = hi;
-    xl[i] = static_cast<float>(vn - static_cast<double>(hi));
+    xprev[i] = x[i];
+    x[i] = y[i] * inv;
   }
 }
 
-// Number of eigenvalues below x of the tridiagonal (a, b) (negative pivots of T - x I).
-__device__ int sturm_count_dev(const double* a, const double* b, int m, double x) {
+// Number of eigenvalues below x of the tridiagonal (a, b2 = b^2) (negative pivots of T - x I).
+__device__ int sturm_count_f(const float* a, const float* b2, int m, float x) {
   int cnt = 0;
-  double q = 1.0;
+  float q = 1.0f;
   for (int i = 0; i < m; ++i) {
-    const double off = (i > 0) ? b[i - 1] * b[i - 1] / q : 0.0;
-    q = a[i] - x - off;
-    if (q == 0.0) q = -1e-300;
-    if (q < 0.0) ++cnt;
+    q = a[i] - x - ((i > 0) ? b2[i - 1] / q : 0.0f);
+    if (q == 0.0f) q = -1e-30f;
+    if (q < 0.0f) ++cnt;
   }
   return cnt;
 }
 
-// Spectral bounds of H~ from the Lanczos tridiagonal (small + lanczos_at) and Gershgorin's
-// interval (small + gersh_at): the extreme Ritz values by bisection, widened by 2% of their
-// span and clamped to Gershgorin's interval, into small[bounds_at..+1]; small[bounds_at+2] = 1 when
-// the estimate (not Gershgorin's interval) is used.
+// Spectral bounds of a matrix from its Lanczos tridiagonal (small + lanczos_at) and
+// Gershgorin's interval (small + gersh_at): the extreme Ritz values by multisection on FP32
+// Sturm counts, widened by 2% of their span and clamped to Gershgorin's interval, into
+// small[bounds_at..+1]; small[bounds_at+2] = 1 when the estimate (not Gershgorin's interval) is
+// used.  Two warps, one per end; each round evaluates 32 Sturm counts at once and shrinks the
+// bracket 33-fold, down to the FP32 resolution of the counts (about 1e-6 of the tridiagonal's
+// norm), which takes five or six rounds.
 __global__ void lanczos_bounds_kernel(double* small, int steps, int gersh_at, int lanczos_at,
                                       int bounds_at) {
-  // one warp: each multisection round evaluates 32 Sturm counts at once and shrinks the
-  // interval 33-fold, so the two extremes take ~10 rounds each
-  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
+  __shared__ float af[kMaxLanczos], b2f[kMaxLanczos];
+  __shared__ int m_sh, finite_sh;
+  __shared__ float glo_sh, ghi_sh, t_sh[2];
+  if (blockIdx.x != 0) return;
+  const int lane = threadIdx.x & 31, end = threadIdx.x >> 5;
   const double g_lo = small[gersh_at], g_hi = small[gersh_at + 1];
   const double* a = small + lanczos_at;
   const double* b = a + steps;
-  int m = steps;
-  for (int k = 0; k < steps; ++k)
-    if (!(b[k] > 0.0)) {
-      m = k + 1;
-      break;
+  if (threadIdx.x == 0) {
+    int m = steps;
+    for (int k = 0; k < steps; ++k)
+      if (!(b[k] > 0.0)) {
+        m = k + 1;
+        break;
+      }
+    bool finite = true;
+    float glo = INFINITY, ghi = -INFINITY;
+    for (int i = 0; i < m; ++i) {
+      finite = finite && isfinite(a[i]) && isfinite(b[i]);
+      af[i] = static_cast<float>(a[i]);
+      b2f[i] = static_cast<float>(b[i] * b[i]);
+      const float r = static_cast<float>((i > 0 ? fabs(b[i - 1]) : 0.0) +
+                                         (i + 1 < m ? fabs(b[i]) : 0.0));
+      glo = fminf(glo, af[i] - r);
+      ghi = fmaxf(ghi, af[i] + r);
     }
-  bool finite = true;
-  double glo = INFINITY, ghi = -INFINITY;
-  for (int i = 0; i < m; ++i) {
-    finite = finite && isfinite(a[i]) && isfinite(b[i]);
-    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < m ? fabs(b[i]) : 0.0);
-    glo = fmin(glo, a[i] - r);
-    ghi = fmax(ghi, a[i] + r);
+    m_sh = m;
+    finite_sh = finite ? 1 : 0;
+    // the tridiagonal's own Gershgorin interval, opened by its FP32 resolution
+    const float pad = 1e-6f * fmaxf(fabsf(glo), fabsf(ghi)) + 1e-30f;
+    glo_sh = glo - pad;
+    ghi_sh = ghi + pad;
   }
+  __syncthreads();
+  const int m = m_sh;
+  if (finite_sh) {
+    // end 0: the least x with at least one eigenvalue below it; end 1: with all m below it
+    const int want = (end == 0) ? 1 : m;
+    float l = glo_sh, u = ghi_sh;
+    const float tol = 1e-6f * fmaxf(fabsf(glo_sh), fabsf(ghi_sh));
+    for (int it = 0; it < 12 && u - l > tol; ++it) {
+      const float x = l + (u - l) * static_cast<float>(lane + 1) * (1.0f / 33.0f);
+      const bool above = sturm_count_f(af, b2f, m, x) >= want;
+      const unsigned mask = __ballot_sync(0xffffffffu, above);
+      // the first point at or above the target bounds it from above, the one before from below
+      const int first = mask ? __ffs(mask) - 1 : 32;
+      const float nu = (first < 32) ? l + (u - l) * static_cast<float>(first + 1) * (1.0f / 33.0f)
+                                    : u;
+      const float nl = (first > 0) ? l + (u - l) * static_cast<float>(first) * (1.0f / 33.0f) : l;
+      l = nl;
+      u = nu;
+    }
+    if (lane == 0) t_sh[end] = (end == 0) ? l : u;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   double lo = g_lo, hi = g_hi;
   double t_raw[2] = {g_lo, g_hi};
-  if (finite) {
-    double t[2];
-    for (int end = 0; end < 2; ++end) {
-      // end 0: the least x with at least one eigenvalue below it; end 1: with all m below it
-      const int want = (end == 0) ? 1 : m;
-      double l = glo, u = ghi;
-      for (int it = 0; it < 64 && u - l > 1e-15 * (fabs(l) + fabs(u)); ++it) {
-        const double x = l + (u - l) * (lane + 1) / 33.0;
-        const bool above = sturm_count_dev(a, b, m, x) >= want;
-        const unsigned mask = __ballot_sync(0xffffffffu, above);
-        // the first point at or above the target bounds it from above, the one before from below
-        const int first = mask ? __ffs(mask) - 1 : 32;
-        const double nu = (first < 32) ? l + (u - l) * (first + 1) / 33.0 : u;
-        const double nl = (first > 0) ? l + (u - l) * first / 33.0 : l;
-        l = nl;
-        u = nu;
-      }
-      t[end] = u;
-    }
-    t_raw[0] = t[0];
-    t_raw[1] = t[1];
-    const double margin = 0.02 * (t[1] - t[0]) + 1e-12 * fmax(fabs(t[0]), fabs(t[1]));
-    const double c_lo = fmax(g_lo, t[0] - margin), c_hi = fmin(g_hi, t[1] + margin);
+  if (finite_sh) {
+    const double t0 = t_sh[0], t1 = t_sh[1];
+    t_raw[0] = t0;
+    t_raw[1] = t1;
+    const double margin = 0.02 * (t1 - t0) + 1e-6 * fmax(fabs(t0), fabs(t1));
+    const double c_lo = fmax(g_lo, t0 - margin), c_hi = fmin(g_hi, t1 + margin);
     if (isfinite(c_lo) && isfinite(c_hi) && c_hi > c_lo) {
       lo = c_lo;
       hi = c_hi;
     }
   }
-  if (lane == 0) {
-    small[bounds_at] = lo;
-    small[bounds_at + 1] = hi;
-    small[bounds_at + 2] = (lo == g_lo && hi == g_hi) ? 0.0 : 1.0;  // 1: the estimate was used
-    small[bounds_at + 3] = finite ? t_raw[0] : g_lo;                 // the extreme Ritz values
-    small[bounds_at + 4] = finite ? t_raw[1] : g_hi;
-  }
+  small[bounds_at] = lo;
+  small[bounds_at + 1] = hi;
+  small[bounds_at + 2] = (lo == g_lo && hi == g_hi) ? 0.0 : 1.0;  // 1: the estimate was used
+  small[bounds_at + 3] = finite_sh ? t_raw[0] : g_lo;              // the extreme Ritz values
+  small[bounds_at + 4] = finite_sh ? t_raw[1] : g_hi;
 }
 
 __global__ void scale_coef_kernel(const double* bounds, int inv_sqrt, double* coef) {
@@ -1968,37 +2138,37 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
 
 cudaError_t lanczos(const double* A, int64_t lda, int n, int steps, double* work,
                     double* partials, double* ab_dev, cudaStream_t stream) {
+  (void)partials;
   if (n <= 0 || steps <= 0) return cudaSuccess;
-  float* xh = reinterpret_cast<float*>(work);
-  float* xl = xh + n;
-  double* y = work + n;
-  double* v = work + 2 * static_cast<int64_t>(n);
-  double* vprev = work + 3 * static_cast<int64_t>(n);
+  float* x = reinterpret_cast<float*>(work);
+  float* xprev = x + n;
+  float* y = xprev + n;
   const bool rows_fit = n % 2 == 0 && n <= kFusedMaxCols && lda % 2 == 0 &&
                         (reinterpret_cast<uintptr_t>(A) & 15) == 0;
   const int nb = (n + kRowsPerBlock - 1) / kRowsPerBlock;
   count_launch();
-  lanczos_init_kernel<<<1, 1024, 0, stream>>>(n, xh, xl, v, vprev);
+  lanczos_init_kernel<<<1, 1024, 0, stream>>>(n, x, xprev);
   for (int k = 0; k < steps; ++k) {
     count_launch();
     if (!rows_fit)
-      matvec_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, n, xh, xl, y, partials);
+      matvec_f32_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, n, x, y);
     else if (n / 2 <= 128 * kFusedPPT)
-      matvec_rows_kernel<128><<<n, 128, 0, stream>>>(A, lda, n, xh, xl, y, partials);
+      matvec_rows_f32_kernel<128><<<n, 128, 0, stream>>>(A, lda, n, x, y);
     else if (n / 2 <= 256 * kFusedPPT)
-      matvec_rows_kernel<256><<<n, 256, 0, stream>>>(A, lda, n, xh, xl, y, partials);
+      matvec_rows_f32_kernel<256><<<n, 256, 0, stream>>>(A, lda, n, x, y);
     else
-      matvec_rows_kernel<512><<<n, 512, 0, stream>>>(A, lda, n, xh, xl, y, partials);
+      matvec_rows_f32_kernel<512><<<n, 512, 0, stream>>>(A, lda, n, x, y);
     count_launch();
-    lanczos_update_kernel<<<1, 1024, 0, stream>>>(y, v, vprev, xh, xl, n, ab_dev, k, steps);
+    lanczos_update_kernel<<<1, 1024, 0, stream>>>(y, x, xprev, n, ab_dev, k, steps);
   }
   return cudaGetLastError();
 }
 
 cudaError_t lanczos_bounds(double* small, int steps, int gersh_at, int lanczos_at, int bounds_at,
                            cudaStream_t stream) {
+  if (steps > kMaxLanczos) return cudaErrorInvalidValue;
   count_launch();
-  lanczos_bounds_kernel<<<1, 32, 0, stream>>>(small, steps, gersh_at, lanczos_at, bounds_at);
+  lanczos_bounds_kernel<<<1, 64, 0, stream>>>(small, steps, gersh_at, lanczos_at, bounds_at);
   return cudaGetLastError();
 }
 

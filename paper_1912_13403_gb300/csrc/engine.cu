@@ -117,12 +117,12 @@ double alg_flops(const gdm_handle* h, bool sym) {
 }
 
 // Tensor-pipe work of one sliced launch: slice pairs x computed tile area x 2 K
-double sliced_flops(const gdm_handle* h, int ph, bool sym) {
+double sliced_flops(const gdm_handle* h, const Precision& pr, bool sym) {
   const double n = static_cast<double>(h->n);
   const double t = std::ceil(n / 128.0);
   const double tiles = sym ? t * (t + 1) / 2 : t * t;
   SlicedGemmArgs tmp;
-  const int pairs = build_pairs(h->phase[ph].nslice, h->phase[ph].max_order, &tmp);
+  const int pairs = build_pairs(pr.nslice, pr.max_order, &tmp);
   return pairs * tiles * 128.0 * 128.0 * 2.0 * n;
 }
 
@@ -130,11 +130,15 @@ double sliced_flops(const gdm_handle* h, int ph, bool sym) {
 // exact_diag: recompute the diagonal from the FP64 operands.  Needed where the two factors
 // have (nearly) parallel rows (X X, X^2 W, delta delta): there the residual-slice terms of the
 // diagonal add up with one sign and the FP32 accumulators' truncation biases them.
+// fmt: a format other than the phase's for this product (its slice width must be the
+// operands'; it may read only their leading slices), e.g. a short format for a small term.
 cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const double* D,
                     double alpha, double beta, double diag, bool sym, int ph,
-                    const double* coef = nullptr, bool exact_diag = false) {
+                    const double* coef = nullptr, bool exact_diag = false,
+                    const Precision* fmt = nullptr) {
   const int n = static_cast<int>(h->n);
   if (sliced(h, ph)) {
+    const Precision& pr = fmt != nullptr ? *fmt : h->phase[ph];
     SlicedGemmArgs a;
     a.mode = sym ? kGemmSym : 0;
     a.C = C;
@@ -160,7 +164,7 @@ cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const dou
       a.kcount = reinterpret_cast<unsigned long long*>(h->small + SM_KCOUNT);
       const double t = std::ceil(static_cast<double>(n) / 128.0);
       const double nk = std::ceil(static_cast<double>(n) /
-                                  static_cast<double>(sliced_gemm_bk(h->phase[ph].nslice)));
+                                  static_cast<double>(sliced_gemm_bk(pr.nslice)));
       h->kstages_dense += (sym ? t * (t + 1) / 2 : t * t) * nk;
     }
     // exact diagonal from the row dot products of the right operand's slicing pass, when that
@@ -173,11 +177,11 @@ cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const dou
       e1 = pool_event(h);
       cudaEventRecord(e0, h->stream);
     }
-    cudaError_t e = sliced_gemm(*A.sl, *Bt.sl, h->phase[ph], a, h->stream);
+    cudaError_t e = sliced_gemm(*A.sl, *Bt.sl, pr, a, h->stream);
     if (e != cudaSuccess) return e;
     if (h->profiling) {
       cudaEventRecord(e1, h->stream);
-      h->prof_pending.push_back({e0, e1, sliced_flops(h, ph, sym), alg_flops(h, sym), 0, ph});
+      h->prof_pending.push_back({e0, e1, sliced_flops(h, pr, sym), alg_flops(h, sym), 0, ph});
     }
     if (!exact_diag || a.diag_dot != nullptr) return cudaSuccess;
     e = diag_fix(A.f, h->ld, Bt.f, h->ld, C, h->ld, n, n, alpha, beta, D, h->ld, diag, coef,
@@ -452,14 +456,26 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
     // the sliced products leave in Z^T S Z, and another step cannot lower it.
     if (refine_at_floor(derr_prev, derr)) break;
     derr_prev = derr;
+    // The update as Z <- Z + Z G with G = F - I = -delta/2 + 3 delta^2/8: both products have a
+    // small factor (||delta|| <= ~0.005 after the hand-over), so they read only the leading
+    // slices of their operands - delta^2 two (20 bits with the 9-bit format), Z G three
+    // (29 bits) - and Z itself is added exactly in FP64 by the epilogue.  Their rounding then
+    // stays far below the step's remainder (5/8) delta^3.  delta^2 keeps the exact diagonal
+    // (delta's rows are parallel to themselves); Z G needs none (Z's rows are not parallel to
+    // G's, and Z's own diagonal is added in FP64).
+    const Precision& rp = h->phase[GDM_PHASE_REFINE];
+    const int sq_ns = std::min(rp.nslice, 2), zg_ns = std::min(rp.nslice, 3);
+    const Precision sq_fmt{sq_ns, std::min(1, 2 * (sq_ns - 1)), rp.bits};
+    const Precision zg_fmt{zg_ns, std::min(2, 2 * (zg_ns - 1)), rp.bits};
     CK(slice(h, Dl, &h->sl[SL_B], GDM_PHASE_REFINE, kDotSelf));
-    CK(product(h, {Dl, &h->sl[SL_B]}, {Dl, &h->sl[SL_B]}, F, nullptr, Dl, 0.375, -0.5, 1.0, true,
-               GDM_PHASE_REFINE, nullptr, true));                    // F = I - d/2 + 3d^2/8
+    CK(product(h, {Dl, &h->sl[SL_B]}, {Dl, &h->sl[SL_B]}, F, nullptr, Dl, 0.375, -0.5, 0.0, true,
+               GDM_PHASE_REFINE, nullptr, true, &sq_fmt));           // G = -d/2 + 3d^2/8
     CK(slice(h, F, &h->sl[SL_A], GDM_PHASE_REFINE));
     double* Znew = h->f[F_X];
     double* Zt_new = h->f[F_X2];
-    CK(product(h, zc, {F, &h->sl[SL_A]}, Znew, Zt_new, nullptr, 1.0, 0.0, 0.0, false,
-               GDM_PHASE_REFINE, nullptr, true));                    // Z <- Z F
+    // Z + Z G: the addend is read transposed, so Z enters through Z^T
+    CK(product(h, zc, {F, &h->sl[SL_A]}, Znew, Zt_new, zct.f, 1.0, 1.0, 0.0, false,
+               GDM_PHASE_REFINE, nullptr, false, &zg_fmt));          // Z <- Z (I + G)
     std::swap(h->f[F_Z], h->f[F_X]);
     std::swap(h->f[F_ZT], h->f[F_X2]);
     CK(slice(h, h->f[F_Z], &h->sl[SL_Z], GDM_PHASE_REFINE));

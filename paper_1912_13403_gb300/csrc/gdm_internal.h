@@ -9,6 +9,7 @@
 namespace gdm {
 
 constexpr int kMaxPairs = 16;
+constexpr int kMaxLanczos = 64;  // Lanczos steps at most (the tridiagonal's storage)
 constexpr int kEpilogueWarps = 8;   // split-k counters per tile (one per epilogue warp)
 
 // Error word written by kernels (never a trap): bit flags, OR-ed atomically.
@@ -67,7 +68,7 @@ struct SlicedGemmArgs {
   int64_t ldc = 0;
   double* Ct = nullptr;               // optional: also write C^T
   int64_t ldct = 0;
-  const double* D = nullptr;          // optional addend, read as D^T (pass symmetric D only)
+  const double* D = nullptr;          // optional addend, read transposed: C_ij += beta D_ji
   int64_t ldd = 0;
   double alpha = 1.0, beta = 0.0;
   double diag = 0.0;                  // added to the diagonal of C
@@ -198,7 +199,8 @@ cudaError_t zero_column(double* A, int64_t lda, int rows, int col, cudaStream_t 
 // `steps` Lanczos steps on the symmetric n x n matrix A from a fixed start vector (no
 // reorthogonalisation): ab_dev[k] = alpha_k and ab_dev[steps + k] = beta_k for k < steps, the
 // diagonal and off-diagonal of the tridiagonal whose extreme eigenvalues estimate A's from inside.
-// `work` holds >= 4 n doubles, `partials` >= n.
+// FP32 recurrence (see elementwise.cu); `work` holds >= 2 n doubles (three FP32 vectors);
+// `partials` is unused.
 cudaError_t lanczos(const double* A, int64_t lda, int n, int steps, double* work,
                     double* partials, double* ab_dev, cudaStream_t stream);
 
@@ -207,7 +209,8 @@ cudaError_t lanczos(const double* A, int64_t lda, int n, int steps, double* work
 // by bisection on Sturm counts, widened by 2% of their span and clamped to Gershgorin's
 // interval, into small[bounds_at..+1]; small[bounds_at + 2] = 1 when the estimate is used, 0
 // when Gershgorin's interval is (a non-finite or degenerate recurrence); small[bounds_at + 3..4]
-// the extreme Ritz values themselves (Gershgorin's bounds when there are none).  One warp.
+// the extreme Ritz values themselves (Gershgorin's bounds when there are none).  FP32
+// arithmetic (estimates to ~1e-6 of the matrix norm); steps <= kMaxLanczos.
 cudaError_t lanczos_bounds(double* small, int steps, int gersh_at, int lanczos_at, int bounds_at,
                            cudaStream_t stream);
 

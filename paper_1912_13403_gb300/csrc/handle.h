@@ -27,7 +27,6 @@ enum SmallSlot {
   SM_EST_S = 168,    // 5: the same for S
   SM_LANCZOS = 32,   // 2 x kMaxLanczos: alpha_k, then beta_k, of the Lanczos recurrence on H~
 };
-constexpr int kMaxLanczos = 64;
   // lockstep batches: the problem's BatchCtl (batch.cu) from this double on
 constexpr int SM_BATCH = 256;
 

@@ -357,12 +357,16 @@ def test_truncated_purification_matches_oracle_route(g, tau):
     Q = p.factors["Q"]
     P_exact = Q[:, :p.n_occ] @ Q[:, :p.n_occ].T
     # the same fixed number of filtered steps on both sides (before the idempotency floor, where
-    # the stopping decision is sensitive to rounding).  At tau = 1e-5 the route is smooth in its
-    # input (a 1e-10 perturbation moves the 9th iterate by ~1e-9, measured on the oracle); at
-    # tau = 1e-7 elements near the threshold flip under 1e-12 perturbations (~6e-8 at 1e-12,
-    # ~6e-7 at 1e-10), so the bound there allows the flips of the GPU's rounding
+    # the stopping decision is sensitive to rounding).  The filtered map is discontinuous at the
+    # threshold: two evaluations that differ only by the products' rounding keep or drop the
+    # elements of X^2 lying within that rounding of tau, and each such flip moves the iterate by
+    # ~tau.  Measured on the oracle (symmetric perturbations of X^2 of 1e-11 of its largest
+    # element, the sliced products' rounding level, four trials): at tau = 1e-5 no flip in three
+    # trials (9th iterate moved by 1e-9), 4 flips in one (moved by 1.7e-5); at tau = 1e-7 8-18
+    # flips each (moved by 3e-7 to 4e-7).  The bounds allow a few flips; the whole-solve checks
+    # below hold the route to a quarter of its own truncation error.
     K = 9
-    bound_k = {1e-7: 2e-6, 1e-5: 1e-7}[tau]
+    bound_k = {1e-7: 2e-6, 1e-5: 5e-5}[tau]
     with g.Handle(p.n, p.n_occ) as h:
         h.set_truncation(tau)
         h.set_max_iter(0, K)

@@ -78,6 +78,7 @@ __global__ void batch_init_kernel(BatchCtl* c, Trs4State* st, double n_occ, int 
   st->idem = INFINITY;
   st->max_iter = max_purif;
   st->check_trace = 1;
+  st->floor_rule = 1;
   st->n = static_cast<double>(n);
 }
 

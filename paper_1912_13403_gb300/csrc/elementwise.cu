@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kRowThreads)
 }
 
 // ---- FP32 double-float arithmetic: FP64-accurate reductions without the FP64 ALU ----------
-// x ~ hi + lo with |x - hi - lo| <= 2^-52 |x|, from the FP64 bit pattern (integer operations
+// x ~ hi + lo with |x - hi - lo| < 2^-47 |x|, from the FP64 bit pattern (integer operations
 // and one int->float conversion).  Magnitudes outside FP32's normal range flush to 0 (inputs
 // of this engine are far from 2^-126).
 __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
@@ -121,8 +121,9 @@ __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
   }
 }
 
-// The same split from the two 32-bit words of the double (lo word first in memory), for data
-// that is loaded and kept in integer registers.
+// A split of the same kind from the two 32-bit words of the double (lo word first in memory),
+// for data that is loaded and kept in integer registers: hi the top 24 significant bits, lo the
+// next 23 (fewer integer operations than normalising the whole remainder).
 __device__ __forceinline__ void split_words(unsigned whi, unsigned wlo, float& hi, float& lo) {
   const int E = static_cast<int>((whi >> 20) & 0x7FF);
   const unsigned sign = whi & 0x80000000u;
@@ -130,17 +131,18 @@ __device__ __forceinline__ void split_words(unsigned whi, unsigned wlo, float& h
   // hi: the top 24 significant bits, truncated
   const unsigned hbits = sign | (static_cast<unsigned>(ef) << 23) | ((whi & 0xFFFFFu) << 3) |
                          (wlo >> 29);
-  // lo: the remaining 29 bits, normalised
-  const unsigned rem = wlo & ((1u << 29) - 1u);
-  const int msb = 31 - __clz(rem | 1u);
-  const int el = E - 1075 + msb + 127;
-  const unsigned mant = (msb >= 23) ? (rem >> (msb - 23)) : (rem << (23 - msb));
-  const unsigned lbits = sign | (static_cast<unsigned>(el) << 23) | (mant & 0x7FFFFFu);
+  // lo: the next 23 bits (bits 28..6 of the low word), as 2^k (1 + m 2^-23) - 2^k with 2^k the
+  // weight of bit 29: one exact FP32 subtraction (both operands share the exponent) instead of
+  // normalising the remainder bit by bit.  |x - hi - lo| < 2^-46 |x|.
+  const unsigned fk = sign | (static_cast<unsigned>(E - 919) << 23);  // 2^k, k = E - 1046
+  const float f1 = __uint_as_float(fk | ((wlo >> 6) & 0x7FFFFFu));
+  const float f0 = __uint_as_float(fk);
   const bool normal = (E != 0) && (E != 0x7FF) && (ef > 0) && (ef < 255);
   const unsigned nan_bit = (E == 0x7FF && ((whi & 0xFFFFFu) | wlo) != 0u) ? 1u : 0u;
   hi = __uint_as_float(normal ? hbits
                               : (E == 0x7FF || ef >= 255 ? (sign | 0x7F800000u | nan_bit) : 0u));
-  lo = __uint_as_float((normal && rem != 0u && el > 0) ? lbits : 0u);
+  // 2^k is an FP32 normal number for E >= 920 (|x| >= 2^-103); below that lo is dropped
+  lo = (normal && E >= 920) ? __fsub_rn(f1, f0) : 0.0f;
 }
 
 // x truncated to FP32 from the two words of the double (integer operations only): the top 24
@@ -467,15 +469,27 @@ enum { kFormPlain = 0, kFormPow2 = 1, kFormGeneral = 2, kFormSplit = 3 };
 struct DFCoef {
   float ah, al, bh, bl, ch, cl;
 };
+// The coefficients' FP32 splits from their bit patterns (split_words: 2^-46 relative), with
+// integer operations only: these are block-uniform values, and GB300's FP64 pipe would hold up
+// every thread of the block at its start.
 __device__ __forceinline__ DFCoef df_coef(double a, double b, double c) {
   DFCoef k;
-  k.ah = __double2float_rn(a);
-  k.al = __double2float_rn(a - static_cast<double>(k.ah));
-  k.bh = __double2float_rn(b);
-  k.bl = __double2float_rn(b - static_cast<double>(k.bh));
-  k.ch = __double2float_rn(c);
-  k.cl = __double2float_rn(c - static_cast<double>(k.ch));
+  split_words(static_cast<unsigned>(__double2hiint(a)), static_cast<unsigned>(__double2loint(a)),
+              k.ah, k.al);
+  split_words(static_cast<unsigned>(__double2hiint(b)), static_cast<unsigned>(__double2loint(b)),
+              k.bh, k.bl);
+  split_words(static_cast<unsigned>(__double2hiint(c)), static_cast<unsigned>(__double2loint(c)),
+              k.ch, k.cl);
   return k;
+}
+
+// Block-uniform tests of a coefficient on its bit pattern (no FP64 compare): x == 0 (either
+// sign) and x == 1.  A NaN is neither.
+__device__ __forceinline__ bool coef_is_zero(double x) {
+  return (static_cast<unsigned long long>(__double_as_longlong(x)) << 1) == 0ull;
+}
+__device__ __forceinline__ bool coef_is_one(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x)) == 0x3FF0000000000000ull;
 }
 // (hi, lo) = two_sum(a, b) for any a, b
 __device__ __forceinline__ void two_sum_f(float a, float b, float& hi, float& lo) {
@@ -552,10 +566,11 @@ template <int MODE, int DOT>
 __device__ __forceinline__ bool form_pair(int p, int row, uint4 x, uint4 x2, bool with_x2,
                                           double a, double b, int ak, bool aneg, bool has_c,
                                           double c, const TruncArgs& tr, uint4* yr, uint4& y,
-                                          float& ss, DF& acc, uint4* split = nullptr) {
+                                          float& ss, DF& acc, uint4* split = nullptr,
+                                          const DFCoef* kc = nullptr) {
   if constexpr (MODE == kFormSplit) {
     // slices-only pass (the host picks this mode only without an FP64 output and filtering)
-    const DFCoef k = df_coef(a, b, c);
+    const DFCoef k = (kc != nullptr) ? *kc : df_coef(a, b, c);
     float xh0, xl0, xh1, xl1, zh0 = 0.f, zl0 = 0.f, zh1 = 0.f, zl1 = 0.f;
     split_words(x.y, x.x, xh0, xl0);
     split_words(x.w, x.z, xh1, xl1);
@@ -730,10 +745,10 @@ __global__ void __launch_bounds__(kRowsPerBlock * 32, 4)
   // the forming arithmetic, decided once per warp (uniform)
   int ak = 0;
   bool aneg = false;
-  const bool no_x2 = (X2 == nullptr || b == 0.0);
-  const bool has_c = (c != 0.0);
+  const bool no_x2 = (X2 == nullptr || coef_is_zero(b));
+  const bool has_c = !coef_is_zero(c);
   int mode = kFormGeneral;
-  if (no_x2 && a == 1.0) mode = kFormPlain;
+  if (no_x2 && coef_is_one(a)) mode = kFormPlain;
   else if (no_x2 && pow2_coef(a, ak, aneg)) mode = kFormPow2;
   const uint4* xr = reinterpret_cast<const uint4*>(X + row * ldx);
   const uint4* x2r = (X2 != nullptr) ? reinterpret_cast<const uint4*>(X2 + row * ldx2) : nullptr;
@@ -829,14 +844,14 @@ __device__ __forceinline__ float rint_f(float x) {
 }
 
 // Balanced digits of t = y 2^k (|t| < 2^11) from y's FP32 split y = hi + lo (split_words: hi the
-// top 24 bits, lo the next 24, together y to 2^-47), on the FP32 pipe.  What remains of t after
+// top 24 bits, lo the next 23, together y to 2^-46), on the FP32 pipe.  What remains of t after
 // each digit is kept exactly as an unevaluated pair (r_hi, r_lo) with |r_lo| <= ulp(r_hi) / 2:
 //   d_0 = rint(t_hi),                 (r_hi, r_lo) = two_sum(t_hi - d_0, t_lo)
 //   d_s = rint(r_hi 2^b),             (r_hi, r_lo) = two_sum(r_hi 2^b - d_s, r_lo 2^b)
 //   d_last = rint(r_hi 2^b + r_lo 2^b).
 // Each digit is subtracted from the value it rounds, so the subtraction is exact, and the
 // two-sum (Dekker's fast form: |first| >= |second| or first = 0 holds here) is exact; the digits
-// therefore represent t to half a unit of the last slice (plus the split's 2^-47 |t|).  Deciding
+// therefore represent t to half a unit of the last slice (plus the split's 2^-46 |t|).  Deciding
 // a digit from r_hi alone leaves at most 1/2 + 2^-13 units, so every later digit stays within
 // +-2^(b-1) (2^(b-1) + 1/2 rounds to even) and d_0 within +-2^11: all exact in FP16.
 template <int NS, int BITS>
@@ -943,6 +958,8 @@ __device__ __forceinline__ void form_slice_row(const uint4* xr, const uint4* x2r
                        ? tr.mask + static_cast<int64_t>(row >> 7) * tr.mask_ld : nullptr;
   float ss = 0.0f;
   DF acc{0.0f, 0.0f};
+  DFCoef kc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if constexpr (MODE == kFormSplit) kc = df_coef(a, b, c);  // once per thread, not per pair
 #pragma unroll
   for (int i = 0; i < kFusedPPT; ++i) {
     const int p0 = i * THREADS + w * 32;  // warp-uniform: the warp's first pair
@@ -952,7 +969,7 @@ __device__ __forceinline__ void form_slice_row(const uint4* xr, const uint4* x2r
       if (p < npairs) {
         uint4 y, sp;
         nz = form_pair<MODE, DOT>(p, row, v[i], kNeedX2 ? v2[i] : v[i], with_x2, a, b, ak, aneg,
-                                  has_c, c, tr, yr, y, ss, acc, &sp);
+                                  has_c, c, tr, yr, y, ss, acc, &sp, &kc);
         v[i] = sp;  // from here on the row is held as its FP32 splits
       }
       if (mrow != nullptr) {
@@ -1046,10 +1063,10 @@ __global__ void __launch_bounds__(THREADS, HAS_X2 ? 1 : 1024 / THREADS)
   // the forming arithmetic, decided once per block (uniform)
   int ak = 0;
   bool aneg = false;
-  const bool no_x2 = (!HAS_X2 || b == 0.0);
-  const bool has_c = (c != 0.0);
+  const bool no_x2 = (!HAS_X2 || coef_is_zero(b));
+  const bool has_c = !coef_is_zero(c);
   int mode = kFormGeneral;
-  if (no_x2 && a == 1.0) mode = kFormPlain;
+  if (no_x2 && coef_is_one(a)) mode = kFormPlain;
   else if (no_x2 && pow2_coef(a, ak, aneg)) mode = kFormPow2;
   // slices only: form in double-float (no FP64 result to write, no filtering)
   if (mode == kFormGeneral && Y == nullptr && tr.tau_bits == 0ull) mode = kFormSplit;
@@ -1083,9 +1100,12 @@ template <int THREADS>
 __global__ void __launch_bounds__(THREADS)
     slice_traces_kernel(const double* X2, const double* X, int64_t ld, int n, int cols,
                         __half* out, double* out_scale, int64_t out_ld, int64_t plane, int nslice,
-                        int bits, double* partials, const int* skip) {
+                        int bits, double* partials, const int* skip,
+                        const double* __restrict__ x_row_dot) {
   __shared__ float red_ss[THREADS / 32];
   __shared__ DF red_dot[3][THREADS / 32];
+  // ||X_r||^2 is X's own row dot product when X's slicing pass left it (x_row_dot != null)
+  const bool own_x_dot = (x_row_dot == nullptr);
   __shared__ unsigned long long diag_sh[2];
   __shared__ int shift_sh;
   if (skip != nullptr && *skip != 0) return;
@@ -1129,14 +1149,14 @@ __global__ void __launch_bounds__(THREADS)
       ss = fmaf(h0, h0, fmaf(h1, h1, ss));
       a3 = df_fma(df_fma(a3, h0, l0, g0, k0), h1, l1, g1, k1);
       a4 = df_fma(df_fma(a4, h0, l0, h0, l0), h1, l1, h1, l1);
-      a5 = df_fma(df_fma(a5, g0, k0, g0, k0), g1, k1, g1, k1);
+      if (own_x_dot) a5 = df_fma(df_fma(a5, g0, k0, g0, k0), g1, k1, g1, k1);
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
   a3 = df_warp_sum(a3);
   a4 = df_warp_sum(a4);
-  a5 = df_warp_sum(a5);
+  if (own_x_dot) a5 = df_warp_sum(a5);
   if (lane == 0) {
     red_ss[w] = ss;
     red_dot[0][w] = a3;
@@ -1158,7 +1178,7 @@ __global__ void __launch_bounds__(THREADS)
     pr[1] = __longlong_as_double(static_cast<long long>(diag_sh[1]));
     pr[2] = df_to_double(d3);
     pr[3] = df_to_double(d4);
-    pr[4] = df_to_double(d5);
+    pr[4] = own_x_dot ? df_to_double(d5) : x_row_dot[row];
     int e = 0;
     unsigned long long scb;
     if (t > 0.0f && isfinite(t)) {
@@ -1525,6 +1545,15 @@ __global__ void trs4_control_kernel(const double* partials, int nblocks, Trs4Sta
     stop = 1;
   } else if (fabs(idem) < 1e-4 * Nf && fabs(idem) > 0.5 * fabs(st->idem_prev)) {
     stop = 2;  // the idempotency error no longer falls: the arithmetic's floor is reached
+  } else if (st->floor_rule && st->iter > 0 && fabs(st->idem_prev) < 0.01 &&
+             (st->branch == 3 || (st->branch == 2 && st->method == kPurifyTrs4)) &&
+             fabs(idem) > 20.0 * st->idem_prev * st->idem_prev) {
+    // The step that made this iterate was quadratic: with every eigenvalue within
+    // e = Tr(X - X^2) < 0.01 of 0 or 1, McWeeny maps a distance d to at most 3 d^2 and the
+    // TRS4 map (0 <= gamma <= 6) to at most 6 d^2 + O(d^3), so in exact arithmetic the new
+    // error is below 6 e_prev^2.  An error more than 20 e_prev^2 was set by the products'
+    // rounding: this iterate is at the floor, and a further step would only confirm it.
+    stop = 2;
   }
   if (stop == 0 && st->max_iter > 0 && st->iter >= st->max_iter) stop = 4;
   // Estimated spectral bounds that missed part of the spectrum leave Tr X outside [0, n].
@@ -1665,9 +1694,10 @@ __global__ void x0_coef_kernel(const double* bounds, double* coef) {
 
 // Start vector: a fixed pseudo-random vector (integer hash) in [-0.5, 0.5), normalised; the
 // previous vector 0.  One block.
-__global__ void lanczos_init_kernel(int n, float* x, float* xprev) {
+__global__ void lanczos_init_kernel(int n, float* x, float* xprev, unsigned* counter) {
   __shared__ float red[32];
   __shared__ float inv_sh;
+  if (threadIdx.x == 0 && counter != nullptr) *counter = 0u;
   float acc = 0.0f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     unsigned h = static_cast<unsigned>(i) * 2654435761u + 0x9E3779B9u;
@@ -1685,46 +1715,6 @@ __global__ void lanczos_init_kernel(int n, float* x, float* xprev) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     x[i] *= inv;
     xprev[i] = 0.0f;
-  }
-}
-
-// y = A x, one row per block with all of the row's loads in flight (rows of even length up to
-// kFusedMaxCols, 16-byte aligned).
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS)
-    matvec_rows_f32_kernel(const double* A, int64_t lda, int n, const float* __restrict__ x,
-                           float* y) {
-  __shared__ float red[THREADS / 32];
-  const int row = blockIdx.x;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int npairs = n >> 1;
-  const uint4* ar = reinterpret_cast<const uint4*>(A + row * lda);
-  const float2* x2 = reinterpret_cast<const float2*>(x);
-  uint4 va[kFusedPPT];
-#pragma unroll
-  for (int i = 0; i < kFusedPPT; ++i) {
-    const int p = i * THREADS + threadIdx.x;
-    va[i] = make_uint4(0u, 0u, 0u, 0u);
-    if (p < npairs) va[i] = ar[p];
-  }
-  float acc = 0.0f;
-#pragma unroll
-  for (int i = 0; i < kFusedPPT; ++i) {
-    const int p = i * THREADS + threadIdx.x;
-    if (p < npairs) {
-      const float2 xv = x2[p];
-      acc = fmaf(trunc_words(va[i].y, va[i].x), xv.x, acc);
-      acc = fmaf(trunc_words(va[i].w, va[i].z), xv.y, acc);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) red[w] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float t = 0.0f;
-    for (int j = 0; j < THREADS / 32; ++j) t += red[j];
-    y[row] = t;
   }
 }
 
@@ -1782,6 +1772,115 @@ __global__ void lanczos_update_kernel(float* y, float* x, float* xprev, int n, d
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     xprev[i] = x[i];
     x[i] = y[i] * inv;
+  }
+}
+
+// One whole Lanczos step in one launch: y = A x with one block per row (rows of even length up
+// to kFusedMaxCols), then the last block to finish (a counter in global memory; no block waits
+// for another) does the step's vector update as lanczos_update_kernel does, and resets the
+// counter for the next launch.  MODE 0 reads the FP64 matrix; MODE 1 reads it and also writes
+// its FP32 truncation to a32 (row stride lda32 floats); MODE 2 reads that FP32 copy, half the
+// bytes, which stays in L2 between steps for n up to ~5600.
+constexpr int kLanczosRead64 = 0, kLanczosCopy32 = 1, kLanczosRead32 = 2;
+
+template <int THREADS, int MODE>
+__global__ void __launch_bounds__(THREADS)
+    lanczos_step_kernel(const double* A, int64_t lda, float* a32, int64_t lda32, int n,
+                        float* y, float* x, float* xprev, unsigned* counter, double* ab, int k,
+                        int kmax) {
+  __shared__ float red[32];
+  __shared__ float alpha_sh, inv_sh;
+  __shared__ int last_sh;
+  const int row = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int npairs = n >> 1;
+  const float2* x2 = reinterpret_cast<const float2*>(x);
+  float acc = 0.0f;
+  if (MODE == kLanczosRead32) {
+    const float2* ar = reinterpret_cast<const float2*>(a32 + row * lda32);
+    float2 va[kFusedPPT];
+#pragma unroll
+    for (int i = 0; i < kFusedPPT; ++i) {
+      const int p = i * THREADS + threadIdx.x;
+      va[i] = make_float2(0.0f, 0.0f);
+      if (p < npairs) va[i] = ar[p];
+    }
+#pragma unroll
+    for (int i = 0; i < kFusedPPT; ++i) {
+      const int p = i * THREADS + threadIdx.x;
+      if (p < npairs) {
+        const float2 xv = x2[p];
+        acc = fmaf(va[i].x, xv.x, acc);
+        acc = fmaf(va[i].y, xv.y, acc);
+      }
+    }
+  } else {
+    const uint4* ar = reinterpret_cast<const uint4*>(A + row * lda);
+    float2* cr = (MODE == kLanczosCopy32) ? reinterpret_cast<float2*>(a32 + row * lda32) : nullptr;
+    uint4 va[kFusedPPT];
+#pragma unroll
+    for (int i = 0; i < kFusedPPT; ++i) {
+      const int p = i * THREADS + threadIdx.x;
+      va[i] = make_uint4(0u, 0u, 0u, 0u);
+      if (p < npairs) va[i] = ar[p];
+    }
+#pragma unroll
+    for (int i = 0; i < kFusedPPT; ++i) {
+      const int p = i * THREADS + threadIdx.x;
+      if (p < npairs) {
+        const float a0 = trunc_words(va[i].y, va[i].x), a1 = trunc_words(va[i].w, va[i].z);
+        if (MODE == kLanczosCopy32) cr[p] = make_float2(a0, a1);
+        const float2 xv = x2[p];
+        acc = fmaf(a0, xv.x, acc);
+        acc = fmaf(a1, xv.y, acc);
+      }
+    }
+  }
+  // fixed summation order: per thread, warp butterfly, warps in turn
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) red[w] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int j = 0; j < THREADS / 32; ++j) t += red[j];
+    y[row] = t;
+    __threadfence();
+    const unsigned done = atomicAdd(counter, 1u);
+    last_sh = (done + 1u == gridDim.x) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!last_sh) return;
+  // the last block: every y[i] is written and visible (fence before each block's count)
+  __threadfence();
+  if (threadIdx.x == 0) *counter = 0u;
+  const float beta_prev = (k > 0) ? static_cast<float>(ab[kmax + k - 1]) : 0.0f;
+  float s = 0.0f;
+  for (int i = threadIdx.x; i < n; i += THREADS) s = fmaf(x[i], __ldcg(y + i), s);
+  s = block_sum_f(s, red);
+  if (threadIdx.x == 0) alpha_sh = s;
+  __syncthreads();
+  const float alpha = alpha_sh;
+  float ss = 0.0f;
+  for (int i = threadIdx.x; i < n; i += THREADS) {
+    const float wv = __ldcg(y + i) - alpha * x[i] - beta_prev * xprev[i];
+    ss = fmaf(wv, wv, ss);
+  }
+  ss = block_sum_f(ss, red);
+  if (threadIdx.x == 0) {
+    const float beta = sqrtf(ss);
+    ab[k] = static_cast<double>(alpha);
+    const bool ends = !(beta > 1e-5f * (fabsf(alpha) + beta_prev));
+    ab[kmax + k] = ends ? 0.0 : static_cast<double>(beta);
+    inv_sh = ends ? 0.0f : 1.0f / beta;
+  }
+  __syncthreads();
+  const float inv = inv_sh;
+  for (int i = threadIdx.x; i < n; i += THREADS) {
+    const float xi = x[i];
+    const float wv = __ldcg(y + i) - alpha * xi - beta_prev * xprev[i];
+    xprev[i] = xi;
+    x[i] = wv * inv;
   }
 }
 
@@ -2137,29 +2236,46 @@ cudaError_t form_and_slice(const double* X, int64_t ldx, const double* X2, int64
 }
 
 cudaError_t lanczos(const double* A, int64_t lda, int n, int steps, double* work,
-                    double* partials, double* ab_dev, cudaStream_t stream) {
+                    double* partials, double* ab_dev, cudaStream_t stream, float* a32,
+                    int64_t lda32) {
   (void)partials;
   if (n <= 0 || steps <= 0) return cudaSuccess;
   float* x = reinterpret_cast<float*>(work);
   float* xprev = x + n;
   float* y = xprev + n;
+  unsigned* counter = reinterpret_cast<unsigned*>(y + n);
   const bool rows_fit = n % 2 == 0 && n <= kFusedMaxCols && lda % 2 == 0 &&
                         (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+  const bool copy32 = rows_fit && a32 != nullptr && lda32 >= n && lda32 % 2 == 0 &&
+                      (reinterpret_cast<uintptr_t>(a32) & 7) == 0;
   const int nb = (n + kRowsPerBlock - 1) / kRowsPerBlock;
   count_launch();
-  lanczos_init_kernel<<<1, 1024, 0, stream>>>(n, x, xprev);
+  lanczos_init_kernel<<<1, 1024, 0, stream>>>(n, x, xprev, counter);
+  const int threads = (n / 2 <= 128 * kFusedPPT) ? 128 : (n / 2 <= 256 * kFusedPPT) ? 256 : 512;
   for (int k = 0; k < steps; ++k) {
     count_launch();
-    if (!rows_fit)
+    if (!rows_fit) {
       matvec_f32_kernel<<<nb, kRowsPerBlock * 32, 0, stream>>>(A, lda, n, x, y);
-    else if (n / 2 <= 128 * kFusedPPT)
-      matvec_rows_f32_kernel<128><<<n, 128, 0, stream>>>(A, lda, n, x, y);
-    else if (n / 2 <= 256 * kFusedPPT)
-      matvec_rows_f32_kernel<256><<<n, 256, 0, stream>>>(A, lda, n, x, y);
-    else
-      matvec_rows_f32_kernel<512><<<n, 512, 0, stream>>>(A, lda, n, x, y);
-    count_launch();
-    lanczos_update_kernel<<<1, 1024, 0, stream>>>(y, x, xprev, n, ab_dev, k, steps);
+      count_launch();
+      lanczos_update_kernel<<<1, 1024, 0, stream>>>(y, x, xprev, n, ab_dev, k, steps);
+      continue;
+    }
+    // the first step reads the FP64 matrix and leaves its FP32 copy, the later ones read that
+    const int mode = !copy32 ? kLanczosRead64 : (k == 0 ? kLanczosCopy32 : kLanczosRead32);
+#define GDM_LZ(T, M)                                                                   \
+  lanczos_step_kernel<T, M><<<n, T, 0, stream>>>(A, lda, a32, lda32, n, y, x, xprev, counter, \
+                                                 ab_dev, k, steps)
+#define GDM_LZT(T)                                     \
+  do {                                                 \
+    if (mode == kLanczosRead64) GDM_LZ(T, kLanczosRead64);      \
+    else if (mode == kLanczosCopy32) GDM_LZ(T, kLanczosCopy32); \
+    else GDM_LZ(T, kLanczosRead32);                    \
+  } while (0)
+    if (threads == 128) GDM_LZT(128);
+    else if (threads == 256) GDM_LZT(256);
+    else GDM_LZT(512);
+#undef GDM_LZT
+#undef GDM_LZ
   }
   return cudaGetLastError();
 }
@@ -2193,7 +2309,7 @@ cudaError_t trs4_traces(const double* X, const double* X2, int64_t ld, int n, do
 
 cudaError_t slice_traces(const double* X2, const double* X, int64_t ld, int n, SliceBuf* out,
                          int nslice, int bits, double* partials, int* nrows, cudaStream_t stream,
-                         const int* skip, bool zero_pad) {
+                         const int* skip, bool zero_pad, const double* x_row_dot) {
   *nrows = 0;
   if (n <= 0) return cudaSuccess;
   if (!slice_traces_fits(X2, X, ld, n, out, nslice, zero_pad)) return cudaErrorInvalidValue;
@@ -2210,15 +2326,15 @@ cudaError_t slice_traces(const double* X2, const double* X, int64_t ld, int n, S
   if (npairs <= 128 * kFusedPPT)
     slice_traces_kernel<128><<<n, 128, 0, stream>>>(X2, X, ld, n, cols, out->data,
                                                    out->row_scale, out->ld, plane, nslice, bits,
-                                                   partials, skip);
+                                                   partials, skip, x_row_dot);
   else if (npairs <= 256 * kFusedPPT)
     slice_traces_kernel<256><<<n, 256, 0, stream>>>(X2, X, ld, n, cols, out->data,
                                                    out->row_scale, out->ld, plane, nslice, bits,
-                                                   partials, skip);
+                                                   partials, skip, x_row_dot);
   else
     slice_traces_kernel<512><<<n, 512, 0, stream>>>(X2, X, ld, n, cols, out->data,
                                                    out->row_scale, out->ld, plane, nslice, bits,
-                                                   partials, skip);
+                                                   partials, skip, x_row_dot);
   *nrows = n;
   return cudaGetLastError();
 }

@@ -317,7 +317,10 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
   // (estimates of lambda_max and lambda_min of S from inside the spectrum)
   CK(gershgorin(S, ld, n, h->partials, bounds, s));
   const int lzs = std::min(kLanczosS, n);
-  CK(lanczos(S, ld, n, lzs, h->lanczos_ws, h->partials, h->small + SM_LANCZOS, s));
+  // the FP32 copy of S for the recurrence's later steps lives in M's buffer (unused until the
+  // Newton-Schulz iteration)
+  CK(lanczos(S, ld, n, lzs, h->lanczos_ws, h->partials, h->small + SM_LANCZOS, s,
+             reinterpret_cast<float*>(h->f[F_T]), ld));
   CK(lanczos_bounds(h->small, lzs, SM_BOUNDS_S, SM_LANCZOS, SM_EST_S, s));
   double smv[SM_EST_S + 5];
   gdm_status st = read_small(h, 0, SM_EST_S + 5, smv);
@@ -591,7 +594,9 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   const int lz = (h->bounds_method == GDM_BOUNDS_LANCZOS)
                      ? static_cast<int>(std::min<int64_t>(h->lanczos_steps, n)) : 0;
   if (lz > 0) {
-    CK(lanczos(Ht, ld, n, lz, h->lanczos_ws, h->partials, h->small + SM_LANCZOS, s));
+    // T = Z^T H is consumed: its buffer takes the FP32 copy of H~
+    CK(lanczos(Ht, ld, n, lz, h->lanczos_ws, h->partials, h->small + SM_LANCZOS, s,
+               reinterpret_cast<float*>(h->f[F_T]), ld));
     CK(lanczos_bounds(h->small, lz, SM_GERSH_H, SM_LANCZOS, SM_EST_H, s));
   }
   double sm[SM_EST_H + 3];
@@ -645,6 +650,7 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
   init.n_occ = static_cast<double>(h->n_occ);
   init.method = h->purify;
   init.idem = INFINITY;
+  init.floor_rule = (tr == nullptr) ? 1 : 0;  // a filtered route has its own, higher floor
   CK(cudaMemcpyAsync(h->st_dev, &init, sizeof(init), cudaMemcpyHostToDevice, s));
   h->hist.clear();
   last_idem = INFINITY;
@@ -661,8 +667,11 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
       CK(slice(h, X2, &h->sl[SL_X2], GDM_PHASE_PURIFY, kDotNone, tr));
       x2_sliced = true;
     } else if (pu_sl > 0 && slice_traces_fits(X2, X, ld, n, &h->sl[SL_X2], pu_sl, true)) {
+      // X's slicing pass left ||X_r||^2 in its row dots (self dots of X)
+      const SliceBuf& sx = h->sl[SL_X];
+      const double* x_dots = (sx.row_dot != nullptr && sx.dot_partner == X) ? sx.row_dot : nullptr;
       CK(slice_traces(X2, X, ld, n, &h->sl[SL_X2], pu_sl, bits_for(h, GDM_PHASE_PURIFY),
-                      h->partials, &nb, s, nullptr, true));
+                      h->partials, &nb, s, nullptr, true, x_dots));
       x2_sliced = true;
       row_terms = true;
     }

@@ -199,10 +199,12 @@ cudaError_t zero_column(double* A, int64_t lda, int rows, int col, cudaStream_t 
 // `steps` Lanczos steps on the symmetric n x n matrix A from a fixed start vector (no
 // reorthogonalisation): ab_dev[k] = alpha_k and ab_dev[steps + k] = beta_k for k < steps, the
 // diagonal and off-diagonal of the tridiagonal whose extreme eigenvalues estimate A's from inside.
-// FP32 recurrence (see elementwise.cu); `work` holds >= 2 n doubles (three FP32 vectors);
-// `partials` is unused.
+// FP32 recurrence (see elementwise.cu); `work` holds >= 2 n doubles (three FP32 vectors and a
+// counter); `partials` is unused.  With a32 (n rows of lda32 >= n floats, lda32 even; may be
+// null) the first step also writes A truncated to FP32 there and the later steps read that copy.
 cudaError_t lanczos(const double* A, int64_t lda, int n, int steps, double* work,
-                    double* partials, double* ab_dev, cudaStream_t stream);
+                    double* partials, double* ab_dev, cudaStream_t stream, float* a32 = nullptr,
+                    int64_t lda32 = 0);
 
 // Spectral bounds from a Lanczos tridiagonal (small[lanczos_at..]: alpha_0..alpha_{steps-1},
 // beta_0..beta_{steps-1}) and Gershgorin's interval (small[gersh_at..+1]): the extreme Ritz values
@@ -223,10 +225,12 @@ cudaError_t gershgorin(const double* A, int64_t lda, int n, double* partials, do
 // (partials: kTraceTerms doubles per block, `nblocks` returned through *nblocks).
 constexpr int kTraceTerms = 5;
 // TRS4 trace terms per row (partials: n x kTraceTerms) and the slices of X2 in one pass;
-// slice_traces_fits says whether the shapes and alignments allow it.
+// slice_traces_fits says whether the shapes and alignments allow it.  x_row_dot (may be null):
+// ||X_r||^2 per row as X's own slicing pass computed it, taken instead of summing it again.
 cudaError_t slice_traces(const double* X2, const double* X, int64_t ld, int n, SliceBuf* out,
                          int nslice, int bits, double* partials, int* nrows, cudaStream_t stream,
-                         const int* skip = nullptr, bool zero_pad = false);
+                         const int* skip = nullptr, bool zero_pad = false,
+                         const double* x_row_dot = nullptr);
 bool slice_traces_fits(const double* X2, const double* X, int64_t ld, int n, const SliceBuf* out,
                        int nslice, bool zero_pad = false);
 // w->row_dot[i] = <W_i, X2_i> for W = coef[0] X + coef[1] X2 + coef[2] I, from slice_traces'
@@ -275,6 +279,7 @@ struct Trs4State {
   int check_trace;        // 1: a trace outside [-0.5, n + 0.5] stops with 3 and sets failed
   int failed;
   double n;               // matrix size (for check_trace)
+  int floor_rule;         // 1: also stop once a quadratic step lands at the rounding floor
 };
 cudaError_t trs4_control(const double* partials, int nblocks, Trs4State* st, double tol_idem,
                          cudaStream_t stream);

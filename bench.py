@@ -407,7 +407,7 @@ def torch_fp64_route(H, S, n_occ, torch):
         t1, t2 = float(torch.trace(X)), float(torch.trace(X2))
         t3, t4 = float((X2 * X).sum()), float((X2 * X2).sum())
         idem = t1 - float((X * X).sum())
-        if abs(idem) <= 1e-13 * N or (abs(idem) < 1e-4 * N and abs(idem) > 0.5 * abs(prev_idem)):
+        if abs(idem) <= 1e-11 * N or (abs(idem) < 1e-4 * N and abs(idem) > 0.5 * abs(prev_idem)):
             break
         prev_idem = idem
         trG = t2 - 2.0 * t3 + t4

@@ -154,7 +154,8 @@ gdm_status gdm_set_slices(gdm_handle* h, gdm_phase phase, int nslice, int max_or
                           int slice_bits);
 
 /* Stopping tolerance of the purification: stop when |Tr(X - X^2)| <= idem_tol * n_occ
- * (default 1e-13) or when that error stops falling; trace_tol is the |Tr(P S) - n_occ|
+ * (default 1e-11: the eigenvalues' part of the relative Frobenius error of P is then at most
+ * 1e-11 sqrt(n_occ)) or when that error stops falling; trace_tol is the |Tr(P S) - n_occ|
  * above which the solve reports GDM_ERR_NOT_CONVERGED (default 1e-6; 0 disables). */
 gdm_status gdm_set_tolerance(gdm_handle* h, double idem_tol, double trace_tol);
 

@@ -123,26 +123,24 @@ __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
 
 // A split of the same kind from the two 32-bit words of the double (lo word first in memory),
 // for data that is loaded and kept in integer registers: hi the top 24 significant bits, lo the
-// next 23 (fewer integer operations than normalising the whole remainder).
+// next 23, for |x| in [2^-103, 2^128) (biased FP64 exponent E in [920, 1150]); smaller
+// magnitudes, zero included, give hi = lo = 0, and larger ones, Inf and NaN give hi = NaN (a
+// non-finite row either way).  Branch-free, about a dozen integer operations:
+//  * hi: subtracting 896 from E rebiases the exponent to FP32's (E - 896 in [24, 254] fits the
+//    8-bit field), and a funnel shift by 3 moves exponent and mantissa into FP32's places while
+//    bringing in the low word's top 3 bits; the sign is put back;
+//  * lo: bits 28..6 of the low word, as 2^k (1 + m 2^-23) - 2^k with 2^k (k = E - 1046) the
+//    weight of bit 29, whose FP32 pattern is hi's sign and exponent less 23: one exact FP32
+//    subtraction (both operands share the exponent).  |x - hi - lo| < 2^-46 |x|.
 __device__ __forceinline__ void split_words(unsigned whi, unsigned wlo, float& hi, float& lo) {
-  const int E = static_cast<int>((whi >> 20) & 0x7FF);
-  const unsigned sign = whi & 0x80000000u;
-  const int ef = E - 1023 + 127;
-  // hi: the top 24 significant bits, truncated
-  const unsigned hbits = sign | (static_cast<unsigned>(ef) << 23) | ((whi & 0xFFFFFu) << 3) |
-                         (wlo >> 29);
-  // lo: the next 23 bits (bits 28..6 of the low word), as 2^k (1 + m 2^-23) - 2^k with 2^k the
-  // weight of bit 29: one exact FP32 subtraction (both operands share the exponent) instead of
-  // normalising the remainder bit by bit.  |x - hi - lo| < 2^-46 |x|.
-  const unsigned fk = sign | (static_cast<unsigned>(E - 919) << 23);  // 2^k, k = E - 1046
-  const float f1 = __uint_as_float(fk | ((wlo >> 6) & 0x7FFFFFu));
-  const float f0 = __uint_as_float(fk);
-  const bool normal = (E != 0) && (E != 0x7FF) && (ef > 0) && (ef < 255);
-  const unsigned nan_bit = (E == 0x7FF && ((whi & 0xFFFFFu) | wlo) != 0u) ? 1u : 0u;
-  hi = __uint_as_float(normal ? hbits
-                              : (E == 0x7FF || ef >= 255 ? (sign | 0x7F800000u | nan_bit) : 0u));
-  // 2^k is an FP32 normal number for E >= 920 (|x| >= 2^-103); below that lo is dropped
-  lo = (normal && E >= 920) ? __fsub_rn(f1, f0) : 0.0f;
+  const unsigned E = (whi >> 20) & 0x7FFu;
+  const bool in_range = (E - 920u) <= 230u;
+  const unsigned hbits =
+      (__funnelshift_l(wlo, whi - (896u << 20), 3) & 0x7FFFFFFFu) | (whi & 0x80000000u);
+  const unsigned fk = (hbits & 0xFF800000u) - (23u << 23);
+  const float l = __fsub_rn(__uint_as_float(fk | ((wlo >> 6) & 0x7FFFFFu)), __uint_as_float(fk));
+  hi = __uint_as_float(in_range ? hbits : (E > 1150u ? 0x7FC00000u : 0u));
+  lo = in_range ? l : 0.0f;
 }
 
 // x truncated to FP32 from the two words of the double (integer operations only): the top 24

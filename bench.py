@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="config1")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-fp64-ref", action="store_true", help="skip the all-FP64 GPU solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--truncation", type=float, default=0.0,

@@ -34,7 +34,6 @@
 // partial wave are split along k (sliced_gemm).  Symmetric mode computes only tiles
 // on or above the diagonal and writes the mirror image.
 #include <atomic>
-#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -732,19 +731,7 @@ int build_pairs(int nslice, int max_order, SlicedGemmArgs* a) {
   return np;
 }
 
-// k tile of the two-slice format: 64 (3 stages) unless GDM_GEMM_TWO_SLICE_BK=32 (6 stages)
-static bool two_slice_bk32() {
-  static const bool v = [] {
-    const char* e = getenv("GDM_GEMM_TWO_SLICE_BK");
-    return e != nullptr && e[0] == '3' && e[1] == '2';
-  }();
-  return v;
-}
-
-int sliced_gemm_bk(int nslice) {
-  if (nslice == 2 && two_slice_bk32()) return 32;
-  return (nslice >= 4) ? 32 : 64;
-}
+int sliced_gemm_bk(int nslice) { return (nslice >= 4) ? 32 : 64; }
 
 cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& B, const Precision& prec,
                         SlicedGemmArgs args, cudaStream_t stream) {
@@ -802,9 +789,7 @@ cudaError_t sliced_gemm(const SliceBuf& A, const SliceBuf& B, const Precision& p
     return cudaErrorInvalidValue;
   switch (nslice) {
     case 1: return launch_cfg<1, 64, 6>(ta, tb, args, grid, stream);
-    case 2:
-      return bk == 32 ? launch_cfg<2, 32, 6>(ta, tb, args, grid, stream)
-                      : launch_cfg<2, 64, 3>(ta, tb, args, grid, stream);
+    case 2: return launch_cfg<2, 64, 3>(ta, tb, args, grid, stream);
     case 3: return launch_cfg<3, 64, 2>(ta, tb, args, grid, stream);
     default: return launch_cfg<4, 32, 3>(ta, tb, args, grid, stream);
   }

@@ -1690,6 +1690,20 @@ __global__ void x0_coef_kernel(const double* bounds, double* coef) {
 // and sums in a fixed order.  The Ritz values then carry errors of order 1e-6 ||A||, far inside
 // the margins.
 
+// v_j = +1 or -1 from an integer hash of (j, seed): a Rademacher probe, E[v v^T] = I.  The
+// mixing steps are those of the published 'lowbias32' integer hash (C. Wellons).
+__global__ void rademacher_kernel(double* v, int n, unsigned seed) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  unsigned h = static_cast<unsigned>(j) * 2654435761u + seed * 0x9E3779B9u;
+  h ^= h >> 16;
+  h *= 0x7FEB352Du;
+  h ^= h >> 15;
+  h *= 0x846CA68Bu;
+  h ^= h >> 16;
+  v[j] = (h & 0x80000000u) ? 1.0 : -1.0;
+}
+
 // Start vector: a fixed pseudo-random vector (integer hash) in [-0.5, 0.5), normalised; the
 // previous vector 0.  One block.
 __global__ void lanczos_init_kernel(int n, float* x, float* xprev, unsigned* counter) {
@@ -2477,6 +2491,19 @@ cudaError_t set_identity(double* A, int64_t lda, int n, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   count_launch();
   identity_kernel<<<n, 256, 0, stream>>>(A, lda, n);
+  return cudaGetLastError();
+}
+
+bool matvec_rows_fit(const double* A, int64_t lda, int n, const double* v) {
+  // dot_partials' one-block-per-row path with the vector as every row of B (ldb = 0)
+  return n > 0 && n % 2 == 0 && n <= kFusedMaxCols && lda % 2 == 0 &&
+         (reinterpret_cast<uintptr_t>(A) & 15) == 0 && (reinterpret_cast<uintptr_t>(v) & 15) == 0;
+}
+
+cudaError_t fill_rademacher(double* v, int n, unsigned seed, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  rademacher_kernel<<<(n + 255) / 256, 256, 0, stream>>>(v, n, seed);
   return cudaGetLastError();
 }
 

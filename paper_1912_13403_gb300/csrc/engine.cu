@@ -287,6 +287,43 @@ gdm_status check_device_error(gdm_handle* h) {
 constexpr int kLanczosS = 16;  // Lanczos steps on S for its spectral estimates
 constexpr double kNsHandoff = 0.005;  // ||I - M||_F at which Newton-Schulz hands over
 
+// ||Z^T S Z - I||_F of the refined Z from two Rademacher probes v: E ||(Z^T S Z - I) v||^2 =
+// ||Z^T S Z - I||_F^2, and each probe costs three double-float matrix-vector products
+// (u = Z v, w = S u, t = Z^T w, reading Z^T from its explicit copy) and an FP64 difference
+// t - v, where forming Z^T S Z itself takes two full-precision products.  Scratch: four rows of
+// F_U (the refinement's delta, no longer needed).  *done = false (nothing run) when the rows do
+// not fit the one-block-per-row products; the caller then measures.
+gdm_status probe_z_err(gdm_handle* h, const double* Z, const double* Zt, double* z_err,
+                       bool* done) {
+  *done = false;
+  const int n = static_cast<int>(h->n);
+  const int64_t ld = h->ld;
+  cudaStream_t s = h->stream;
+  const double* S = h->f[F_S];
+  double* v = h->f[F_U];
+  double *u = v + ld, *w = v + 2 * ld, *t = v + 3 * ld;
+  if (n < 4 || !matvec_rows_fit(Z, ld, n, v) || !matvec_rows_fit(Zt, ld, n, v) ||
+      !matvec_rows_fit(S, ld, n, v))
+    return GDM_OK;
+  constexpr int kProbes = 2;
+  for (int p = 0; p < kProbes; ++p) {
+    int nb = 0;
+    CK(fill_rademacher(v, n, 0x51u + static_cast<unsigned>(p), s));
+    CK(dot_partials(Z, ld, v, 0, n, n, 0, u, &nb, s));
+    CK(dot_partials(S, ld, u, 0, n, n, 0, w, &nb, s));
+    CK(dot_partials(Zt, ld, w, 0, n, n, 0, t, &nb, s));
+    CK(form_and_slice(t, ld, v, ld, 1, n, nullptr, 1.0, -1.0, 0.0, t, ld, nullptr, 0, nullptr, s));
+    CK(dot_partials(t, ld, nullptr, 0, 1, n, 0, h->partials + p, &nb, s));  // ||t - v||^2
+  }
+  CK(reduce_partials(h->partials, kProbes, 1, h->small + SM_RED, s));
+  double sum = 0.0;
+  const gdm_status st = read_small(h, SM_RED, 1, &sum);
+  if (st != GDM_OK) return st;
+  *z_err = std::sqrt(sum / kProbes);
+  *done = true;
+  return GDM_OK;
+}
+
 // Whether a refinement step taken from ||delta||_F = before, which measured `after`, reached
 // the rounding floor (the third-order prediction (5/8) before^3 is at or below what is left).
 bool refine_at_floor(double before, double after) {
@@ -436,6 +473,16 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
     double* T = h->f[F_T];
     double* Dl = h->f[F_U];
     double* F = h->f[F_V];
+    if (r == nref && r > 0) {
+      // after the last step only the report remains: estimate it from probes where they fit
+      bool probed = false;
+      st = probe_z_err(h, zc.f, zct.f, &derr, &probed);
+      if (st != GDM_OK) return st;
+      if (probed) {
+        if (!std::isfinite(derr)) return set_err(h, GDM_ERR_NONFINITE, "non-finite Z^T S Z");
+        break;
+      }
+    }
     // Exact diagonals (recomputed from the FP64 operands) for T, delta and Z F: when S is
     // close to I the two factors of each have nearly parallel rows, the truncating FP32
     // accumulators bias every diagonal entry the same way, and the refinement would then drive

@@ -314,5 +314,11 @@ cudaError_t symmetrise(double* A, int64_t lda, int n, cudaStream_t stream);
 
 // Copy rows x cols into a dense-ld destination (device-to-device, strided).
 cudaError_t set_identity(double* A, int64_t lda, int n, cudaStream_t stream);
+// Whether dot_partials(A, lda, v, 0, n, n, 0, y, ...) is the matrix-vector product y = A v in
+// double-float (one block per row, the vector read as every row of B): n even, at most
+// kFusedMaxCols, lda even, A and v 16-byte aligned.
+bool matvec_rows_fit(const double* A, int64_t lda, int n, const double* v);
+// v[j] = +-1 (j < n) from an integer hash of (j, seed).
+cudaError_t fill_rademacher(double* v, int n, unsigned seed, cudaStream_t stream);
 
 }  // namespace gdm

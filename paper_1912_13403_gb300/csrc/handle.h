@@ -69,7 +69,7 @@ struct gdm_handle {
   void* pool = nullptr;
   double* f[gdm::F_COUNT] = {};
   gdm::SliceBuf sl[gdm::SL_COUNT];
-  double* partials = nullptr;  // >= 5 * ceil(n/8) doubles
+  double* partials = nullptr;  // 5 n + 64 doubles
   double* lanczos_ws = nullptr;  // 4 * n_cap doubles: the Lanczos recurrence's vectors
   double* small = nullptr;     // kSmall doubles: coefficients, bounds, reductions
   gdm::Trs4State* st_dev = nullptr;

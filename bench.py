@@ -148,9 +148,9 @@ def job_throughput(units_per_rank, total_ms_this_rank, device="cpu"):
 PHASES = ("newton_schulz", "refine", "transform", "purify")
 
 # DRAM bytes (read + write) per purification product launch at n=4096 from one ncu capture of
-# sliced_gemm_kernel<3,64,2> (profiles/sliced_gemm_purify_n4096.md: X X 371.2 MB, X^2 W 489.4 MB)
+# sliced_gemm_kernel<3,64,2> (profiles/sliced_gemm_purify_n4096.md: X X 370.2 MB, X^2 W 369.9 MB)
 # and the capture's tensor-pipe activity (share of active cycles).
-PURIFY_NCU_N4096 = dict(traffic=430.3e6, tensor_pipe_active=0.766,
+PURIFY_NCU_N4096 = dict(traffic=370.1e6, tensor_pipe_active=0.748,
                         source="profiles/sliced_gemm_purify_n4096.md")
 
 

@@ -67,10 +67,6 @@ const double* st_field(const gdm_handle* h, size_t offset) {
   return reinterpret_cast<const double*>(reinterpret_cast<const char*>(h->st_dev) + offset);
 }
 
-const int* st_field_int(const gdm_handle* h, size_t offset) {
-  return reinterpret_cast<const int*>(reinterpret_cast<const char*>(h->st_dev) + offset);
-}
-
 int slices_for(const gdm_handle* h, int ph) { return sliced(h, ph) ? h->phase[ph].nslice : 0; }
 
 cudaEvent_t pool_event(gdm_handle* h) {
@@ -136,13 +132,10 @@ double sliced_flops(const gdm_handle* h, const Precision& pr, bool sym) {
 // diagonal add up with one sign and the FP32 accumulators' truncation biases them.
 // fmt: a format other than the phase's for this product (its slice width must be the
 // operands'; it may read only their leading slices), e.g. a short format for a small term.
-// skip: a device flag that makes the sliced launch a no-op when non-zero (products enqueued
-// ahead of the host's read of the controller, see the purification loop); the diagonal fix-up,
-// which does not read it, must then be served by the row dot products (diag_dot).
 cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const double* D,
                     double alpha, double beta, double diag, bool sym, int ph,
                     const double* coef = nullptr, bool exact_diag = false,
-                    const Precision* fmt = nullptr, const int* skip = nullptr) {
+                    const Precision* fmt = nullptr) {
   const int n = static_cast<int>(h->n);
   if (sliced(h, ph)) {
     const Precision& pr = fmt != nullptr ? *fmt : h->phase[ph];
@@ -163,7 +156,6 @@ cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const dou
     a.splitk_cnt = h->split_cnt;
     a.splitk_slots = h->split_slots;
     a.splitk_tiles = kSplitTiles;
-    a.skip = skip;
     // truncated purification: skip the k blocks where an operand tile is empty
     if (ph == GDM_PHASE_PURIFY && h->trunc_tau > 0.0 && A.sl->mask_valid && Bt.sl->mask_valid) {
       a.mask_a = A.sl->tile_mask;
@@ -192,7 +184,6 @@ cudaError_t product(gdm_handle* h, Op A, Op Bt, double* C, double* Ct, const dou
       h->prof_pending.push_back({e0, e1, sliced_flops(h, pr, sym), alg_flops(h, sym), 0, ph});
     }
     if (!exact_diag || a.diag_dot != nullptr) return cudaSuccess;
-    if (skip != nullptr) return cudaErrorInvalidValue;  // the fix-up would ignore the flag
     e = diag_fix(A.f, h->ld, Bt.f, h->ld, C, h->ld, n, n, alpha, beta, D, h->ld, diag, coef,
                  h->stream);
     if (e != cudaSuccess || Ct == nullptr) return e;
@@ -245,7 +236,7 @@ const TruncArgs* purify_trunc(const gdm_handle* h, TruncArgs* tmp) {
 }
 
 cudaError_t slice(gdm_handle* h, const double* src, SliceBuf* dst, int ph, int dot = kDotNone,
-                  const TruncArgs* trunc = nullptr, const int* skip = nullptr) {
+                  const TruncArgs* trunc = nullptr) {
   const int n = static_cast<int>(h->n);
   if (!sliced(h, ph)) {
     if (trunc == nullptr) return cudaSuccess;
@@ -254,7 +245,7 @@ cudaError_t slice(gdm_handle* h, const double* src, SliceBuf* dst, int ph, int d
                           nullptr, 0, nullptr, h->stream, 12, kDotNone, trunc, true);
   }
   return form_and_slice(src, h->ld, nullptr, 0, n, n, nullptr, 1.0, 0.0, 0.0, nullptr, 0, dst,
-                        h->phase[ph].nslice, skip, h->stream, h->phase[ph].bits, dot, trunc,
+                        h->phase[ph].nslice, nullptr, h->stream, h->phase[ph].bits, dot, trunc,
                         true);
 }
 
@@ -734,60 +725,8 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
     if (nb == 0) CK(trs4_traces(X, X2, ld, n, h->partials, &nb, s));
     CK(trs4_control(h->partials, nb, h->st_dev, tol_abs, s));
     CK(cudaMemcpyAsync(h->st_host, h->st_dev, sizeof(Trs4State), cudaMemcpyDeviceToHost, s));
-    // W only as slices (sliced products, no filtering, rows within the one-pass kernels): W's
-    // row dots then come from the trace terms and X^2 W takes its diagonal from them
-    const bool need_w = tr != nullptr || pu_sl == 0 || n + (n & 1) > kFusedMaxCols;
-    const double* coefW = st_field(h, offsetof(Trs4State, coefW));
-    // X_next = X^2 W for the product branches (2: TRS4 F + gamma G, 3: McWeeny), with the
-    // launches made no-ops by `skip` when it is non-zero
-    auto product_branch = [&](const int* skip) -> cudaError_t {
-      cudaError_t e = cudaSuccess;
-      if (!x2_sliced && (e = slice(h, X2, &h->sl[SL_X2], GDM_PHASE_PURIFY)) != cudaSuccess)
-        return e;
-      // with row_terms W's row dot products with X^2 follow from the per-row trace terms:
-      // a <X_i, X2_i> + b ||X2_i||^2 + c (X2)_ii
-      if ((e = form_and_slice(X, ld, X2, ld, n, n, coefW, 0, 0, 0, need_w ? W : nullptr, ld,
-                              pu_sl > 0 ? &h->sl[SL_W] : nullptr, pu_sl, skip, s,
-                              bits_for(h, GDM_PHASE_PURIFY), row_terms ? kDotNone : kDotX2, tr,
-                              true)) != cudaSuccess)
-        return e;
-      if (row_terms && (e = w_row_dots(h->partials, n, coefW, &h->sl[SL_W], X2, s)) != cudaSuccess)
-        return e;
-      // with filtering X^2 and W no longer commute: the full product is symmetrised
-      if ((e = product(h, {X2, &h->sl[SL_X2]}, {W, &h->sl[SL_W]}, Xn, nullptr, nullptr, 1.0, 0.0,
-                       0.0, tr == nullptr, GDM_PHASE_PURIFY, nullptr, true, nullptr, skip)) !=
-          cudaSuccess)
-        return e;
-      if (tr != nullptr && (e = symmetrise(Xn, ld, n, s)) != cudaSuccess) return e;
-      return slice(h, Xn, &h->sl[SL_X], GDM_PHASE_PURIFY, kDotSelf, tr, skip);
-    };
-    // Enqueued ahead: when every launch of the product branch can take the controller's
-    // skip_gemm flag (set unless the branch is 2 or 3 and the loop goes on), those launches go
-    // in behind the state read-back and the host waits for the read-back alone, so the GPU
-    // runs the branch while the host decides (one host round trip hidden per iteration).
-    // Canonical purification (branch 4 clears skip_gemm) and the filtered or FP64 routes
-    // decide first.
-    const bool ahead = tr == nullptr && pu_sl > 0 && !need_w && x2_sliced && row_terms &&
-                       h->purify != kPurifyCanonical;
-    size_t prof_mark = h->prof_pending.size();
-    if (ahead) {
-      CK(cudaEventRecord(h->ev_state, s));
-      CK(product_branch(st_field_int(h, offsetof(Trs4State, skip_gemm))));
-      CK(cudaEventSynchronize(h->ev_state));
-    } else {
-      CK(cudaStreamSynchronize(s));
-    }
+    CK(cudaStreamSynchronize(s));
     const Trs4State& t = *h->st_host;
-    if (ahead && !(t.stop == 0 && (t.branch == 2 || t.branch == 3))) {
-      // the branch enqueued ahead ran as no-ops: X's slices were not replaced (their record
-      // names X_next, which they are not), and its product leaves the launch timings
-      h->sl[SL_X].dot_partner = nullptr;
-      for (size_t k = prof_mark; k < h->prof_pending.size(); ++k) {
-        h->ev_pool.push_back(h->prof_pending[k].a);
-        h->ev_pool.push_back(h->prof_pending[k].b);
-      }
-      h->prof_pending.resize(prof_mark);
-    }
     h->hist.push_back({t.idem, t.t[0], t.gamma, t.stop != 0 ? -1 : t.branch});
     // a trace outside [0, n] means eigenvalues far outside [0, 1]: the bounds did not enclose
     // the spectrum (only estimated bounds can do that)
@@ -818,7 +757,23 @@ gdm_status solve_core(gdm_handle* h, gdm_info* info, double* energy_out) {
       if (tr != nullptr) CK(symmetrise(Xn, ld, n, s));
       CK(slice(h, Xn, &h->sl[SL_X], GDM_PHASE_PURIFY, kDotSelf, tr));
     } else if (t.branch == 2 || t.branch == 3) {  // a product: F + gamma G, or McWeeny
-      if (!ahead) CK(product_branch(nullptr));   // else already enqueued and running
+      if (!x2_sliced) CK(slice(h, X2, &h->sl[SL_X2], GDM_PHASE_PURIFY));
+      // W itself is needed only with filtering or FP64 products (the sliced product takes its
+      // diagonal from the row dot products with X^2)
+      const bool need_w = tr != nullptr || pu_sl == 0 || n + (n & 1) > kFusedMaxCols;
+      // W's row dot products with X^2 follow from the per-row trace terms when slice_traces
+      // produced them (no filtering): a <X_i, X2_i> + b ||X2_i||^2 + c (X2)_ii
+      const bool dots_from_traces = row_terms;
+      const double* coefW = st_field(h, offsetof(Trs4State, coefW));
+      CK(form_and_slice(X, ld, X2, ld, n, n, coefW, 0, 0, 0, need_w ? W : nullptr, ld,
+                        pu_sl > 0 ? &h->sl[SL_W] : nullptr, pu_sl, nullptr, s,
+                        bits_for(h, GDM_PHASE_PURIFY), dots_from_traces ? kDotNone : kDotX2, tr, true));
+      if (dots_from_traces) CK(w_row_dots(h->partials, n, coefW, &h->sl[SL_W], X2, s));
+      // with filtering X^2 and W no longer commute: the full product is symmetrised
+      CK(product(h, {X2, &h->sl[SL_X2]}, {W, &h->sl[SL_W]}, Xn, nullptr, nullptr, 1.0, 0.0, 0.0,
+                 tr == nullptr, GDM_PHASE_PURIFY, nullptr, true));
+      if (tr != nullptr) CK(symmetrise(Xn, ld, n, s));
+      CK(slice(h, Xn, &h->sl[SL_X], GDM_PHASE_PURIFY, kDotSelf, tr));
     } else {
       CK(form_and_slice(X, ld, X2, ld, n, n, st_field(h, offsetof(Trs4State, coefX)), 0, 0, 0,
                         Xn, ld, pu_sl > 0 ? &h->sl[SL_X] : nullptr, pu_sl, nullptr, s,
@@ -954,7 +909,6 @@ void free_all(gdm_handle* h) {
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
-  if (h->ev_state) cudaEventDestroy(h->ev_state);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   h->pool = nullptr;
 }
@@ -1114,8 +1068,7 @@ gdm_status gdm_init(gdm_handle** out, int64_t n_basis, int64_t n_occ, int device
   if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMallocHost(&h->host_buf, sizeof(double) * kSmall) != cudaSuccess ||
       cudaMallocHost(&h->st_host, sizeof(Trs4State)) != cudaSuccess ||
-      cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_state, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
     cudaGetLastError();
     free_all(h);
     delete h;

@@ -82,7 +82,6 @@ struct gdm_handle {
   double* host_buf = nullptr;  // pinned: kSmall doubles
   gdm::Trs4State* st_host = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  cudaEvent_t ev_state = nullptr;  // after the purification controller's state read-back
 
   bool have_H = false, have_S = false, z_valid = false;
   bool have_P = false;  // F_XN holds the density matrix of the current H and S

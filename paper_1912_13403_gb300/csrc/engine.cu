@@ -482,6 +482,20 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
         if (!std::isfinite(derr)) return set_err(h, GDM_ERR_NONFINITE, "non-finite Z^T S Z");
         break;
       }
+    } else if (r > 0 && 0.625 * derr_prev * derr_prev < 1e-4) {
+      // The step from derr_prev < 0.0126 predicts (5/8) derr_prev^3 < 1e-4 derr_prev: it most
+      // likely landed on the rounding floor.  The probes decide that at a fraction of the cost
+      // of forming delta; only if they see the step still converging is delta formed for the
+      // next one.  A wrong call (the probes' few per cent spread) stops with ||delta||_F at
+      // most (5/8) 0.0126^3 = 1.3e-6.
+      double est = 0.0;
+      bool probed = false;
+      st = probe_z_err(h, zc.f, zct.f, &est, &probed);
+      if (st != GDM_OK) return st;
+      if (probed && std::isfinite(est) && refine_at_floor(derr_prev, est)) {
+        derr = est;
+        break;
+      }
     }
     // Exact diagonals (recomputed from the FP64 operands) for T, delta and Z F: when S is
     // close to I the two factors of each have nearly parallel rows, the truncating FP32

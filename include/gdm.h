@@ -91,8 +91,9 @@ typedef struct {
   double idem_err;     /* Tr(P~ - P~^2) of the final orthogonal-basis density matrix */
   double z_err;        /* ||Z^T S Z - I||_F after refinement: after at least one refinement
                           step and for even n <= 8192, estimated from two random +-1 probes v
-                          (E ||(Z^T S Z - I) v||^2 = ||Z^T S Z - I||_F^2; a few per cent
-                          typical spread); otherwise measured from Z^T S Z */
+                          (E ||(Z^T S Z - I) v||^2 = ||Z^T S Z - I||_F^2: a statistical
+                          estimate, within 6% and 25% of the measured value on the two
+                          benchmark inputs); otherwise measured from Z^T S Z */
   double trace_err;    /* |Tr(P S) - n_occ| of the returned P */
   double trace_err_raw; /* |Tr(P S) - n_occ| before the final trace correction */
   double energy;       /* Tr(P H) */

@@ -486,8 +486,9 @@ gdm_status compute_z(gdm_handle* h, gdm_info* info) {
       // The step from derr_prev < 0.0126 predicts (5/8) derr_prev^3 < 1e-4 derr_prev: it most
       // likely landed on the rounding floor.  The probes decide that at a fraction of the cost
       // of forming delta; only if they see the step still converging is delta formed for the
-      // next one.  A wrong call (the probes' few per cent spread) stops with ||delta||_F at
-      // most (5/8) 0.0126^3 = 1.3e-6.
+      // next one.  A wrong call (the estimate at or above the prediction while the true
+      // ||delta||_F is below it) stops with ||delta||_F under the prediction, at most
+      // (5/8) 0.0126^3 = 1.3e-6.
       double est = 0.0;
       bool probed = false;
       st = probe_z_err(h, zc.f, zct.f, &est, &probed);
